@@ -1,0 +1,34 @@
+"""Seeded synthetic inputs shaped like the paper's test matrices.
+
+This module holds no arithmetic of the emulation; it only draws inputs, and it
+is the one module that both the CUDA tests/bench and the CPU oracle's callers
+share.
+
+Section IV-A draws the real and imaginary parts of every entry independently
+as (rand - 0.5) * exp(randn * phi), with rand uniform on (0, 1] and randn
+standard normal; phi widens the exponent range.  Draws come from numpy's
+counter-based Philox generator keyed by the seed.  Matrices are returned in
+column-major (Fortran) order, the BLAS layout of the library's entry points.
+"""
+import numpy as np
+
+
+def paper_matrix(rows, cols, phi, seed, dtype=np.complex128):
+    """rows x cols complex matrix, Re/Im = (U(0,1] - 0.5) * exp(phi * N(0,1))."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    parts = []
+    for _ in range(2):
+        u = 1.0 - rng.random((rows, cols))          # (0, 1]
+        g = rng.standard_normal((rows, cols))
+        parts.append((u - 0.5) * np.exp(g * phi))
+    out = np.empty((rows, cols), dtype=np.complex128, order="F")
+    out.real = parts[0]
+    out.imag = parts[1]
+    return np.asfortranarray(out.astype(dtype))
+
+
+def log_uniform_shapes(count, lo, hi, seed):
+    """count (m, n, k) triples drawn log-uniformly in [lo, hi] (integers)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    v = np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=(count, 3)))
+    return np.clip(np.floor(v).astype(np.int64), lo, hi)
