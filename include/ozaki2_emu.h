@@ -1,0 +1,184 @@
+/*
+ * ozaki2_emu.h -- C ABI of the GB300 (sm_103a) Ozaki-II emulation of complex
+ * matrix multiplication (ZGEMM / CGEMM) through the Chinese Remainder Theorem.
+ *
+ * Method (arXiv 2512.08321): Algorithm 1 (Ozaki-II outline, Section II) with
+ * the Karatsuba complex product (Section III-A, eq. karatsuba) and fast-mode
+ * scaling vectors (Section III-B, eqs. mu-fast / nu-fast):
+ *   1. per-row / per-column power-of-two scaling exponents          (Step III)
+ *   2. truncation to integers and split into symmetric residues
+ *      modulo N pairwise-coprime moduli p_l <= 256                  (Steps IV, V-i, V-ii)
+ *   3. three residue products D, E, F per modulus, reduced mod p_l  (Steps V-iii, V-iv)
+ *   4. CRT reconstruction, inverse scaling, alpha/beta              (Steps V-v, V-vi, VI)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major, as in BLAS.  op(X) is X (EMU_OP_N), X^T
+ *   (EMU_OP_T) or X^H (EMU_OP_C).  op(A) is m x k, op(B) is k x n, C is m x n.
+ * - A, B, C and every buffer argument named "device" are device pointers the
+ *   caller owns; the library never frees them.  alpha and beta point to host
+ *   memory holding {re, im}.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   All work is enqueued on it; calls return without synchronising.  Argument
+ *   errors are returned synchronously and nothing is enqueued.  Launch
+ *   failures return EMU_ERR_CUDA.  Errors detected on the device (a bounded
+ *   wait that expired) are recorded in a device status word that
+ *   emu_stream_status() reads.
+ * - beta == 0 means C is not read.  m, n or k == 0 is a quick return (with
+ *   k == 0, C becomes beta*C, or 0 when beta == 0).
+ * - num_moduli N lies in [EMU_MIN_MODULI, EMU_MAX_MODULI]; k <= 2^17 (Section
+ *   II: the bound under which INT8 products accumulate without error).
+ * - The result equals, bit for bit, the round-to-nearest-even binary64 value
+ *   of the exact CRT reconstruction c'_ij scaled by 2^-(x_i + y_j) (then
+ *   alpha/beta in a fixed fma sequence; complex64 output rounds that binary64
+ *   value once more).  Rows of op(A) / columns of op(B) holding Inf or NaN
+ *   produce NaN in the matching row / column of the result.
+ */
+#ifndef OZAKI2_EMU_H
+#define OZAKI2_EMU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EMU_OK = 0,
+  EMU_ERR_INVALID_ARG = 1,   /* emu_last_bad_param() gives the 1-based position */
+  EMU_ERR_K_TOO_LARGE = 2,   /* k > 2^17 (Section II) */
+  EMU_ERR_MODULI_RANGE = 3,  /* num_moduli outside [EMU_MIN_MODULI, EMU_MAX_MODULI] */
+  EMU_ERR_ALLOC = 4,         /* workspace allocation failed */
+  EMU_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
+  EMU_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
+  EMU_ERR_UNSUPPORTED = 7,   /* no GPU / not an sm_103 device / feature not built */
+  EMU_ERR_WORKSPACE = 8      /* caller workspace smaller than emu_workspace_bytes() */
+} emu_status_t;
+
+typedef enum { EMU_OP_N = 0, EMU_OP_T = 1, EMU_OP_C = 2 } emu_op_t;
+
+/* Engine of the residue products (Step V-iii).  Both are exact and give
+ * identical results:
+ *   EMU_ENGINE_F16: tcgen05.mma kind::f16 with TMEM accumulators.  Residues
+ *     |r| <= 128 are exact in fp16; the FP32 accumulator is reduced modulo p
+ *     in TMEM every `chunk` k so every partial sum stays an integer < 2^24.
+ *   EMU_ENGINE_I8: warp-level mma.sync s8 x s8 -> s32 (the INT8 path sm_103a
+ *     offers; tcgen05 kind::i8 is not available on this target). */
+typedef enum { EMU_ENGINE_AUTO = 0, EMU_ENGINE_F16 = 1, EMU_ENGINE_I8 = 2 } emu_engine_t;
+
+#define EMU_MIN_MODULI 2
+#define EMU_MAX_MODULI 24
+#define EMU_MAX_K (1 << 17)
+#define EMU_EXP_NONFINITE (-32768) /* int16 scaling exponent of a flagged row/column */
+
+/* ---------------------------------------------------------------- GEMMs --- */
+
+/* C = alpha * op(A) op(B) + beta * C, complex128 (double2 interleaved {re,im}).
+ * A: device, lda >= max(1, rows of stored A); B: device, ldb likewise;
+ * C: device, ldc >= max(1, m).  alpha, beta: host double[2]. */
+emu_status_t emu_zgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                       const double* alpha, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, const double* beta,
+                       void* C, int64_t ldc, int num_moduli, void* stream);
+
+/* complex64 analogue (float2 data, host float[2] alpha/beta); the CRT is the
+ * same exact integer reconstruction, the output is rounded to binary32. */
+emu_status_t emu_cgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                       const float* alpha, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, const float* beta,
+                       void* C, int64_t ldc, int num_moduli, void* stream);
+
+/* ------------------------------------------------------------ workspace --- */
+
+/* Bytes of device workspace one call of the given shape needs (is_single: 0
+ * for ZGEMM, 1 for CGEMM).  0 on invalid arguments. */
+size_t emu_workspace_bytes(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli);
+
+/* Use caller-owned device memory [ptr, ptr+bytes) as the workspace of this
+ * device (the current device) for subsequent calls; NULL/0 returns to the
+ * library-managed workspace (cudaMalloc'd, grown on demand, freed at exit).
+ * Calls sharing one workspace must be ordered on one stream. */
+emu_status_t emu_set_workspace(void* ptr, size_t bytes);
+
+/* Select the residue-product engine (default EMU_ENGINE_AUTO = F16) and the
+ * k chunk after which the F16 engine reduces its accumulator (multiple of 64,
+ * 64..960; 0 keeps the default 512). */
+emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
+
+/* ----------------------------------------------------- stage entry points --
+ * The four phases of one emulated GEMM on caller buffers, for stage-wise
+ * checking and for composing other pipelines.  is_single selects complex64
+ * (1) or complex128 (0) inputs/outputs. */
+
+/* Step III (Section III-B): int16 exponents x (m, of mu) and y (n, of nu);
+ * EMU_EXP_NONFINITE marks a row/column holding Inf or NaN. */
+emu_status_t emu_stage_exponents(int is_single, emu_op_t transa, emu_op_t transb,
+                                 int64_t m, int64_t n, int64_t k,
+                                 const void* A, int64_t lda, const void* B, int64_t ldb,
+                                 int num_moduli, int16_t* x, int16_t* y, void* stream);
+
+/* Steps IV and V-i/ii: residue planes.  planesA holds 3N planes of m rows,
+ * planesB 3N planes of n rows, each row kpad elements (kpad >= k, multiple of
+ * 64, zero padded); plane 3l+0 / 3l+1 / 3l+2 holds mod(a'_R), mod(a'_I) and
+ * mod(mod(a'_R)+mod(a'_I)) for modulus l.  Elements are int8 (plane_fp16 = 0)
+ * or the same integers as fp16 (plane_fp16 = 1). */
+emu_status_t emu_stage_split(int is_single, emu_op_t transa, emu_op_t transb,
+                             int64_t m, int64_t n, int64_t k,
+                             const void* A, int64_t lda, const void* B, int64_t ldb,
+                             int num_moduli, const int16_t* x, const int16_t* y,
+                             int plane_fp16, int64_t kpad, void* planesA, void* planesB,
+                             void* stream);
+
+/* Steps V-iii/iv: for job j = 3l + c (c = 0: D, 1: E, 2: F of eq. karatsuba)
+ * residues[j*n*ldr + col*ldr + row] = mod(sum_h planesA[j][row][h] *
+ * planesB[j][col][h], p_l) as int8; ldr >= m, multiple of 16.  The engine
+ * must match the plane element type (F16 <-> fp16 planes, I8 <-> int8). */
+emu_status_t emu_stage_residue_gemm(emu_engine_t engine, int64_t m, int64_t n, int64_t kpad,
+                                    int num_moduli, const void* planesA, const void* planesB,
+                                    int8_t* residues, int64_t ldr, void* stream);
+
+/* Steps V-v, V-vi, VI: C = alpha * 2^-(x_i+y_j) c'_ij + beta * C from the
+ * D/E/F residues (E'_R = mod(D-E), E'_I = mod(F-D-E), then exact CRT). */
+emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli,
+                           const int8_t* residues, int64_t ldr,
+                           const int16_t* x, const int16_t* y,
+                           const void* alpha, const void* beta,
+                           void* C, int64_t ldc, void* stream);
+
+/* ------------------------------------------------------ host-side queries -- */
+
+/* Algorithm 1 Steps I-II as computed by the library: the N moduli (greedy
+ * descending pairwise coprime from 256), q_l = (P/p_l)^-1 mod p_l, P as
+ * little-endian 32-bit limbs (p_limbs capacity >= 8) and the limb count L the
+ * CRT uses.  Host only; no GPU needed.  Any output pointer may be NULL. */
+emu_status_t emu_plan_info(int num_moduli, int32_t* moduli, int32_t* q,
+                           uint32_t* p_limbs, int32_t* crt_limbs);
+
+/* Fast-mode scaling exponent E of the library for a quantised row sum S
+ * (sum of ceil(|t| 2^15)^2), i.e. the largest E with 4^E max(2^32,S) <=
+ * (P-1) 2^27.  Host only. */
+int emu_plan_exponent(int num_moduli, uint64_t S);
+
+/* 1-based index of the offending argument of the last EMU_ERR_INVALID_ARG
+ * returned on this thread (0 if none). */
+int emu_last_bad_param(void);
+
+/* Reads and clears the device status word of the current device after
+ * synchronising `stream`: EMU_OK or the first device-side error recorded. */
+emu_status_t emu_stream_status(void* stream);
+
+/* Launches one kernel that waits, with a bounded spin of about
+ * `limit_cycles` SM cycles, on a device flag that nothing sets; the wait
+ * expires and records EMU_ERR_TIMEOUT in the status word.  Exercises the
+ * bounded-wait path without faulting or hanging the GPU. */
+emu_status_t emu_selftest_bounded_wait(int64_t limit_cycles, void* stream);
+
+/* Library version string (static storage). */
+const char* emu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OZAKI2_EMU_H */

@@ -1,0 +1,403 @@
+// C ABI entry points: argument checks, workspace, the four phases in order.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "emu_internal.h"
+
+namespace emu {
+
+// Device status word: first device-side error recorded (0 = none).
+__device__ unsigned int g_device_status;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+thread_local int t_bad_param = 0;
+
+struct DeviceState {
+  bool init = false;
+  unsigned int* status = nullptr;
+  void* own = nullptr;         // library-managed workspace
+  size_t own_bytes = 0;
+  void* user = nullptr;        // caller workspace (emu_set_workspace)
+  size_t user_bytes = 0;
+};
+
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+emu_engine_t g_engine = EMU_ENGINE_AUTO;
+int g_chunk_k = 512;
+
+emu_status_t bad(int idx) {
+  t_bad_param = idx;
+  return EMU_ERR_INVALID_ARG;
+}
+
+int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) return -1;
+  return d;
+}
+
+// Per-device set-up: sm_103 check and the address of the status word.
+emu_status_t device_init(int dev, DeviceState*& ds) {
+  if (dev < 0 || dev >= kMaxDevices) return EMU_ERR_UNSUPPORTED;
+  ds = &g_dev[dev];
+  if (ds->init) return EMU_OK;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return EMU_ERR_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return EMU_ERR_UNSUPPORTED;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return EMU_ERR_CUDA;
+  ds->status = static_cast<unsigned int*>(p);
+  ds->init = true;
+  return EMU_OK;
+}
+
+// Workspace layout of one GEMM.
+struct Layout {
+  int64_t kpad, ldr;
+  size_t off_x, off_y, off_scr, off_pa, off_pb, off_res, total;
+};
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16) {
+  Layout L;
+  L.kpad = round_up(k > 0 ? k : 1, 64);
+  L.ldr = round_up(m, 16);
+  const size_t esz = fp16 ? 2 : 1;
+  size_t o = 0;
+  L.off_x = o;   o += al(static_cast<size_t>(m) * 2);
+  L.off_y = o;   o += al(static_cast<size_t>(n) * 2);
+  L.off_scr = o; o += al(exponents_scratch_bytes(m > n ? m : n));
+  L.off_pa = o;  o += al(static_cast<size_t>(3 * N) * m * L.kpad * esz);
+  L.off_pb = o;  o += al(static_cast<size_t>(3 * N) * n * L.kpad * esz);
+  L.off_res = o; o += al(static_cast<size_t>(3 * N) * n * L.ldr);
+  L.total = o;
+  return L;
+}
+
+emu_engine_t resolve(emu_engine_t e) { return e == EMU_ENGINE_AUTO ? EMU_ENGINE_F16 : e; }
+
+emu_status_t get_workspace(DeviceState* ds, size_t need, char** out) {
+  if (ds->user) {
+    if (ds->user_bytes < need) return EMU_ERR_WORKSPACE;
+    *out = static_cast<char*>(ds->user);
+    return EMU_OK;
+  }
+  if (ds->own_bytes < need) {
+    if (ds->own) {
+      cudaFree(ds->own);   // implicitly waits for work that used it
+      ds->own = nullptr;
+      ds->own_bytes = 0;
+    }
+    if (cudaMalloc(&ds->own, need) != cudaSuccess) {
+      cudaGetLastError();
+      return EMU_ERR_ALLOC;
+    }
+    ds->own_bytes = need;
+  }
+  *out = static_cast<char*>(ds->own);
+  return EMU_OK;
+}
+
+// Strides of op(A) rows (i, h) and of op(B) columns seen as rows (j, h).
+void strides_a(emu_op_t ta, int64_t lda, int64_t& rs, int64_t& hs) {
+  if (ta == EMU_OP_N) { rs = 1; hs = lda; } else { rs = lda; hs = 1; }
+}
+void strides_b(emu_op_t tb, int64_t ldb, int64_t& rs, int64_t& hs) {
+  if (tb == EMU_OP_N) { rs = ldb; hs = 1; } else { rs = 1; hs = ldb; }
+}
+
+bool valid_op(emu_op_t t) { return t == EMU_OP_N || t == EMU_OP_T || t == EMU_OP_C; }
+
+emu_status_t check_common(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda,
+                          int64_t ldb, int64_t ldc, int N, bool need_c) {
+  t_bad_param = 0;
+  if (!valid_op(ta)) return bad(1);
+  if (!valid_op(tb)) return bad(2);
+  if (m < 0) return bad(3);
+  if (n < 0) return bad(4);
+  if (k < 0) return bad(5);
+  const int64_t rows_a = ta == EMU_OP_N ? m : k;
+  const int64_t rows_b = tb == EMU_OP_N ? k : n;
+  if (lda < (rows_a > 1 ? rows_a : 1)) return bad(8);
+  if (ldb < (rows_b > 1 ? rows_b : 1)) return bad(10);
+  if (need_c && ldc < (m > 1 ? m : 1)) return bad(13);
+  if (N < EMU_MIN_MODULI || N > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
+  if (k > EMU_MAX_K) return EMU_ERR_K_TOO_LARGE;
+  if (m > (int64_t(1) << 31) || n > (int64_t(1) << 31)) return bad(m > n ? 3 : 4);
+  return EMU_OK;
+}
+
+emu_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA; }
+
+emu_status_t run_residue_gemm(emu_engine_t eng, int64_t m, int64_t n, int64_t kpad, const Plan& pl,
+                              const void* pa, const void* pb, int8_t* res, int64_t ldr,
+                              DeviceState* ds, cudaStream_t st) {
+  if (eng == EMU_ENGINE_I8)
+    return cuda_status(launch_gemm_i8(m, n, kpad, pl, static_cast<const int8_t*>(pa),
+                                      static_cast<const int8_t*>(pb), res, ldr, st));
+  const cudaError_t e = launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, g_chunk_k, ds->status, st);
+  if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
+  return cuda_status(e);
+}
+
+template <bool SINGLE>
+emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
+                  const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
+                  void* C, int64_t ldc, int N, void* stream) {
+  emu_status_t s = check_common(ta, tb, m, n, k, lda, ldb, ldc, N, true);
+  if (s != EMU_OK) return s;
+  if (m == 0 || n == 0) return EMU_OK;
+  if (!C) return bad(12);
+  if (k > 0 && !A) return bad(7);
+  if (k > 0 && !B) return bad(9);
+  DeviceState* ds = nullptr;
+  s = device_init(current_device(), ds);
+  if (s != EMU_OK) return s;
+  const Plan* pl = get_plan(N);
+  const emu_engine_t eng = resolve(g_engine);
+  const bool fp16 = (eng == EMU_ENGINE_F16);
+  const Layout L = layout(m, n, k, N, fp16);
+  char* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    s = get_workspace(ds, L.total, &ws);
+  }
+  if (s != EMU_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int16_t* x = reinterpret_cast<int16_t*>(ws + L.off_x);
+  int16_t* y = reinterpret_cast<int16_t*>(ws + L.off_y);
+  void* scr = ws + L.off_scr;
+  void* pa = ws + L.off_pa;
+  void* pb = ws + L.off_pb;
+  int8_t* res = reinterpret_cast<int8_t*>(ws + L.off_res);
+  int64_t rsa, hsa, rsb, hsb;
+  strides_a(ta, lda, rsa, hsa);
+  strides_b(tb, ldb, rsb, hsb);
+  cudaError_t e;
+  if (k == 0) {
+    // empty inner dimension: the product is zero
+    if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
+    if ((e = cudaMemsetAsync(y, 0, static_cast<size_t>(n) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
+    if ((e = cudaMemsetAsync(res, 0, static_cast<size_t>(3 * N) * n * L.ldr, st)) != cudaSuccess)
+      return EMU_ERR_CUDA;
+  } else {
+    if ((e = launch_exponents(SINGLE, A, m, k, rsa, hsa, *pl, x, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
+    if ((e = launch_exponents(SINGLE, B, n, k, rsb, hsb, *pl, y, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
+    if ((e = launch_split(SINGLE, ta == EMU_OP_C, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st)) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    if ((e = launch_split(SINGLE, tb == EMU_OP_C, B, n, k, rsb, hsb, *pl, y, fp16, L.kpad, pb, st)) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    s = run_residue_gemm(eng, m, n, L.kpad, *pl, pa, pb, res, L.ldr, ds, st);
+    if (s != EMU_OK) return s;
+  }
+  return cuda_status(launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st));
+}
+
+}  // namespace
+
+unsigned int* device_status_ptr() {
+  DeviceState* ds = nullptr;
+  if (device_init(current_device(), ds) != EMU_OK) return nullptr;
+  return ds->status;
+}
+
+__global__ void bounded_wait_kernel(const volatile unsigned int* flag, long long limit,
+                                    unsigned int* status) {
+  const long long t0 = clock64();
+  while (*flag == 0u) {
+    if (clock64() - t0 > limit) {
+      atomicCAS(status, 0u, static_cast<unsigned int>(EMU_ERR_TIMEOUT));
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
+// A flag no code ever sets: the self-test's wait on it can only expire.
+__device__ unsigned int g_never_set = 0u;
+
+cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* status, cudaStream_t st) {
+  void* f = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&f, g_never_set);
+  if (e != cudaSuccess) return e;
+  bounded_wait_kernel<<<1, 1, 0, st>>>(static_cast<const unsigned int*>(f), limit_cycles, status);
+  return cudaGetLastError();
+}
+
+}  // namespace emu
+
+extern "C" {
+
+emu_status_t emu_zgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                       const double* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       const double* beta, void* C, int64_t ldc, int num_moduli, void* stream) {
+  if (!alpha) return emu::bad(6);
+  if (!beta) return emu::bad(11);
+  return emu::gemm<false>(transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0],
+                          beta[1], C, ldc, num_moduli, stream);
+}
+
+emu_status_t emu_cgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                       const float* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       const float* beta, void* C, int64_t ldc, int num_moduli, void* stream) {
+  if (!alpha) return emu::bad(6);
+  if (!beta) return emu::bad(11);
+  return emu::gemm<true>(transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0],
+                         beta[1], C, ldc, num_moduli, stream);
+}
+
+size_t emu_workspace_bytes(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli) {
+  (void)is_single;
+  if (m < 0 || n < 0 || k < 0 || num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return 0;
+  return emu::layout(m, n, k, num_moduli, emu::resolve(emu::g_engine) == EMU_ENGINE_F16).total;
+}
+
+emu_status_t emu_set_workspace(void* ptr, size_t bytes) {
+  emu::DeviceState* ds = nullptr;
+  const int dev = emu::current_device();
+  if (dev < 0 || dev >= emu::kMaxDevices) return EMU_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(emu::g_mu);
+  ds = &emu::g_dev[dev];
+  ds->user = bytes ? ptr : nullptr;
+  ds->user_bytes = ptr ? bytes : 0;
+  return EMU_OK;
+}
+
+emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k) {
+  if (engine != EMU_ENGINE_AUTO && engine != EMU_ENGINE_F16 && engine != EMU_ENGINE_I8) return emu::bad(1);
+  if (chunk_k != 0 && (chunk_k < 64 || chunk_k > 960 || chunk_k % 64)) return emu::bad(2);
+  emu::g_engine = engine;
+  if (chunk_k) emu::g_chunk_k = chunk_k;
+  return EMU_OK;
+}
+
+emu_status_t emu_stage_exponents(int is_single, emu_op_t transa, emu_op_t transb, int64_t m,
+                                 int64_t n, int64_t k, const void* A, int64_t lda, const void* B,
+                                 int64_t ldb, int num_moduli, int16_t* x, int16_t* y, void* stream) {
+  emu_status_t s = emu::check_common(transa, transb, m, n, k, lda, ldb, 1, num_moduli, false);
+  if (s != EMU_OK) return s;
+  emu::DeviceState* ds = nullptr;
+  s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* scr = nullptr;
+  const size_t sb = emu::exponents_scratch_bytes(m > n ? m : n);
+  if (cudaMallocAsync(&scr, sb, st) != cudaSuccess) return EMU_ERR_ALLOC;
+  int64_t rs, hs;
+  cudaError_t e = cudaSuccess;
+  emu::strides_a(transa, lda, rs, hs);
+  if (m > 0) e = emu::launch_exponents(is_single != 0, A, m, k, rs, hs, *pl, x, scr, st);
+  emu::strides_b(transb, ldb, rs, hs);
+  if (e == cudaSuccess && n > 0) e = emu::launch_exponents(is_single != 0, B, n, k, rs, hs, *pl, y, scr, st);
+  cudaFreeAsync(scr, st);
+  return emu::cuda_status(e);
+}
+
+emu_status_t emu_stage_split(int is_single, emu_op_t transa, emu_op_t transb, int64_t m, int64_t n,
+                             int64_t k, const void* A, int64_t lda, const void* B, int64_t ldb,
+                             int num_moduli, const int16_t* x, const int16_t* y, int plane_fp16,
+                             int64_t kpad, void* planesA, void* planesB, void* stream) {
+  emu_status_t s = emu::check_common(transa, transb, m, n, k, lda, ldb, 1, num_moduli, false);
+  if (s != EMU_OK) return s;
+  if (kpad < k || kpad % 64) return emu::bad(15);
+  emu::DeviceState* ds = nullptr;
+  s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int64_t rs, hs;
+  cudaError_t e = cudaSuccess;
+  emu::strides_a(transa, lda, rs, hs);
+  e = emu::launch_split(is_single != 0, transa == EMU_OP_C, A, m, k, rs, hs, *pl, x, plane_fp16 != 0,
+                        kpad, planesA, st);
+  emu::strides_b(transb, ldb, rs, hs);
+  if (e == cudaSuccess)
+    e = emu::launch_split(is_single != 0, transb == EMU_OP_C, B, n, k, rs, hs, *pl, y, plane_fp16 != 0,
+                          kpad, planesB, st);
+  return emu::cuda_status(e);
+}
+
+emu_status_t emu_stage_residue_gemm(emu_engine_t engine, int64_t m, int64_t n, int64_t kpad,
+                                    int num_moduli, const void* planesA, const void* planesB,
+                                    int8_t* residues, int64_t ldr, void* stream) {
+  emu::t_bad_param = 0;
+  if (engine != EMU_ENGINE_AUTO && engine != EMU_ENGINE_F16 && engine != EMU_ENGINE_I8) return emu::bad(1);
+  if (m < 0) return emu::bad(2);
+  if (n < 0) return emu::bad(3);
+  if (kpad < 0 || kpad % 64) return emu::bad(4);
+  if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
+  if (ldr < m || ldr % 16) return emu::bad(9);
+  emu::DeviceState* ds = nullptr;
+  emu_status_t s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  return emu::run_residue_gemm(emu::resolve(engine), m, n, kpad, *pl, planesA, planesB, residues, ldr, ds,
+                               static_cast<cudaStream_t>(stream));
+}
+
+emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli, const int8_t* residues,
+                           int64_t ldr, const int16_t* x, const int16_t* y, const void* alpha,
+                           const void* beta, void* C, int64_t ldc, void* stream) {
+  emu::t_bad_param = 0;
+  if (m < 0) return emu::bad(2);
+  if (n < 0) return emu::bad(3);
+  if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
+  if (ldr < m || ldr % 16) return emu::bad(6);
+  if (!alpha) return emu::bad(9);
+  if (!beta) return emu::bad(10);
+  if (ldc < (m > 1 ? m : 1)) return emu::bad(12);
+  emu::DeviceState* ds = nullptr;
+  emu_status_t s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  double ar, ai, br, bi;
+  if (is_single) {
+    const float* a = static_cast<const float*>(alpha);
+    const float* b = static_cast<const float*>(beta);
+    ar = a[0]; ai = a[1]; br = b[0]; bi = b[1];
+  } else {
+    const double* a = static_cast<const double*>(alpha);
+    const double* b = static_cast<const double*>(beta);
+    ar = a[0]; ai = a[1]; br = b[0]; bi = b[1];
+  }
+  return emu::cuda_status(emu::launch_crt(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi,
+                                          C, ldc, static_cast<cudaStream_t>(stream)));
+}
+
+int emu_last_bad_param(void) { return emu::t_bad_param; }
+
+emu_status_t emu_stream_status(void* stream) {
+  emu::DeviceState* ds = nullptr;
+  emu_status_t s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return EMU_ERR_CUDA;
+  unsigned int v = 0;
+  if (cudaMemcpy(&v, ds->status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return EMU_ERR_CUDA;
+  if (v) {
+    const unsigned int zero = 0;
+    if (cudaMemcpy(ds->status, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+      return EMU_ERR_CUDA;
+  }
+  return static_cast<emu_status_t>(v);
+}
+
+emu_status_t emu_selftest_bounded_wait(int64_t limit_cycles, void* stream) {
+  if (limit_cycles <= 0 || limit_cycles > (int64_t(1) << 36)) return emu::bad(1);
+  emu::DeviceState* ds = nullptr;
+  emu_status_t s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  return emu::cuda_status(
+      emu::launch_bounded_wait_selftest(limit_cycles, ds->status, static_cast<cudaStream_t>(stream)));
+}
+
+const char* emu_version(void) { return "ozaki2-emu 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// K4: CRT reconstruction, inverse scaling and alpha/beta (Algorithm 1 Steps
+// V-iv..VI with the Karatsuba combination of Section III-A).
+//
+// Per output (i, j), from the int8 residues D_l, E_l, F_l of job 3l+c:
+//   E'_R,l = mod(D_l - E_l, p_l),  E'_I,l = mod(F_l - D_l - E_l, p_l)       (eq. karatsuba)
+//   c' = mod(sum_l (P/p_l) q_l E'_l, P)                                     (Steps V-v, V-vi)
+//   C_ij = alpha RN(c' 2^-(x_i + y_j)) + beta C_ij                          (Step VI)
+//
+// The paper evaluates the CRT sum in two double-precision parts and the final
+// reduction in double-double (Section II, eq. CRTaccumulation; Section IV-A).
+// GB300 has 1/62 of its FP32 rate in FP64, so here the CRT is exact integer
+// arithmetic instead: with u_l = E'_l + 128 in [0, 255] and the quotient
+// r = round(sum_l E'_l q_l / p_l) (an fp32 estimate is exact because
+// |c'| <= (P-1)/8 keeps S/P within 1/8 of an integer),
+//   c' = sum_l w_l u_l + (r + R0)(2^(32L) - P) + K   (mod 2^(32L)),
+// accumulated limb by limb in 64-bit registers and carried once.  The result
+// is the exact c', then rounded once to nearest-even binary64 by integer
+// operations (subnormals included).  complex64 output rounds that binary64
+// value (after alpha/beta) once more to binary32.
+//
+// Thread mapping: 4 consecutive rows i of one column j; the residue bytes of
+// those rows are one 32-bit word per job.
+#include "emu_internal.h"
+
+namespace emu {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kRowsPerThread = 4;
+
+__device__ __forceinline__ int sym_small(int v, int p) {   // |v| <= 3 p / 2 + 1
+  if (2 * v >= p) v -= p;
+  if (2 * v >= p) v -= p;
+  if (2 * v < -p) v += p;
+  if (2 * v < -p) v += p;
+  return v;
+}
+
+// Round the L-limb two's-complement integer c (exact c') times 2^e2 to the
+// nearest binary64 (ties to even), by integer operations only.
+template <int L>
+__device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
+  const bool neg = (c[L - 1] >> 31) != 0;
+  if (neg) {   // two's-complement negate
+    uint32_t carry = 1;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const uint64_t v = static_cast<uint64_t>(~c[t]) + carry;
+      c[t] = static_cast<uint32_t>(v);
+      carry = static_cast<uint32_t>(v >> 32);
+    }
+  }
+  int top = -1;
+#pragma unroll
+  for (int t = 0; t < L; ++t)
+    if (c[t]) top = t;
+  if (top < 0) return 0.0;
+  const int b = 32 * top + (31 - __clz(c[top]));          // leading bit index
+  const int lead = b + e2;
+  const int lsb = max(lead - 52, -1074);
+  const int sh = lsb - e2;                                  // bit index of the result LSB
+  uint64_t q;
+  if (sh <= 0) {
+    // |c'| < 2^53: the value fits in limbs 0..1
+    const uint64_t v = static_cast<uint64_t>(c[0]) | (L > 1 ? static_cast<uint64_t>(c[1]) << 32 : 0ull);
+    q = v << (-sh);
+  } else {
+    // q = bits [sh, sh + 53] of c, plus round and sticky bits
+    q = 0;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int pos = 32 * t - sh;                          // where limb t lands in q
+      if (pos >= 64 || pos <= -32) continue;
+      const uint64_t limb = c[t];
+      q |= pos >= 0 ? (limb << pos) : (limb >> (-pos));
+    }
+    const int rb = sh - 1;                                  // round bit index
+    const bool half = (c[rb >> 5] >> (rb & 31)) & 1u;
+    bool sticky = false;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int lo = 32 * t;
+      if (lo >= rb) continue;
+      const int nb = min(32, rb - lo);
+      const uint32_t mask = nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
+      sticky |= (c[t] & mask) != 0u;
+    }
+    if (half && (sticky || (q & 1ull))) ++q;
+  }
+  uint64_t bits = (static_cast<uint64_t>(lsb + 1074) << 52) + q;
+  if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
+  if (neg) bits |= 0x8000000000000000ull;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// Finish one part: add the quotient term, carry once, round.
+template <int L>
+__device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, const Plan& pl, int e2) {
+  const uint32_t rq = static_cast<uint32_t>(static_cast<int>(rintf(est)) + pl.R0);
+  uint32_t c[L];
+  uint64_t carry = 0;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const uint64_t v = acc[t] + static_cast<uint64_t>(rq) * pl.negP[t] + carry;
+    c[t] = static_cast<uint32_t>(v);
+    carry = v >> 32;
+  }
+  return round_limbs<L>(c, e2);
+}
+
+template <int L, bool SINGLE>
+__global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
+                                                       const __grid_constant__ Plan pl,
+                                                       const int8_t* __restrict__ res, int64_t ldr,
+                                                       const int16_t* __restrict__ x,
+                                                       const int16_t* __restrict__ y, double ar,
+                                                       double ai, double br, double bi,
+                                                       void* __restrict__ Cv, int64_t ldc) {
+  const int64_t j = blockIdx.x;
+  const int64_t i0 = (static_cast<int64_t>(blockIdx.y) * kThreads + threadIdx.x) * kRowsPerThread;
+  if (i0 >= m) return;
+  const int N = pl.N;
+  const int64_t job_stride = n * ldr;
+  const int8_t* base = res + j * ldr + i0;
+
+  // exact limb accumulators for the real and imaginary parts of 4 rows
+  uint64_t accR[kRowsPerThread][L], accI[kRowsPerThread][L];
+  float estR[kRowsPerThread], estI[kRowsPerThread];
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    estR[q] = estI[q] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < L; ++t) accR[q][t] = accI[q][t] = pl.K[t];
+  }
+  for (int l = 0; l < N; ++l) {
+    const int p = pl.p[l];
+    const float qp = pl.qp[l];
+    const uint32_t wd = __ldg(reinterpret_cast<const unsigned int*>(base + (3 * l) * job_stride));
+    const uint32_t we = __ldg(reinterpret_cast<const unsigned int*>(base + (3 * l + 1) * job_stride));
+    const uint32_t wf = __ldg(reinterpret_cast<const unsigned int*>(base + (3 * l + 2) * job_stride));
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int d = static_cast<int8_t>(wd >> (8 * q));
+      const int e = static_cast<int8_t>(we >> (8 * q));
+      const int f = static_cast<int8_t>(wf >> (8 * q));
+      const int er = sym_small(d - e, p);          // E'_R,l
+      const int ei = sym_small(f - d - e, p);      // E'_I,l
+      const uint32_t ur = static_cast<uint32_t>(er + 128), ui = static_cast<uint32_t>(ei + 128);
+#pragma unroll
+      for (int t = 0; t < L; ++t) {
+        const uint64_t w = pl.w[l][t];
+        accR[q][t] += ur * w;
+        accI[q][t] += ui * w;
+      }
+      estR[q] = fmaf(static_cast<float>(er), qp, estR[q]);
+      estI[q] = fmaf(static_cast<float>(ei), qp, estI[q]);
+    }
+  }
+  const int yj = y[j];
+  const bool plain = (ar == 1.0 && ai == 0.0 && br == 0.0 && bi == 0.0);
+  const bool use_beta = !(br == 0.0 && bi == 0.0);
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    const int64_t i = i0 + q;
+    if (i >= m) break;
+    const int xi = x[i];
+    double orr, oi;
+    if (xi == kExpNonfinite || yj == kExpNonfinite) {
+      orr = oi = __longlong_as_double(0x7FF8000000000000ll);
+    } else {
+      const int e2 = -(xi + yj);
+      orr = finish<L>(accR[q], estR[q], pl, e2);
+      oi = finish<L>(accI[q], estI[q], pl, e2);
+    }
+    const int64_t ci = j * ldc + i;
+    if (!plain) {
+      double tr = __fma_rn(ar, orr, -__dmul_rn(ai, oi));
+      double ti = __fma_rn(ar, oi, __dmul_rn(ai, orr));
+      if (use_beta) {
+        double cr, cim;
+        if (SINGLE) {
+          const float2 cv = static_cast<const float2*>(Cv)[ci];
+          cr = cv.x;
+          cim = cv.y;
+        } else {
+          const double2 cv = static_cast<const double2*>(Cv)[ci];
+          cr = cv.x;
+          cim = cv.y;
+        }
+        tr = __fma_rn(br, cr, __fma_rn(-bi, cim, tr));
+        ti = __fma_rn(br, cim, __fma_rn(bi, cr, ti));
+      }
+      orr = tr;
+      oi = ti;
+    }
+    if (SINGLE)
+      static_cast<float2*>(Cv)[ci] = make_float2(__double2float_rn(orr), __double2float_rn(oi));
+    else
+      static_cast<double2*>(Cv)[ci] = make_double2(orr, oi);
+  }
+}
+
+template <int L>
+cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
+                     int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
+                     double br, double bi, void* C, int64_t ldc, cudaStream_t st) {
+  const int64_t per_block = static_cast<int64_t>(kThreads) * kRowsPerThread;
+  dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + per_block - 1) / per_block));
+  if (single)
+    crt_kernel<L, true><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  else
+    crt_kernel<L, false><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
+                       int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
+                       double br, double bi, void* C, int64_t ldc, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (ldr % 16 || n > 2147483647LL || (m + 511) / 512 > 65535) return cudaErrorInvalidValue;
+  switch (pl.L) {
+    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace emu

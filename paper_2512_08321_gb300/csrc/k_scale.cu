@@ -1,0 +1,243 @@
+// K1: fast-mode scaling exponents (Section III-B, eqs. mu-fast / nu-fast).
+//
+// For every row r of A-hat (2k real entries Re/Im of one row of op(A)) or
+// column of B-hat:
+//   e_r = max_h ilogb|v_rh|                                   (pass 1)
+//   S_r = sum_h ceil(|v_rh| 2^(15 - e_r))^2   (exact uint64)  (pass 2)
+//   E_r = max{E : 4^E max(2^32, S_r) <= (P-1) 2^27}           (finalize)
+//   x_r = E_r - e_r  (int16), or EMU_EXP_NONFINITE if the row holds Inf/NaN.
+// This is the paper's floor(P'_fast - max(1, log2 ||t_r||)) - e_r with
+// P'_fast = log2(P-1)/2 - 1.5, decided exactly on the integer upper bound S_r
+// of ||t_r||^2 2^30 (t = v 2^-e) instead of through __log2f; the sums are
+// order independent, so the exponents are deterministic.
+//
+// Element (r, h) of the source is X[r*rs + h*hs] (complex, in elements);
+// either rs == 1 (rows contiguous: one thread per row, coalesced along r) or
+// hs == 1 (entries of a row contiguous: one warp per row).
+#include "emu_internal.h"
+
+namespace emu {
+namespace {
+
+constexpr int kChunkH = 512;      // h handled by one block in the row-contiguous form
+constexpr int kThreads = 256;
+
+template <bool SINGLE>
+struct Bits;
+template <>
+struct Bits<false> {
+  using U = unsigned long long;
+  using V = double2;
+  static constexpr int kMant = 52, kExpMask = 0x7FF, kBias = 1023, kMinLsb = -1074;
+  __device__ static U re(const V& v) { return __double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull; }
+  __device__ static U im(const V& v) { return __double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull; }
+};
+template <>
+struct Bits<true> {
+  using U = unsigned int;
+  using V = float2;
+  static constexpr int kMant = 23, kExpMask = 0xFF, kBias = 127, kMinLsb = -149;
+  __device__ static U re(const V& v) { return __float_as_uint(v.x) & 0x7FFFFFFFu; }
+  __device__ static U im(const V& v) { return __float_as_uint(v.y) & 0x7FFFFFFFu; }
+};
+
+// magnitude bits u (sign cleared): nonfinite?
+template <bool S>
+__device__ __forceinline__ bool nonfinite(typename Bits<S>::U u) {
+  return static_cast<int>(u >> Bits<S>::kMant) == Bits<S>::kExpMask;
+}
+
+// ilogb of a finite nonzero magnitude, offset by +2048 (0 means "no entry")
+template <bool S>
+__device__ __forceinline__ int ilogb_off(typename Bits<S>::U u) {
+  const int ex = static_cast<int>(u >> Bits<S>::kMant);
+  if (ex) return ex - Bits<S>::kBias + 2048;
+  // subnormal: u is the integer significand, value u * 2^kMinLsb
+  const int lead = S ? (31 - __clz(static_cast<unsigned int>(u)))
+                     : (63 - __clzll(static_cast<unsigned long long>(u)));
+  return lead + Bits<S>::kMinLsb + 2048;
+}
+
+// ceil(|v| 2^(15 - e)) for a finite magnitude u (0 -> 0)
+template <bool S>
+__device__ __forceinline__ unsigned long long ceil_q(typename Bits<S>::U u, int e) {
+  if (u == 0) return 0ull;
+  const int ex = static_cast<int>(u >> Bits<S>::kMant);
+  unsigned long long m;
+  int elsb;
+  if (ex) {
+    m = (static_cast<unsigned long long>(u) & ((1ull << Bits<S>::kMant) - 1)) |
+        (1ull << Bits<S>::kMant);
+    elsb = ex - Bits<S>::kBias - Bits<S>::kMant;
+  } else {
+    m = static_cast<unsigned long long>(u);
+    elsb = Bits<S>::kMinLsb;
+  }
+  const int s = e - kSumFracBits - elsb;   // value = m 2^-s
+  if (s <= 0) return m << (-s);
+  if (s >= 64) return 1ull;
+  const unsigned long long q = m >> s;
+  return q + ((m & ((1ull << s) - 1)) != 0ull ? 1ull : 0ull);
+}
+
+__device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long long S) {
+  const unsigned long long M = S > (1ull << 32) ? S : (1ull << 32);
+  const int bm = 64 - __clzll(M);
+  const int bx = pl.sX + (64 - __clzll(pl.Xtop));
+  auto fits = [&](int E) -> bool {
+    const int sh = 2 * E - pl.sX;
+    if (sh >= 64) return false;
+    if (sh >= 0) return M <= (pl.Xtop >> sh);
+    if (-sh >= 64) return true;
+    const unsigned __int128 lhs = static_cast<unsigned __int128>(pl.Xtop) << (-sh);
+    return static_cast<unsigned __int128>(M) <= lhs;
+  };
+  const int d = bx - bm;
+  int E = d >= 0 ? d / 2 : -((-d + 1) / 2);
+  while (!fits(E)) --E;
+  while (fits(E + 1)) ++E;
+  return E;
+}
+
+// ---- pass 1: max exponent and non-finite flag
+template <bool S, bool ROWS_CONTIG>
+__global__ void __launch_bounds__(kThreads) exp_max_kernel(const typename Bits<S>::V* __restrict__ X,
+                                                           int64_t rows, int64_t k, int64_t rs,
+                                                           int64_t hs, int* __restrict__ emax,
+                                                           unsigned int* __restrict__ flag) {
+  using B = Bits<S>;
+  int best = 0;
+  bool bad = false;
+  int64_t r;
+  if (ROWS_CONTIG) {
+    r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    if (r >= rows) return;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h1 = min(k, h0 + kChunkH);
+    for (int64_t h = h0; h < h1; ++h) {
+      const typename B::V v = X[r + h * hs];
+      const typename B::U a = B::re(v), b = B::im(v);
+      bad |= nonfinite<S>(a) | nonfinite<S>(b);
+      if (a && !nonfinite<S>(a)) best = max(best, ilogb_off<S>(a));
+      if (b && !nonfinite<S>(b)) best = max(best, ilogb_off<S>(b));
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    r = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h1 = min(k, h0 + kChunkH);
+    for (int64_t h = h0 + lane; h < h1; h += 32) {
+      const typename B::V v = X[r * rs + h];
+      const typename B::U a = B::re(v), b = B::im(v);
+      bad |= nonfinite<S>(a) | nonfinite<S>(b);
+      if (a && !nonfinite<S>(a)) best = max(best, ilogb_off<S>(a));
+      if (b && !nonfinite<S>(b)) best = max(best, ilogb_off<S>(b));
+    }
+    for (int o = 16; o; o >>= 1) {
+      best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+      bad |= __shfl_xor_sync(0xffffffffu, static_cast<int>(bad), o) != 0;
+    }
+    if (lane) return;
+  }
+  if (best) atomicMax(emax + r, best);
+  if (bad) atomicOr(flag + r, 1u);
+}
+
+// ---- pass 2: exact quantised sum of squares
+template <bool S, bool ROWS_CONTIG>
+__global__ void __launch_bounds__(kThreads) exp_sum_kernel(const typename Bits<S>::V* __restrict__ X,
+                                                           int64_t rows, int64_t k, int64_t rs,
+                                                           int64_t hs, const int* __restrict__ emax,
+                                                           const unsigned int* __restrict__ flag,
+                                                           unsigned long long* __restrict__ sum) {
+  using B = Bits<S>;
+  unsigned long long acc = 0;
+  int64_t r;
+  if (ROWS_CONTIG) {
+    r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    if (r >= rows || flag[r] || emax[r] == 0) return;
+    const int e = emax[r] - 2048;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h1 = min(k, h0 + kChunkH);
+    for (int64_t h = h0; h < h1; ++h) {
+      const typename B::V v = X[r + h * hs];
+      const unsigned long long a = ceil_q<S>(B::re(v), e), b = ceil_q<S>(B::im(v), e);
+      acc += a * a + b * b;
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    r = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+    if (r >= rows || flag[r] || emax[r] == 0) return;
+    const int e = emax[r] - 2048;
+    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h1 = min(k, h0 + kChunkH);
+    for (int64_t h = h0 + lane; h < h1; h += 32) {
+      const typename B::V v = X[r * rs + h];
+      const unsigned long long a = ceil_q<S>(B::re(v), e), b = ceil_q<S>(B::im(v), e);
+      acc += a * a + b * b;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane) return;
+  }
+  if (acc) atomicAdd(sum + r, acc);
+}
+
+__global__ void exp_finalize_kernel(int64_t rows, const int* __restrict__ emax,
+                                    const unsigned int* __restrict__ flag,
+                                    const unsigned long long* __restrict__ sum,
+                                    const __grid_constant__ Plan pl, int16_t* __restrict__ xout) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  if (flag[r]) {
+    xout[r] = kExpNonfinite;
+    return;
+  }
+  const int e = emax[r] ? emax[r] - 2048 : 0;
+  const int E = exponent_from_sum(pl, sum[r]);
+  xout[r] = static_cast<int16_t>(E - e);
+}
+
+template <bool S>
+cudaError_t launch_t(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_t hs,
+                     const Plan& pl, int16_t* xout, void* scratch, cudaStream_t st) {
+  using V = typename Bits<S>::V;
+  const V* X = static_cast<const V*>(Xv);
+  int* emax = static_cast<int*>(scratch);
+  unsigned int* flag = reinterpret_cast<unsigned int*>(emax + round_up(rows, 64));
+  unsigned long long* sum = reinterpret_cast<unsigned long long*>(flag + round_up(rows, 64));
+  cudaError_t err = cudaMemsetAsync(scratch, 0, exponents_scratch_bytes(rows), st);
+  if (err != cudaSuccess) return err;
+  const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
+  if (ychunks > 0) {
+    const bool rows_contig = (rs == 1);
+    if (rows_contig) {
+      dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
+      exp_max_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
+      exp_sum_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
+    } else {
+      dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
+      exp_max_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
+      exp_sum_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
+    }
+  }
+  exp_finalize_kernel<<<static_cast<unsigned int>((rows + 255) / 256), 256, 0, st>>>(
+      rows, emax, flag, sum, pl, xout);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t exponents_scratch_bytes(int64_t rows) {
+  return static_cast<size_t>(round_up(rows, 64)) * (4 + 4 + 8);
+}
+
+cudaError_t launch_exponents(bool single, const void* X, int64_t rows, int64_t k, int64_t rs,
+                             int64_t hs, const Plan& pl, int16_t* xout, void* scratch,
+                             cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  return single ? launch_t<true>(X, rows, k, rs, hs, pl, xout, scratch, st)
+                : launch_t<false>(X, rows, k, rs, hs, pl, xout, scratch, st);
+}
+
+}  // namespace emu

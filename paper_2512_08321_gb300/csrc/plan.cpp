@@ -1,0 +1,245 @@
+// Host-side plan: Algorithm 1 Steps I-II and the constants of the exact CRT.
+//
+// Step I   moduli p_l <= 256, pairwise coprime.  The paper does not list them;
+//          this library takes the greedy descending set (keep c = 256, 255,
+//          ... when coprime to all kept so far).
+// Step II  q_l = (P/p_l)^-1 mod p_l, CRT weights w_l = (P/p_l) q_l, so that
+//          sum_l w_l E'_l == A'B' (mod P) (Section II).
+// The CRT is evaluated exactly in L 32-bit limbs modulo 2^(32L) > 8|c'|:
+//   c' = sum_l w_l u_l + r' (2^(32L) - P) + K,  u_l = E'_l + 128,
+//   r' = r + R0 with r = round(S/P) and K = R0 P - 128 sum_l w_l.
+#include <cstring>
+#include <mutex>
+
+#include "emu_internal.h"
+
+namespace emu {
+namespace {
+
+constexpr int kBigLimbs = 8;  // 256-bit scratch integers
+
+struct Big {
+  uint32_t v[kBigLimbs];
+  Big() { std::memset(v, 0, sizeof(v)); }
+  explicit Big(uint64_t x) : Big() {
+    v[0] = static_cast<uint32_t>(x);
+    v[1] = static_cast<uint32_t>(x >> 32);
+  }
+};
+
+void mul_small(Big& a, uint32_t s) {
+  uint64_t carry = 0;
+  for (int i = 0; i < kBigLimbs; ++i) {
+    uint64_t t = static_cast<uint64_t>(a.v[i]) * s + carry;
+    a.v[i] = static_cast<uint32_t>(t);
+    carry = t >> 32;
+  }
+}
+
+uint32_t divmod_small(Big& a, uint32_t s) {  // a /= s, returns a mod s
+  uint64_t rem = 0;
+  for (int i = kBigLimbs - 1; i >= 0; --i) {
+    uint64_t cur = (rem << 32) | a.v[i];
+    a.v[i] = static_cast<uint32_t>(cur / s);
+    rem = cur % s;
+  }
+  return static_cast<uint32_t>(rem);
+}
+
+void add(Big& a, const Big& b) {
+  uint64_t carry = 0;
+  for (int i = 0; i < kBigLimbs; ++i) {
+    uint64_t t = static_cast<uint64_t>(a.v[i]) + b.v[i] + carry;
+    a.v[i] = static_cast<uint32_t>(t);
+    carry = t >> 32;
+  }
+}
+
+void sub(Big& a, const Big& b) {  // modulo 2^256
+  int64_t borrow = 0;
+  for (int i = 0; i < kBigLimbs; ++i) {
+    int64_t t = static_cast<int64_t>(a.v[i]) - b.v[i] - borrow;
+    borrow = t < 0 ? 1 : 0;
+    a.v[i] = static_cast<uint32_t>(t);
+  }
+}
+
+int bitlen(const Big& a) {
+  for (int i = kBigLimbs - 1; i >= 0; --i)
+    if (a.v[i]) return 32 * i + (32 - __builtin_clz(a.v[i]));
+  return 0;
+}
+
+void shl(Big& a, int s) {
+  Big r;
+  int w = s / 32, b = s % 32;
+  for (int i = kBigLimbs - 1; i >= 0; --i) {
+    if (i - w < 0) continue;
+    uint64_t x = static_cast<uint64_t>(a.v[i - w]) << b;
+    if (b && i - w - 1 >= 0) x |= a.v[i - w - 1] >> (32 - b);
+    r.v[i] = static_cast<uint32_t>(x);
+  }
+  a = r;
+}
+
+uint64_t extract64(const Big& a, int s) {  // floor(a / 2^s) truncated to 64 bits
+  uint64_t r = 0;
+  for (int bit = 63; bit >= 0; --bit) {
+    int pos = s + bit;
+    if (pos < 32 * kBigLimbs && ((a.v[pos / 32] >> (pos % 32)) & 1u)) r |= (1ull << bit);
+  }
+  return r;
+}
+
+int gcd_int(int a, int b) {
+  while (b) {
+    int t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+void build(int N, Plan& pl) {
+  std::memset(&pl, 0, sizeof(pl));
+  pl.N = N;
+  // Step I: greedy descending pairwise-coprime moduli
+  int count = 0;
+  for (int c = 256; c >= 2 && count < N; --c) {
+    bool ok = true;
+    for (int i = 0; i < count; ++i)
+      if (gcd_int(c, pl.p[i]) != 1) ok = false;
+    if (ok) pl.p[count++] = c;
+  }
+  Big P(1);
+  for (int l = 0; l < N; ++l) mul_small(P, static_cast<uint32_t>(pl.p[l]));
+  const int bitsP = bitlen(P);
+  pl.L = (bitsP + 1 + 31) / 32;
+  // Step II and the CRT weights
+  Big sumw;
+  for (int l = 0; l < N; ++l) {
+    const uint32_t p = static_cast<uint32_t>(pl.p[l]);
+    Big M = P;
+    divmod_small(M, p);                        // M = P / p_l exactly
+    Big Mc = M;
+    const uint32_t mmod = divmod_small(Mc, p);  // (P/p_l) mod p_l
+    uint32_t q = 0;
+    for (uint32_t t = 1; t < p; ++t)            // inverse by exhaustive search
+      if ((mmod * t) % p == 1u) {
+        q = t;
+        break;
+      }
+    Big w = M;
+    mul_small(w, q);
+    for (int t = 0; t < kMaxLimbs; ++t) pl.w[l][t] = t < pl.L ? w.v[t] : 0u;
+    add(sumw, w);
+    pl.qp[l] = static_cast<float>(static_cast<double>(q) / static_cast<double>(p));
+    pl.barrett[l] = static_cast<uint32_t>((1ull << 32) / p);
+    pl.two32[l] = static_cast<uint32_t>((1ull << 32) % p);
+    uint32_t v = 1 % p;
+    for (int s = 0; s < kPow2Table; ++s) {
+      pl.pow2[l][s] = static_cast<uint8_t>(v);
+      v = (v * 2u) % p;
+    }
+  }
+  // negP = 2^(32L) - P, K = R0 P - 128 sum w (mod 2^(32L))
+  Big zero;
+  Big negP = zero;
+  sub(negP, P);
+  pl.R0 = 128 * N;
+  Big K = P;
+  mul_small(K, static_cast<uint32_t>(pl.R0));
+  Big w128 = sumw;
+  mul_small(w128, 128u);
+  sub(K, w128);
+  for (int t = 0; t < kMaxLimbs; ++t) {
+    pl.negP[t] = t < pl.L ? negP.v[t] : 0u;
+    pl.K[t] = t < pl.L ? K.v[t] : 0u;
+  }
+  // X = (P - 1) 2^27 for the fast-mode exponent rule
+  Big X = P;
+  sub(X, Big(1));
+  shl(X, 27);
+  const int bx = bitlen(X);
+  pl.sX = bx > 63 ? bx - 63 : 0;
+  pl.Xtop = extract64(X, pl.sX);
+}
+
+std::mutex g_mu;
+Plan g_plans[kMaxModuli + 1];
+bool g_built[kMaxModuli + 1] = {};
+
+}  // namespace
+
+const Plan* get_plan(int N) {
+  if (N < EMU_MIN_MODULI || N > EMU_MAX_MODULI) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_built[N]) {
+    build(N, g_plans[N]);
+    g_built[N] = true;
+  }
+  return &g_plans[N];
+}
+
+// Largest E with 4^E * max(2^32, S) <= X, X = (P-1) 2^27 = Xtop 2^sX + rest.
+// Shared by host queries; the device copy lives in k_scale.cu.
+int plan_exponent(const Plan& pl, uint64_t S) {
+  const uint64_t M = S > (1ull << 32) ? S : (1ull << 32);
+  const int bm = 64 - __builtin_clzll(M);
+  const int bx = pl.sX + (64 - __builtin_clzll(pl.Xtop));
+  auto fits = [&](int E) -> bool {
+    const int sh = 2 * E - pl.sX;            // floor(X / 4^E) = floor(Xtop * 2^-sh)
+    if (sh >= 64) return false;
+    if (sh >= 0) return M <= (pl.Xtop >> sh);
+    if (-sh >= 64) return true;
+    const unsigned __int128 lhs = static_cast<unsigned __int128>(pl.Xtop) << (-sh);
+    return static_cast<unsigned __int128>(M) <= lhs;
+  };
+  int d = bx - bm;
+  int E = d >= 0 ? d / 2 : -((-d + 1) / 2);   // floor(d / 2)
+  while (!fits(E)) --E;
+  while (fits(E + 1)) ++E;
+  return E;
+}
+
+}  // namespace emu
+
+extern "C" {
+
+emu_status_t emu_plan_info(int num_moduli, int32_t* moduli, int32_t* q, uint32_t* p_limbs,
+                           int32_t* crt_limbs) {
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  if (!pl) return EMU_ERR_MODULI_RANGE;
+  emu::Big P(1);
+  for (int l = 0; l < pl->N; ++l) {
+    if (moduli) moduli[l] = pl->p[l];
+    emu::mul_small(P, static_cast<uint32_t>(pl->p[l]));
+  }
+  if (q) {
+    for (int l = 0; l < pl->N; ++l) {
+      emu::Big M = P;
+      emu::divmod_small(M, static_cast<uint32_t>(pl->p[l]));
+      emu::Big Mc = M;
+      const uint32_t mmod = emu::divmod_small(Mc, static_cast<uint32_t>(pl->p[l]));
+      int32_t qq = 0;
+      for (int t = 1; t < pl->p[l]; ++t)
+        if ((mmod * static_cast<uint32_t>(t)) % static_cast<uint32_t>(pl->p[l]) == 1u) {
+          qq = t;
+          break;
+        }
+      q[l] = qq;
+    }
+  }
+  if (p_limbs)
+    for (int t = 0; t < 8; ++t) p_limbs[t] = P.v[t];
+  if (crt_limbs) *crt_limbs = pl->L;
+  return EMU_OK;
+}
+
+int emu_plan_exponent(int num_moduli, uint64_t S) {
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  if (!pl) return -100000;
+  return emu::plan_exponent(*pl, S);
+}
+
+}  // extern "C"

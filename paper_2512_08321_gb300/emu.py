@@ -1,0 +1,209 @@
+"""Thin ctypes binding of the C ABI in include/ozaki2_emu.h.
+
+Argument marshalling only: every step of the emulation runs in the CUDA
+library.  The functions keep the C names; device buffers are passed as
+integer addresses (``tensor.data_ptr()``) and streams as ``cudaStream_t``
+handles (``torch.cuda.current_stream().cuda_stream``).  There is no CPU
+fallback: loading fails loudly when the library has not been built.
+"""
+import ctypes
+import os
+
+import torch  # loads the CUDA runtime the library links against
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libozaki2emu.so")
+
+EMU_OK = 0
+EMU_ERR_INVALID_ARG = 1
+EMU_ERR_K_TOO_LARGE = 2
+EMU_ERR_MODULI_RANGE = 3
+EMU_ERR_ALLOC = 4
+EMU_ERR_CUDA = 5
+EMU_ERR_TIMEOUT = 6
+EMU_ERR_UNSUPPORTED = 7
+EMU_ERR_WORKSPACE = 8
+STATUS_NAMES = {0: "EMU_OK", 1: "EMU_ERR_INVALID_ARG", 2: "EMU_ERR_K_TOO_LARGE",
+                3: "EMU_ERR_MODULI_RANGE", 4: "EMU_ERR_ALLOC", 5: "EMU_ERR_CUDA",
+                6: "EMU_ERR_TIMEOUT", 7: "EMU_ERR_UNSUPPORTED", 8: "EMU_ERR_WORKSPACE"}
+
+OPS = {"N": 0, "T": 1, "C": 2}
+EMU_ENGINE_AUTO, EMU_ENGINE_F16, EMU_ENGINE_I8 = 0, 1, 2
+EMU_EXP_NONFINITE = -32768
+EMU_MIN_MODULI, EMU_MAX_MODULI = 2, 24
+
+_c_i64 = ctypes.c_int64
+_c_ptr = ctypes.c_void_p
+_c_int = ctypes.c_int
+
+# (name, restype, argtypes) of every exported function
+_SIGS = [
+    ("emu_zgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_double),
+                           _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_double), _c_ptr,
+                           _c_i64, _c_int, _c_ptr]),
+    ("emu_cgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
+                           _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
+                           _c_i64, _c_int, _c_ptr]),
+    ("emu_workspace_bytes", ctypes.c_size_t, [_c_int, _c_i64, _c_i64, _c_i64, _c_int]),
+    ("emu_set_workspace", _c_int, [_c_ptr, ctypes.c_size_t]),
+    ("emu_set_engine", _c_int, [_c_int, _c_int]),
+    ("emu_stage_exponents", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
+                                     _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_ptr]),
+    ("emu_stage_split", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
+                                 _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_int, _c_i64, _c_ptr,
+                                 _c_ptr, _c_ptr]),
+    ("emu_stage_residue_gemm", _c_int, [_c_int, _c_i64, _c_i64, _c_i64, _c_int, _c_ptr, _c_ptr,
+                                        _c_ptr, _c_i64, _c_ptr]),
+    ("emu_stage_crt", _c_int, [_c_int, _c_i64, _c_i64, _c_int, _c_ptr, _c_i64, _c_ptr, _c_ptr,
+                               _c_ptr, _c_ptr, _c_ptr, _c_i64, _c_ptr]),
+    ("emu_plan_info", _c_int, [_c_int, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32)]),
+    ("emu_plan_exponent", _c_int, [_c_int, ctypes.c_uint64]),
+    ("emu_last_bad_param", _c_int, []),
+    ("emu_stream_status", _c_int, [_c_ptr]),
+    ("emu_selftest_bounded_wait", _c_int, [_c_i64, _c_ptr]),
+    ("emu_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+class EmuError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        bp = lib().emu_last_bad_param() if status == EMU_ERR_INVALID_ARG else 0
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}" + (f" (argument {bp})" if bp else ""))
+
+
+def check(status, where):
+    if status != EMU_OK:
+        raise EmuError(status, where)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _op(op):
+    return OPS[op.upper()] if isinstance(op, str) else int(op)
+
+
+# ------------------------------------------------------------ C-named calls
+def emu_zgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a = (ctypes.c_double * 2)(float(alpha.real), float(alpha.imag))
+    b = (ctypes.c_double * 2)(float(beta.real), float(beta.imag))
+    return lib().emu_zgemm(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc,
+                           num_moduli, _stream(stream))
+
+
+def emu_cgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a = (ctypes.c_float * 2)(float(alpha.real), float(alpha.imag))
+    b = (ctypes.c_float * 2)(float(beta.real), float(beta.imag))
+    return lib().emu_cgemm(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc,
+                           num_moduli, _stream(stream))
+
+
+def emu_workspace_bytes(is_single, m, n, k, num_moduli):
+    return lib().emu_workspace_bytes(int(is_single), m, n, k, num_moduli)
+
+
+def emu_set_workspace(ptr, nbytes):
+    return lib().emu_set_workspace(ptr, nbytes)
+
+
+def emu_set_engine(engine, chunk_k=0):
+    return lib().emu_set_engine(int(engine), int(chunk_k))
+
+
+def emu_stage_exponents(is_single, transa, transb, m, n, k, A, lda, B, ldb, num_moduli, x, y, stream=None):
+    return lib().emu_stage_exponents(int(is_single), _op(transa), _op(transb), m, n, k, A, lda, B, ldb,
+                                     num_moduli, x, y, _stream(stream))
+
+
+def emu_stage_split(is_single, transa, transb, m, n, k, A, lda, B, ldb, num_moduli, x, y, plane_fp16,
+                    kpad, planesA, planesB, stream=None):
+    return lib().emu_stage_split(int(is_single), _op(transa), _op(transb), m, n, k, A, lda, B, ldb,
+                                 num_moduli, x, y, int(plane_fp16), kpad, planesA, planesB, _stream(stream))
+
+
+def emu_stage_residue_gemm(engine, m, n, kpad, num_moduli, planesA, planesB, residues, ldr, stream=None):
+    return lib().emu_stage_residue_gemm(int(engine), m, n, kpad, num_moduli, planesA, planesB, residues,
+                                        ldr, _stream(stream))
+
+
+def emu_stage_crt(is_single, m, n, num_moduli, residues, ldr, x, y, alpha, beta, C, ldc, stream=None):
+    T = ctypes.c_float if is_single else ctypes.c_double
+    a = (T * 2)(float(alpha.real), float(alpha.imag))
+    b = (T * 2)(float(beta.real), float(beta.imag))
+    return lib().emu_stage_crt(int(is_single), m, n, num_moduli, residues, ldr, x, y,
+                               ctypes.cast(a, _c_ptr), ctypes.cast(b, _c_ptr), C, ldc, _stream(stream))
+
+
+def emu_plan_info(num_moduli):
+    """(status, moduli, q, P as int, crt limb count) computed by the library."""
+    mod = (ctypes.c_int32 * EMU_MAX_MODULI)()
+    q = (ctypes.c_int32 * EMU_MAX_MODULI)()
+    limbs = (ctypes.c_uint32 * 8)()
+    L = ctypes.c_int32()
+    st = lib().emu_plan_info(num_moduli, mod, q, limbs, ctypes.byref(L))
+    P = sum(int(limbs[t]) << (32 * t) for t in range(8))
+    return st, list(mod[:num_moduli]), list(q[:num_moduli]), P, L.value
+
+
+def emu_plan_exponent(num_moduli, S):
+    return lib().emu_plan_exponent(num_moduli, int(S))
+
+
+def emu_last_bad_param():
+    return lib().emu_last_bad_param()
+
+
+def emu_stream_status(stream=None):
+    return lib().emu_stream_status(_stream(stream))
+
+
+def emu_selftest_bounded_wait(limit_cycles, stream=None):
+    return lib().emu_selftest_bounded_wait(int(limit_cycles), _stream(stream))
+
+
+def emu_version():
+    return lib().emu_version().decode()
+
+
+# ------------------------------------------------- torch tensor conveniences
+def gemm(A_store, B_store, C_store, m, n, k, num_moduli, transa="N", transb="N",
+         alpha=1.0, beta=0.0, lda=None, ldb=None, ldc=None, stream=None):
+    """Emulated GEMM on column-major matrices held as C-contiguous (cols x ld)
+    torch tensors (complex128 -> ZGEMM, complex64 -> CGEMM).  Raises on error."""
+    single = A_store.dtype == torch.complex64
+    lda = lda if lda is not None else A_store.shape[-1]
+    ldb = ldb if ldb is not None else B_store.shape[-1]
+    ldc = ldc if ldc is not None else C_store.shape[-1]
+    f = emu_cgemm if single else emu_zgemm
+    st = f(transa, transb, m, n, k, complex(alpha), A_store.data_ptr(), lda, B_store.data_ptr(), ldb,
+           complex(beta), C_store.data_ptr(), ldc, num_moduli, stream)
+    return check(st, "emu_cgemm" if single else "emu_zgemm")

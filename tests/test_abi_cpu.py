@@ -1,0 +1,100 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares; the
+host-side plan and argument checks agree with the oracle.  No GPU needed:
+nothing here launches device work."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.moduli import Plan
+from oracle.scaling import exponent_E
+from paper_2512_08321_gb300 import emu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(emu_[a-z0-9_]+)\s*\(", txt):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(emu.LIB_PATH):
+        from paper_2512_08321_gb300.build import build
+        build()
+    return emu.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    decl = declared_functions()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(L, name), name
+    assert decl == set(emu.exported_names())
+
+
+def test_version(L):
+    assert "sm_103a" in emu.emu_version()
+
+
+@pytest.mark.parametrize("N", [2, 3, 6, 9, 14, 16, 17, 20, 24])
+def test_plan_matches_oracle(L, N):
+    st, mod, q, P, limbs = emu.emu_plan_info(N)
+    ref = Plan(N)
+    assert st == emu.EMU_OK
+    assert mod == ref.p and q == ref.q and P == ref.P
+    assert 2 ** (32 * limbs - 1) > ref.P // 8            # c' fits the two's-complement limbs
+
+
+@pytest.mark.parametrize("N", [2, 5, 8, 14, 20, 24])
+def test_plan_exponent_matches_oracle(L, N):
+    P = Plan(N).P
+    rng = np.random.default_rng(N)
+    Ss = [0, 1, 2 ** 32 - 1, 2 ** 32, 2 ** 32 + 1, 2 ** 50, 2 ** 50 - 1, 3 * 2 ** 40]
+    Ss += [int(v) for v in rng.integers(0, 2 ** 50, 200)]
+    for S in Ss:
+        assert emu.emu_plan_exponent(N, S) == exponent_E(S, P), S
+
+
+def test_plan_range(L):
+    assert emu.emu_plan_info(1)[0] == emu.EMU_ERR_MODULI_RANGE
+    assert emu.emu_plan_info(25)[0] == emu.EMU_ERR_MODULI_RANGE
+
+
+def test_argument_checks_before_device_work(L):
+    # rejected synchronously, before any CUDA call
+    Z = 0
+    st = emu.emu_zgemm("N", "N", -1, 4, 4, 1.0, Z, 4, Z, 4, 0.0, Z, 4, 14, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 3
+    st = emu.emu_zgemm("N", "N", 4, 4, 4, 1.0, Z, 3, Z, 4, 0.0, Z, 4, 14, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 8
+    st = emu.emu_zgemm("T", "N", 4, 4, 5, 1.0, Z, 4, Z, 5, 0.0, Z, 4, 14, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 8
+    st = emu.emu_cgemm("N", "C", 4, 6, 4, 1.0, Z, 4, Z, 5, 0.0, Z, 4, 8, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 10
+    st = emu.emu_zgemm("N", "N", 4, 4, 4, 1.0, Z, 4, Z, 4, 0.0, Z, 3, 14, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 13
+    assert emu.emu_zgemm("N", "N", 4, 4, 4, 1.0, Z, 4, Z, 4, 0.0, Z, 4, 1, 0) == emu.EMU_ERR_MODULI_RANGE
+    assert emu.emu_zgemm("N", "N", 4, 4, 4, 1.0, Z, 4, Z, 4, 0.0, Z, 4, 25, 0) == emu.EMU_ERR_MODULI_RANGE
+    k = 2 ** 17 + 1
+    assert emu.emu_zgemm("N", "N", 4, 4, k, 1.0, Z, 4, Z, k, 0.0, Z, 4, 14, 0) == emu.EMU_ERR_K_TOO_LARGE
+    assert emu.emu_zgemm(7, "N", 4, 4, 4, 1.0, Z, 4, Z, 4, 0.0, Z, 4, 14, 0) == emu.EMU_ERR_INVALID_ARG
+    assert emu.emu_last_bad_param() == 1
+    # quick return: empty output touches nothing
+    assert emu.emu_zgemm("N", "N", 0, 4, 4, 1.0, Z, 1, Z, 4, 0.0, Z, 1, 14, 0) == emu.EMU_OK
+    assert emu.emu_set_engine(1, 100) == emu.EMU_ERR_INVALID_ARG
+    assert emu.emu_set_engine(9, 0) == emu.EMU_ERR_INVALID_ARG
+
+
+def test_workspace_query(L):
+    b14 = emu.emu_workspace_bytes(0, 1000, 900, 700, 14)
+    b16 = emu.emu_workspace_bytes(0, 1000, 900, 700, 16)
+    assert 0 < b14 < b16
+    assert emu.emu_workspace_bytes(0, -1, 900, 700, 14) == 0
