@@ -1,4 +1,5 @@
 // C ABI entry points: argument checks, workspace, the four phases in order.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -27,6 +28,13 @@ struct DeviceState {
 
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
+std::atomic<uint64_t> g_launches{0};
+cudaEvent_t g_phase_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+bool g_phase_on = false;
+
+void phase(int i, cudaStream_t st) {
+  if (g_phase_on) cudaEventRecord(g_phase_ev[i], st);
+}
 emu_engine_t g_engine = EMU_ENGINE_AUTO;
 int g_chunk_k = 512;
 
@@ -180,6 +188,7 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
   strides_a(ta, lda, rsa, hsa);
   strides_b(tb, ldb, rsb, hsb);
   cudaError_t e;
+  phase(0, st);
   if (k == 0) {
     // empty inner dimension: the product is zero
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
@@ -189,17 +198,24 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
   } else {
     if ((e = launch_exponents(SINGLE, A, m, k, rsa, hsa, *pl, x, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = launch_exponents(SINGLE, B, n, k, rsb, hsb, *pl, y, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
+    phase(1, st);
     if ((e = launch_split(SINGLE, ta == EMU_OP_C, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st)) != cudaSuccess)
       return EMU_ERR_CUDA;
     if ((e = launch_split(SINGLE, tb == EMU_OP_C, B, n, k, rsb, hsb, *pl, y, fp16, L.kpad, pb, st)) != cudaSuccess)
       return EMU_ERR_CUDA;
+    phase(2, st);
     s = run_residue_gemm(eng, m, n, L.kpad, *pl, pa, pb, res, L.ldr, ds, st);
     if (s != EMU_OK) return s;
+    phase(3, st);
   }
-  return cuda_status(launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st));
+  s = cuda_status(launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st));
+  phase(4, st);
+  return s;
 }
 
 }  // namespace
+
+void count_launches(int n) { g_launches.fetch_add(static_cast<uint64_t>(n), std::memory_order_relaxed); }
 
 unsigned int* device_status_ptr() {
   DeviceState* ds = nullptr;
@@ -227,6 +243,7 @@ cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* sta
   cudaError_t e = cudaGetSymbolAddress(&f, g_never_set);
   if (e != cudaSuccess) return e;
   bounded_wait_kernel<<<1, 1, 0, st>>>(static_cast<const unsigned int*>(f), limit_cycles, status);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -397,6 +414,22 @@ emu_status_t emu_selftest_bounded_wait(int64_t limit_cycles, void* stream) {
   return emu::cuda_status(
       emu::launch_bounded_wait_selftest(limit_cycles, ds->status, static_cast<cudaStream_t>(stream)));
 }
+
+emu_status_t emu_set_phase_events(void* const* events, int count) {
+  if (count == 0) {
+    emu::g_phase_on = false;
+    return EMU_OK;
+  }
+  if (count != 5 || !events) return emu::bad(2);
+  for (int i = 0; i < 5; ++i) {
+    if (!events[i]) return emu::bad(1);
+    emu::g_phase_ev[i] = static_cast<cudaEvent_t>(events[i]);
+  }
+  emu::g_phase_on = true;
+  return EMU_OK;
+}
+
+uint64_t emu_kernel_launches(void) { return emu::g_launches.load(); }
 
 const char* emu_version(void) { return "ozaki2-emu 0.1 (sm_103a)"; }
 

@@ -67,6 +67,9 @@ cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
 cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* status,
                                          cudaStream_t st);
 
+// Launch accounting (api.cu): launchers report each kernel they enqueue.
+void count_launches(int n);
+
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace emu

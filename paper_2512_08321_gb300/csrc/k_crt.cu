@@ -210,6 +210,7 @@ cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const in
     crt_kernel<L, true><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   else
     crt_kernel<L, false><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -477,6 +477,7 @@ cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, 
   const long long grid = s.units < g_sms ? s.units : g_sms;
   gemm_f16_kernel<<<static_cast<unsigned int>(grid), kThreads, kSmemBytes, st>>>(mapA, mapB, pl, s, m, n, res, ldr,
                                                                                  status);
+  count_launches(1);
   return cudaGetLastError();
 }
 

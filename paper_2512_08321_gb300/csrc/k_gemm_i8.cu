@@ -162,6 +162,7 @@ cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
   dim3 grid(static_cast<unsigned int>((m + BM - 1) / BM), static_cast<unsigned int>((n + BN - 1) / BN),
             static_cast<unsigned int>(3 * pl.N));
   gemm_i8_kernel<<<grid, kThreads, 0, st>>>(m, n, kpad, pl, planesA, planesB, res, ldr);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -215,14 +215,17 @@ cudaError_t launch_t(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_
       dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
       exp_max_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
       exp_sum_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
+      count_launches(2);
     } else {
       dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
       exp_max_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
       exp_sum_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
+      count_launches(2);
     }
   }
   exp_finalize_kernel<<<static_cast<unsigned int>((rows + 255) / 256), 256, 0, st>>>(
       rows, emax, flag, sum, pl, xout);
+  count_launches(1);
   return cudaGetLastError();
 }
 

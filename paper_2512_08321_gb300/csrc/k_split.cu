@@ -224,6 +224,7 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
   else
     split_kernel<SINGLE, false, T><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl,
                                                               kpad, static_cast<T*>(planes));
+  count_launches(1);
   return cudaGetLastError();
 }
 

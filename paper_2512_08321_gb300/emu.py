@@ -62,6 +62,8 @@ _SIGS = [
     ("emu_last_bad_param", _c_int, []),
     ("emu_stream_status", _c_int, [_c_ptr]),
     ("emu_selftest_bounded_wait", _c_int, [_c_i64, _c_ptr]),
+    ("emu_set_phase_events", _c_int, [ctypes.POINTER(_c_ptr), _c_int]),
+    ("emu_kernel_launches", ctypes.c_uint64, []),
     ("emu_version", ctypes.c_char_p, []),
 ]
 
@@ -188,6 +190,21 @@ def emu_stream_status(stream=None):
 
 def emu_selftest_bounded_wait(limit_cycles, stream=None):
     return lib().emu_selftest_bounded_wait(int(limit_cycles), _stream(stream))
+
+
+def emu_set_phase_events(events):
+    """events: five torch.cuda.Event(enable_timing=True), or None to stop."""
+    if not events:
+        return lib().emu_set_phase_events(None, 0)
+    for e in events:
+        if not e.cuda_event:        # torch creates the CUDA event on first record
+            e.record()
+    arr = (_c_ptr * 5)(*[e.cuda_event for e in events])
+    return lib().emu_set_phase_events(arr, 5)
+
+
+def emu_kernel_launches():
+    return lib().emu_kernel_launches()
 
 
 def emu_version():

@@ -32,3 +32,22 @@ def log_uniform_shapes(count, lo, hi, seed):
     rng = np.random.Generator(np.random.Philox(seed))
     v = np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=(count, 3)))
     return np.clip(np.floor(v).astype(np.int64), lo, hi)
+
+
+def paper_matrix_device(rows, cols, phi, seed, dtype, device="cuda"):
+    """Same distribution as paper_matrix, drawn on the GPU (torch Philox).
+
+    Returns the column-major rows x cols matrix as a C-contiguous
+    (cols x rows) torch tensor, i.e. leading dimension `rows`.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    single = dtype in (np.complex64, "complex64", torch.complex64)
+    real_t = torch.float32 if single else torch.float64
+    parts = []
+    for _ in range(2):
+        u = 1.0 - torch.rand((cols, rows), generator=g, device=device, dtype=real_t)
+        n = torch.randn((cols, rows), generator=g, device=device, dtype=real_t)
+        parts.append((u - 0.5) * torch.exp(n * phi))
+    return torch.complex(parts[0], parts[1])
