@@ -53,7 +53,8 @@ typedef enum {
   EMU_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
   EMU_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
   EMU_ERR_UNSUPPORTED = 7,   /* no GPU / not an sm_103 device / feature not built */
-  EMU_ERR_WORKSPACE = 8      /* caller workspace smaller than emu_workspace_bytes() */
+  EMU_ERR_WORKSPACE = 8,     /* caller workspace smaller than emu_workspace_bytes() */
+  EMU_ERR_SIZE_LIMIT = 9     /* m or n above EMU_STATIC_EXP_MAX_ROWS (allocation-free entry point) */
 } emu_status_t;
 
 typedef enum { EMU_OP_N = 0, EMU_OP_T = 1, EMU_OP_C = 2 } emu_op_t;
@@ -146,6 +147,32 @@ emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli,
                            const void* alpha, const void* beta,
                            void* C, int64_t ldc, void* stream);
 
+/* Allocation-free variant of emu_stage_exponents (the paper has no counterpart:
+ * this is a service to callers that cannot let the library allocate).
+ * Callers whose device memory belongs to their own pool or caching allocator,
+ * or that cannot accept the device-wide synchronisation of cudaMalloc/cudaFree,
+ * get the same x and y as emu_stage_exponents, with the per-row scratch (16
+ * bytes a row) taken from a fixed device array compiled into the library
+ * instead of memory allocated per call.  Nothing is allocated: no cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * - m and n are limited to EMU_STATIC_EXP_MAX_ROWS; larger sizes return
+ *   EMU_ERR_SIZE_LIMIT before any GPU work.  Other arguments as in
+ *   emu_stage_exponents.
+ * - The array (1 MiB) stays resident on every GPU that loads the library
+ *   until the process exits.
+ * - The first call made with a device current looks up the array's device
+ *   address (cudaGetSymbolAddress) for that device; make that first call
+ *   before any stream capture.
+ * - Every call on a device shares the one array, which keeps the last call's
+ *   contents; each call clears the part it uses before using it.  Calls that
+ *   can overlap on the GPU (different streams, no ordering between them)
+ *   race on the array and must not be issued that way. */
+#define EMU_STATIC_EXP_MAX_ROWS 65536
+emu_status_t emu_stage_exponents_static(int is_single, emu_op_t transa, emu_op_t transb,
+                                        int64_t m, int64_t n, int64_t k,
+                                        const void* A, int64_t lda, const void* B, int64_t ldb,
+                                        int num_moduli, int16_t* x, int16_t* y, void* stream);
+
 /* ------------------------------------------------------ host-side queries -- */
 
 /* Algorithm 1 Steps I-II as computed by the library: the N moduli (greedy
@@ -173,6 +200,16 @@ emu_status_t emu_stream_status(void* stream);
  * expires and records EMU_ERR_TIMEOUT in the status word.  Exercises the
  * bounded-wait path without faulting or hanging the GPU. */
 emu_status_t emu_selftest_bounded_wait(int64_t limit_cycles, void* stream);
+
+/* Phase timing: when set, every following emu_zgemm/emu_cgemm records
+ * events[0..4] (cudaEvent_t passed as void*) on its stream at the start of
+ * the call and after the exponent, split, residue-product and CRT phases.
+ * count must be 5, or 0 with events NULL to stop.  The caller owns the events.
+ * Host state of the calling process, not per thread. */
+emu_status_t emu_set_phase_events(void* const* events, int count);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t emu_kernel_launches(void);
 
 /* Library version string (static storage). */
 const char* emu_version(void);

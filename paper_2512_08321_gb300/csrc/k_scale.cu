@@ -14,6 +14,8 @@
 // Element (r, h) of the source is X[r*rs + h*hs] (complex, in elements);
 // either rs == 1 (rows contiguous: one thread per row, coalesced along r) or
 // hs == 1 (entries of a row contiguous: one warp per row).
+#include <mutex>
+
 #include "emu_internal.h"
 
 namespace emu {
@@ -244,3 +246,77 @@ cudaError_t launch_exponents(bool single, const void* X, int64_t rows, int64_t k
 }
 
 }  // namespace emu
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the exponent phase.
+//
+// Some callers cannot let a library allocate device memory: applications whose
+// device memory is owned by their own pool or caching allocator (a cudaMalloc
+// from inside the library can fail, or fragment that pool, at a point the
+// caller does not control), and latency-sensitive callers that cannot afford
+// the implicit device-wide synchronisation of cudaMalloc/cudaFree.  For them,
+// emu_stage_exponents_static computes the same per-row/per-column scaling
+// exponents as emu_stage_exponents, but its per-row scratch (max exponent,
+// non-finite flag, quantised sum: 16 bytes a row) lives in the fixed device
+// array below instead of memory allocated per call.  The array holds up to
+// kStaticExpMaxRows rows (1 MiB) and stays resident on every GPU that loads
+// this library until the process exits.
+namespace {
+
+constexpr int64_t kStaticExpMaxRows = EMU_STATIC_EXP_MAX_ROWS;
+constexpr int kStaticMaxDevices = 64;
+
+// host code sees only a stand-in symbol: its device address comes from
+// cudaGetSymbolAddress, taken once per device in static_scratch() below
+static __device__ __align__(256) unsigned char g_exp_scratch[kStaticExpMaxRows * 16];
+
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of g_exp_scratch on the current device; looked up on the
+// first call made with that device current.
+cudaError_t static_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_exp_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" emu_status_t emu_stage_exponents_static(int is_single, emu_op_t transa, emu_op_t transb,
+                                                   int64_t m, int64_t n, int64_t k, const void* A,
+                                                   int64_t lda, const void* B, int64_t ldb, int num_moduli,
+                                                   int16_t* x, int16_t* y, void* stream) {
+  const bool ok_ops = (transa == EMU_OP_N || transa == EMU_OP_T || transa == EMU_OP_C) &&
+                      (transb == EMU_OP_N || transb == EMU_OP_T || transb == EMU_OP_C);
+  if (!ok_ops || m < 0 || n < 0 || k < 0) return EMU_ERR_INVALID_ARG;
+  const int64_t rows_a = transa == EMU_OP_N ? m : k;
+  const int64_t rows_b = transb == EMU_OP_N ? k : n;
+  if (lda < (rows_a > 1 ? rows_a : 1) || ldb < (rows_b > 1 ? rows_b : 1)) return EMU_ERR_INVALID_ARG;
+  if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
+  if (k > EMU_MAX_K) return EMU_ERR_K_TOO_LARGE;
+  if (m > kStaticExpMaxRows || n > kStaticExpMaxRows) return EMU_ERR_SIZE_LIMIT;
+  if ((m > 0 && !x) || (n > 0 && !y) || (k > 0 && ((m > 0 && !A) || (n > 0 && !B)))) return EMU_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  if (static_scratch(&scratch) != cudaSuccess) return EMU_ERR_CUDA;
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // op(A) rows (i, h) and op(B) columns (j, h): strides as in the allocating entry point
+  const int64_t rsa = transa == EMU_OP_N ? 1 : lda, hsa = transa == EMU_OP_N ? lda : 1;
+  const int64_t rsb = transb == EMU_OP_N ? ldb : 1, hsb = transb == EMU_OP_N ? 1 : ldb;
+  // launch_exponents clears the part of the scratch it uses before each pass
+  cudaError_t e = cudaSuccess;
+  if (m > 0) e = emu::launch_exponents(is_single != 0, A, m, k, rsa, hsa, *pl, x, scratch, st);
+  if (e == cudaSuccess && n > 0) e = emu::launch_exponents(is_single != 0, B, n, k, rsb, hsb, *pl, y, scratch, st);
+  return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA;
+}

@@ -23,9 +23,12 @@ EMU_ERR_CUDA = 5
 EMU_ERR_TIMEOUT = 6
 EMU_ERR_UNSUPPORTED = 7
 EMU_ERR_WORKSPACE = 8
+EMU_ERR_SIZE_LIMIT = 9
 STATUS_NAMES = {0: "EMU_OK", 1: "EMU_ERR_INVALID_ARG", 2: "EMU_ERR_K_TOO_LARGE",
                 3: "EMU_ERR_MODULI_RANGE", 4: "EMU_ERR_ALLOC", 5: "EMU_ERR_CUDA",
-                6: "EMU_ERR_TIMEOUT", 7: "EMU_ERR_UNSUPPORTED", 8: "EMU_ERR_WORKSPACE"}
+                6: "EMU_ERR_TIMEOUT", 7: "EMU_ERR_UNSUPPORTED", 8: "EMU_ERR_WORKSPACE",
+                9: "EMU_ERR_SIZE_LIMIT"}
+EMU_STATIC_EXP_MAX_ROWS = 65536
 
 OPS = {"N": 0, "T": 1, "C": 2}
 EMU_ENGINE_AUTO, EMU_ENGINE_F16, EMU_ENGINE_I8 = 0, 1, 2
@@ -49,6 +52,8 @@ _SIGS = [
     ("emu_set_engine", _c_int, [_c_int, _c_int]),
     ("emu_stage_exponents", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
                                      _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_ptr]),
+    ("emu_stage_exponents_static", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
+                                            _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_ptr]),
     ("emu_stage_split", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
                                  _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_int, _c_i64, _c_ptr,
                                  _c_ptr, _c_ptr]),
@@ -144,6 +149,13 @@ def emu_set_engine(engine, chunk_k=0):
 def emu_stage_exponents(is_single, transa, transb, m, n, k, A, lda, B, ldb, num_moduli, x, y, stream=None):
     return lib().emu_stage_exponents(int(is_single), _op(transa), _op(transb), m, n, k, A, lda, B, ldb,
                                      num_moduli, x, y, _stream(stream))
+
+
+def emu_stage_exponents_static(is_single, transa, transb, m, n, k, A, lda, B, ldb, num_moduli, x, y,
+                               stream=None):
+    """Allocation-free exponent phase (fixed scratch inside the library)."""
+    return lib().emu_stage_exponents_static(int(is_single), _op(transa), _op(transb), m, n, k, A, lda, B, ldb,
+                                            num_moduli, x, y, _stream(stream))
 
 
 def emu_stage_split(is_single, transa, transb, m, n, k, A, lda, B, ldb, num_moduli, x, y, plane_fp16,
