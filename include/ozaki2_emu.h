@@ -90,6 +90,55 @@ emu_status_t emu_cgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
                        const void* B, int64_t ldb, const float* beta,
                        void* C, int64_t ldc, int num_moduli, void* stream);
 
+/* --------------------------------------------------------- grouped GEMMs ---
+ * Many complex GEMMs of uneven shapes on one moduli count.  Every phase of
+ * the method (Algorithm 1 Steps III-VI, Karatsuba of Section III-A) runs as
+ * ONE persistent launch over all problems; the sequence is captured once in
+ * a CUDA graph.  Problem i: C_i = alpha_i op(A_i) op(B_i) + beta_i C_i with the
+ * per-problem arguments of emu_zgemm taken from the arrays (host arrays of
+ * length count; alpha and beta hold 2*count doubles {re, im}, also for
+ * complex64).  Problems with m_i = 0 or n_i = 0 are skipped.  The results are
+ * bit-identical to count separate emu_zgemm/emu_cgemm calls. */
+typedef struct emu_grouped_s* emu_grouped_t;
+
+/* Build a grouped plan: workspace (cudaMalloc, owned by the plan), device
+ * descriptor tables and the CUDA graph.  tile_n: rows of op(A) per tile of the
+ * residue-product launch (64, 128 or 256), or 0 to let the autotuner time the
+ * three on this problem set (the choice is remembered per problem-set
+ * signature, and kept in the file named by EMU_AUTOTUNE_CACHE if set).
+ * Synchronous; returns EMU_ERR_INVALID_ARG / EMU_ERR_K_TOO_LARGE /
+ * EMU_ERR_MODULI_RANGE as emu_zgemm would for any problem. */
+emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa, const emu_op_t* transb,
+                                const int64_t* m, const int64_t* n, const int64_t* k, const double* alpha,
+                                const void* const* A, const int64_t* lda, const void* const* B,
+                                const int64_t* ldb, const double* beta, void* const* C, const int64_t* ldc,
+                                int num_moduli, int tile_n, emu_grouped_t* plan);
+/* Replay the plan's graph on `stream` (asynchronous).  The matrices are read
+ * and written at the addresses given at creation. */
+emu_status_t emu_grouped_run(emu_grouped_t plan, void* stream);
+/* Tile width the plan uses, and the number of kernels one replay launches. */
+int emu_grouped_tile(emu_grouped_t plan);
+int emu_grouped_kernels(emu_grouped_t plan);
+/* Diagnostic: run the plan's four phases once on `stream` outside the graph,
+ * with events between them, synchronise, and store the milliseconds of the
+ * exponent, split, residue-product and CRT launches in ms[0..3]. */
+emu_status_t emu_grouped_phase_times(emu_grouped_t plan, float* ms, void* stream);
+/* Free the plan (waits for its work to finish). */
+emu_status_t emu_grouped_destroy(emu_grouped_t plan);
+
+/* One-shot grouped ZGEMM / CGEMM: create (autotuned), run on `stream`,
+ * synchronise, destroy. */
+emu_status_t emu_zgemm_grouped(int count, const emu_op_t* transa, const emu_op_t* transb,
+                               const int64_t* m, const int64_t* n, const int64_t* k, const double* alpha,
+                               const void* const* A, const int64_t* lda, const void* const* B,
+                               const int64_t* ldb, const double* beta, void* const* C, const int64_t* ldc,
+                               int num_moduli, void* stream);
+emu_status_t emu_cgemm_grouped(int count, const emu_op_t* transa, const emu_op_t* transb,
+                               const int64_t* m, const int64_t* n, const int64_t* k, const double* alpha,
+                               const void* const* A, const int64_t* lda, const void* const* B,
+                               const int64_t* ldb, const double* beta, void* const* C, const int64_t* ldc,
+                               int num_moduli, void* stream);
+
 /* ------------------------------------------------------------ workspace --- */
 
 /* Bytes of device workspace one call of the given shape needs (is_single: 0

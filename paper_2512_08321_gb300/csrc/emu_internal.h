@@ -13,6 +13,8 @@ namespace emu {
 constexpr int kMaxModuli = EMU_MAX_MODULI;
 constexpr int kMaxLimbs = 6;        // 32-bit limbs of the CRT accumulator (P < 2^191)
 constexpr int kPow2Table = 128;     // 2^s mod p for s in [0, 128)
+constexpr int kChunkBits = 13;      // residue split: a' in signed 13-bit chunks
+constexpr int kMaxChunks = 8;       // 8 x 13 = 104 bits > every |a'| (< 2^97)
 constexpr int kSumFracBits = 15;    // row sums use ceil(|t| 2^15), Section III-B reading
 constexpr int16_t kExpNonfinite = EMU_EXP_NONFINITE;
 
@@ -32,6 +34,9 @@ struct Plan {
   uint32_t negP[kMaxLimbs];               // 2^(32L) - P
   uint32_t K[kMaxLimbs];                  // R0*P - 128*sum_l w_l  (mod 2^(32L))
   uint8_t pow2[kMaxModuli][kPow2Table];   // 2^s mod p_l
+  int nchunk;                             // 13-bit chunks covering every |a'| (< 2^(Emax+1))
+  float w13[kMaxModuli][kMaxChunks];      // 2^(13 t) mod p_l, symmetric, as float
+  float inv_p[kMaxModuli];                // 1 / p_l rounded to float
 };
 
 // Host: build (and cache) the plan of N moduli; nullptr when N is out of range.
@@ -66,6 +71,63 @@ cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
 
 cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* status,
                                          cudaStream_t st);
+
+// ------------------------------------------------------------- grouped launches
+// A segment is the rows of op(A) (or the columns of op(B)) of one problem of a
+// grouped call; a block of a grouped launch finds its segment by binary search
+// on block_begin.
+struct ExpSeg {
+  const void* X;
+  int64_t rows, k, rs, hs;
+  int16_t* xout;
+  int* emax;
+  unsigned int* flag;
+  unsigned long long* sum;
+  long long block_begin;     // first block of this segment in the flattened grid
+  int hchunks;               // blocks along h per row block
+  int rows_contig;
+};
+struct SplitSeg {
+  const void* X;
+  int64_t rows, k, rs, hs;
+  const int16_t* xexp;
+  void* planes;
+  int64_t kpad;
+  long long block_begin;
+  int htiles;
+  int conj;
+  int rows_contig;
+};
+struct CrtProb {
+  const int8_t* res;
+  int64_t ldr, m, n, ldc;
+  const int16_t* x;
+  const int16_t* y;
+  void* C;
+  double ar, ai, br, bi;
+  long long block_begin;
+  int iblocks;
+};
+// block counts of one segment/problem in the grouped launches
+long long exp_seg_blocks(ExpSeg& s);       // sets hchunks, rows_contig; returns blocks
+long long split_seg_blocks(SplitSeg& s);   // sets htiles, rows_contig
+long long crt_prob_blocks(CrtProb& c);     // sets iblocks
+cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, int nseg, long long blocks,
+                                     const long long* row_begin_dev, long long total_rows, const Plan& pl,
+                                     cudaStream_t st);
+cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_dev, int nseg, long long blocks,
+                                 const Plan& pl, cudaStream_t st);
+cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob, long long blocks, const Plan& pl,
+                               cudaStream_t st);
+size_t group_problem_bytes();
+bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, const void* planesA,
+                        const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,
+                        long long* unit_begin);
+cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long total_units, const Plan& pl,
+                                    int tile_n, unsigned int* status, cudaStream_t st);
+cudaError_t prepare_gemm_f16();
+extern int g_f16_group;
+extern int g_f16_tile_n;
 
 // Launch accounting (api.cu): launchers report each kernel they enqueue.
 void count_launches(int n);

@@ -109,15 +109,11 @@ __device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, co
 }
 
 template <int L, bool SINGLE>
-__global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
-                                                       const __grid_constant__ Plan pl,
-                                                       const int8_t* __restrict__ res, int64_t ldr,
-                                                       const int16_t* __restrict__ x,
-                                                       const int16_t* __restrict__ y, double ar,
-                                                       double ai, double br, double bi,
-                                                       void* __restrict__ Cv, int64_t ldc) {
-  const int64_t j = blockIdx.x;
-  const int64_t i0 = (static_cast<int64_t>(blockIdx.y) * kThreads + threadIdx.x) * kRowsPerThread;
+__device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
+                                          int64_t ldr, const int16_t* __restrict__ x, const int16_t* __restrict__ y,
+                                          double ar, double ai, double br, double bi, void* __restrict__ Cv,
+                                          int64_t ldc, int64_t j, int64_t iblock) {
+  const int64_t i0 = (iblock * kThreads + threadIdx.x) * kRowsPerThread;
   if (i0 >= m) return;
   const int N = pl.N;
   const int64_t job_stride = n * ldr;
@@ -132,12 +128,18 @@ __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
 #pragma unroll
     for (int t = 0; t < L; ++t) accR[q][t] = accI[q][t] = pl.K[t];
   }
+  auto word = [&](int q) { return __ldg(reinterpret_cast<const unsigned int*>(base + q * job_stride)); };
+  // the residue words of modulus l+1 are loaded while modulus l is processed
+  uint32_t nd = word(0), ne = word(1), nf = word(2);
   for (int l = 0; l < N; ++l) {
     const int p = pl.p[l];
     const float qp = pl.qp[l];
-    const uint32_t wd = __ldg(reinterpret_cast<const unsigned int*>(base + (3 * l) * job_stride));
-    const uint32_t we = __ldg(reinterpret_cast<const unsigned int*>(base + (3 * l + 1) * job_stride));
-    const uint32_t wf = __ldg(reinterpret_cast<const unsigned int*>(base + (3 * l + 2) * job_stride));
+    const uint32_t wd = nd, we = ne, wf = nf;
+    if (l + 1 < N) {
+      nd = word(3 * l + 3);
+      ne = word(3 * l + 4);
+      nf = word(3 * l + 5);
+    }
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int d = static_cast<int8_t>(wd >> (8 * q));
@@ -200,6 +202,34 @@ __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
   }
 }
 
+
+template <int L, bool SINGLE>
+__global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
+                                                       const __grid_constant__ Plan pl,
+                                                       const int8_t* __restrict__ res, int64_t ldr,
+                                                       const int16_t* __restrict__ x,
+                                                       const int16_t* __restrict__ y, double ar,
+                                                       double ai, double br, double bi,
+                                                       void* __restrict__ Cv, int64_t ldc) {
+  crt_block<L, SINGLE>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, Cv, ldc, blockIdx.x, blockIdx.y);
+}
+
+// one launch over every problem of a grouped call: blocks are (column, row block) of each problem
+template <int L, bool SINGLE>
+__global__ void __launch_bounds__(kThreads) crt_grouped(const CrtProb* __restrict__ probs, int nprob,
+                                                        const __grid_constant__ Plan pl) {
+  int lo = 0, hi = nprob - 1;
+  const long long b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  const CrtProb& c = probs[lo];
+  const long long local = b - c.block_begin;
+  crt_block<L, SINGLE>(c.m, c.n, pl, c.res, c.ldr, c.x, c.y, c.ar, c.ai, c.br, c.bi, c.C, c.ldc,
+                       local / c.iblocks, local % c.iblocks);
+}
+
 template <int L>
 cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                      int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
@@ -214,7 +244,37 @@ cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const in
   return cudaGetLastError();
 }
 
+template <int L>
+cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long long blocks, const Plan& pl,
+                             cudaStream_t st) {
+  const unsigned int gb = static_cast<unsigned int>(blocks);
+  if (single) crt_grouped<L, true><<<gb, kThreads, 0, st>>>(probs, nprob, pl);
+  else crt_grouped<L, false><<<gb, kThreads, 0, st>>>(probs, nprob, pl);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+long long crt_prob_blocks(CrtProb& c) {
+  const int64_t per_block = static_cast<int64_t>(kThreads) * kRowsPerThread;
+  c.iblocks = static_cast<int>((c.m + per_block - 1) / per_block);
+  return static_cast<long long>(c.n) * c.iblocks;
+}
+
+cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob, long long blocks, const Plan& pl,
+                               cudaStream_t st) {
+  if (nprob <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  switch (pl.L) {
+    case 2: return launch_grouped_l<2>(single, probs_dev, nprob, blocks, pl, st);
+    case 3: return launch_grouped_l<3>(single, probs_dev, nprob, blocks, pl, st);
+    case 4: return launch_grouped_l<4>(single, probs_dev, nprob, blocks, pl, st);
+    case 5: return launch_grouped_l<5>(single, probs_dev, nprob, blocks, pl, st);
+    case 6: return launch_grouped_l<6>(single, probs_dev, nprob, blocks, pl, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                        int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,

@@ -29,6 +29,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "emu_internal.h"
@@ -37,18 +38,28 @@ namespace emu {
 namespace {
 
 constexpr int BM = 128;                 // MMA M: output columns per tile
-constexpr int BN = 256;                 // MMA N: output rows per tile
 constexpr int BK = 64;                  // k per stage (128 bytes of fp16)
 constexpr int UK = 16;                  // k per tcgen05.mma kind::f16
 constexpr int kStages = 4;
 constexpr int kStageA = BM * BK * 2;    // 16 KB: MMA operand A (B planes)
-constexpr int kStageB = BN * BK * 2;    // 32 KB: MMA operand B (A planes)
-constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kTmemCols = 512;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 constexpr long long kWaitLimit = 1ll << 32;    // SM cycles (about 2 s) per wait
+
+// Tile width BN (MMA N: output rows per tile) is a template parameter:
+// 256 for large problems, 128 or 64 for small ones.
+template <int BN>
+struct Cfg {
+  static constexpr int kStageB = BN * BK * 2;                 // MMA operand B (A planes)
+  static constexpr int kStageBytes = kStageA + kStageB;
+  static constexpr int kTmemCols = 2 * BN;                    // two accumulator slots
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  // kind::f16 instruction descriptor: fp16 A/B, fp32 D, both K-major, M = BM, N = BN
+  static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) |
+                                     (static_cast<uint32_t>(BN >> 3) << 17) |
+                                     (static_cast<uint32_t>(BM >> 4) << 24);
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+};
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -117,17 +128,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// kind::f16 instruction descriptor: fp16 A/B, fp32 D, both K-major, M x N.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (static_cast<uint32_t>(BN >> 3) << 17) |
-                            (static_cast<uint32_t>(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, bool accumulate) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        bool accumulate) {
   const uint32_t acc = accumulate ? 1u : 0u;
   asm volatile(
       "{\n.reg .pred p;\n"
       "setp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
@@ -160,43 +168,117 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ schedule
+// One work unit: a BM x BN output tile of one problem and a pair of jobs
+// (jb < 0 when the job count is odd and this is the last pair).
+struct Unit {
+  int ja, jb, tj, ti;
+  int nkb, ck, nch;                 // k-blocks, k-blocks per chunk, chunks
+  const CUtensorMap* mapA;          // B planes of the problem (MMA operand A)
+  const CUtensorMap* mapB;          // A planes of the problem (MMA operand B)
+  int8_t* res;
+  int64_t ldr, n;
+};
+
+// Tile order inside one problem: column tiles in groups of `group`,
+// column-fastest inside a group, so concurrently running CTAs share operands in L2.
+__device__ __forceinline__ void tile_coords(int t, int TJ, int TI, int group, int& tj, int& ti) {
+  const int per_group = group * TI;
+  const int g = t / per_group;
+  const int first = g * group;
+  const int gsz = min(group, TJ - first);
+  const int r = t - g * per_group;
+  tj = first + r % gsz;
+  ti = r / gsz;
+}
+
 struct Sched {
   int J;          // jobs = 3N
   int pairs;      // ceil(J / 2)
   int TJ, TI;     // tiles along output columns (BM) and rows (BN)
   int tiles;
-  int group;      // tile rasterisation: groups of `group` column tiles
+  int group;      // tile rasterisation
   int nkb;        // k-blocks
   int ck;         // k-blocks per chunk
   int nch;        // chunks
   long long units;
 };
 
-__device__ __forceinline__ void unit_coords(const Sched& s, long long u, int& ja, int& jb, int& tj, int& ti) {
-  const int pair = static_cast<int>(u / s.tiles);
-  const int t = static_cast<int>(u % s.tiles);
-  ja = 2 * pair;
-  jb = (2 * pair + 1 < s.J) ? 2 * pair + 1 : -1;
-  // column tiles in groups of s.group; inside a group, column-fastest
-  const int per_group = s.group * s.TI;
-  const int g = t / per_group;
-  const int first = g * s.group;
-  const int gsz = min(s.group, s.TJ - first);
-  const int r = t - g * per_group;
-  tj = first + r % gsz;
-  ti = r / gsz;
-}
+// one GEMM: tensor maps are kernel parameters
+struct SingleWork {
+  const CUtensorMap* mapA;
+  const CUtensorMap* mapB;
+  Sched s;
+  int8_t* res;
+  int64_t ldr, n;
+  __device__ long long units() const { return s.units; }
+  __device__ Unit get(long long u) const {
+    Unit w;
+    const int pair = static_cast<int>(u / s.tiles);
+    const int t = static_cast<int>(u % s.tiles);
+    w.ja = 2 * pair;
+    w.jb = (2 * pair + 1 < s.J) ? 2 * pair + 1 : -1;
+    tile_coords(t, s.TJ, s.TI, s.group, w.tj, w.ti);
+    w.nkb = s.nkb;
+    w.ck = s.ck;
+    w.nch = s.nch;
+    w.mapA = mapA;
+    w.mapB = mapB;
+    w.res = res;
+    w.ldr = ldr;
+    w.n = n;
+    return w;
+  }
+};
 
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_f16_kernel(const __grid_constant__ CUtensorMap mapA,   // B planes: MMA operand A
-                    const __grid_constant__ CUtensorMap mapB,   // A planes: MMA operand B
-                    const __grid_constant__ Plan pl, const Sched s, int64_t m, int64_t n,
-                    int8_t* __restrict__ res, int64_t ldr, unsigned int* status) {
+// many GEMMs sharing N: per-problem descriptors (with their tensor maps) in global memory
+struct GroupProblem {  // CUtensorMap members give it 64-byte alignment
+  CUtensorMap mapA;
+  CUtensorMap mapB;
+  int8_t* res;
+  int64_t ldr, n;
+  long long unit_begin;             // first unit of this problem
+  int TJ, TI, tiles, group, nkb, ck, nch, J;
+};
+
+struct GroupWork {
+  const GroupProblem* probs;
+  int count;
+  long long total;
+  __device__ long long units() const { return total; }
+  __device__ Unit get(long long u) const {
+    int lo = 0, hi = count - 1;       // last problem with unit_begin <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+    }
+    const GroupProblem& P = probs[lo];
+    const long long v = u - P.unit_begin;
+    Unit w;
+    const int pair = static_cast<int>(v / P.tiles);
+    const int t = static_cast<int>(v % P.tiles);
+    w.ja = 2 * pair;
+    w.jb = (2 * pair + 1 < P.J) ? 2 * pair + 1 : -1;
+    tile_coords(t, P.TJ, P.TI, P.group, w.tj, w.ti);
+    w.nkb = P.nkb;
+    w.ck = P.ck;
+    w.nch = P.nch;
+    w.mapA = &P.mapA;
+    w.mapB = &P.mapB;
+    w.res = P.res;
+    w.ldr = P.ldr;
+    w.n = P.n;
+    return w;
+  }
+};
+
+template <int BN, class Work>
+__device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigned int* status, bool fence_maps) {
+  using C = Cfg<BN>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;                 // 1024-aligned operand stages
   uint8_t* gbase = smem_raw + (base - raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kStages * kStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kStages * C::kStageBytes);
   // barrier layout: full[S], empty[S], tfull[2], tempty[2], done
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int i) { return bar0 + 8u * i; };
@@ -209,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Ctl ctl{status, abort_s};
+  const long long nunits = W.units();
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
@@ -225,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols));
+                 "r"(C::kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   tc_fence_before();
@@ -238,22 +321,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       long long it = 0;
       bool ok = true;
-      for (long long u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
-        int ja, jb, tj, ti;
-        unit_coords(s, u, ja, jb, tj, ti);
-        for (int c = 0; ok && c < s.nch; ++c) {
+      const CUtensorMap* fenced = nullptr;
+      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+        const Unit U = W.get(u);
+        if (fence_maps && U.mapA != fenced) {
+          // descriptors written by the host into global memory: acquire them for the TMA unit
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(U.mapA) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(U.mapB) : "memory");
+          fenced = U.mapA;
+        }
+        for (int c = 0; ok && c < U.nch; ++c) {
           for (int which = 0; ok && which < 2; ++which) {
-            const int job = which ? jb : ja;
+            const int job = which ? U.jb : U.ja;
             if (job < 0) continue;
-            const int kb1 = min(s.nkb, (c + 1) * s.ck);
-            for (int kb = c * s.ck; kb < kb1; ++kb, ++it) {
+            const int kb1 = min(U.nkb, (c + 1) * U.ck);
+            for (int kb = c * U.ck; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
-              const uint32_t sa = base + st * kStageBytes;
-              mbar_expect_tx(full(st), kStageBytes);
-              tma_load_3d(sa, &mapA, full(st), kb * BK, tj * BM, job);
-              tma_load_3d(sa + kStageA, &mapB, full(st), kb * BK, ti * BN, job);
+              const uint32_t sa = base + st * C::kStageBytes;
+              mbar_expect_tx(full(st), C::kStageBytes);
+              tma_load_3d(sa, U.mapA, full(st), kb * BK, U.tj * BM, job);
+              tma_load_3d(sa + kStageA, U.mapB, full(st), kb * BK, U.ti * BN, job);
             }
           }
         }
@@ -274,30 +363,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       long long it = 0;
       int used[2] = {0, 0};
       bool ok = true;
-      for (long long u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
-        int ja, jb, tj, ti;
-        unit_coords(s, u, ja, jb, tj, ti);
-        for (int c = 0; ok && c < s.nch; ++c) {
+      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+        const Unit U = W.get(u);
+        for (int c = 0; ok && c < U.nch; ++c) {
           for (int which = 0; ok && which < 2; ++which) {
-            const int job = which ? jb : ja;
+            const int job = which ? U.jb : U.ja;
             if (job < 0) continue;
             const int slot = which;
             if (!mbar_wait(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u, ctl)) { ok = false; break; }
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
-            const int kb0 = c * s.ck, kb1 = min(s.nkb, (c + 1) * s.ck);
+            const int kb0 = c * U.ck, kb1 = min(U.nkb, (c + 1) * U.ck);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
               if (!mbar_wait(full(st), ph, ctl)) { ok = false; break; }
               tc_fence_after();
-              const uint32_t sa = base + st * kStageBytes;
+              const uint32_t sa = base + st * C::kStageBytes;
               const uint64_t da = smem_desc(sa), db = smem_desc(sa + kStageA);
 #pragma unroll
               for (int kk = 0; kk < BK / UK; ++kk) {
                 // advance the start address by 32 bytes per 16 fp16 of k
                 const uint64_t off = static_cast<uint64_t>((kk * UK * 2) >> 4);
-                mma_f16(td, da + off, db + off, !(c == 0 && kb == kb0 && kk == 0));
+                mma_f16(td, da + off, db + off, C::kIdesc, !(c == 0 && kb == kb0 && kk == 0));
               }
               mma_commit(empty(st));
             }
@@ -315,20 +403,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    constexpr int kHalf = BN / 2;                   // columns of a slot per epilogue warp
     const int ew = warp - 2;
     const int quad = warp & 3;                      // TMEM lanes 32*quad .. 32*quad+31
-    const int half = ew >> 2;                       // columns [128*half, 128*half+128) of a slot
+    const int half = ew >> 2;                       // columns [kHalf*half, kHalf*half + kHalf) of a slot
     const int row_in_tile = quad * 32 + lane;       // output column within the tile
     int used[2] = {0, 0};
     bool ok = true;
-    for (long long u = blockIdx.x; ok && u < s.units; u += gridDim.x) {
-      int ja, jb, tj, ti;
-      unit_coords(s, u, ja, jb, tj, ti);
-      const int64_t col = static_cast<int64_t>(tj) * BM + row_in_tile;
-      for (int c = 0; ok && c < s.nch; ++c) {
-        const bool last = (c == s.nch - 1);
+    for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      const Unit U = W.get(u);
+      const int64_t col = static_cast<int64_t>(U.tj) * BM + row_in_tile;
+      for (int c = 0; ok && c < U.nch; ++c) {
+        const bool last = (c == U.nch - 1);
         for (int which = 0; ok && which < 2; ++which) {
-          const int job = which ? jb : ja;
+          const int job = which ? U.jb : U.ja;
           if (job < 0) continue;
           const int slot = which;
           const int l = job / 3;
@@ -338,11 +426,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(tfull(slot), static_cast<uint32_t>(used[slot] & 1), ctl)) { ok = false; break; }
           tc_fence_after();
           const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) +
-                              static_cast<uint32_t>(slot * BN + half * 128);
+                              static_cast<uint32_t>(slot * BN + half * kHalf);
           if (!last) {
             // in-place reduction: keeps every later partial sum below 2^24
 #pragma unroll 1
-            for (int cc = 0; cc < 128; cc += 32) {
+            for (int cc = 0; cc < kHalf; cc += 32) {
               uint32_t v[32];
               tmem_ld32(ta + cc, v);
               tmem_wait_ld();
@@ -359,15 +447,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive(tempty(slot));
           } else {
             // final: exact symmetric residue, int8, row-contiguous
-            int8_t* out = res + static_cast<int64_t>(job) * n * ldr + col * ldr + static_cast<int64_t>(ti) * BN +
-                          half * 128;
-            const int64_t row0 = static_cast<int64_t>(ti) * BN + half * 128;
+            const int64_t row0 = static_cast<int64_t>(U.ti) * BN + half * kHalf;
+            int8_t* out = U.res + static_cast<int64_t>(job) * U.n * U.ldr + col * U.ldr + row0;
 #pragma unroll 1
-            for (int cc = 0; cc < 128; cc += 32) {
+            for (int cc = 0; cc < kHalf; cc += 32) {
               uint32_t v[32];
               tmem_ld32(ta + cc, v);
               tmem_wait_ld();
-              if (cc == 96) {
+              if (cc == kHalf - 32) {
                 tc_fence_before();
                 mbar_arrive(tempty(slot));          // TMEM slot may be refilled
               }
@@ -385,11 +472,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 w[q] = packed;
               }
-              if (col < n) {
+              if (col < U.n) {
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                   const int64_t r0 = row0 + cc + 16 * q;
-                  if (r0 < ldr)
+                  if (r0 < U.ldr)
                     *reinterpret_cast<uint4*>(out + cc + 16 * q) =
                         make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
                 }
@@ -406,7 +493,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::kTmemCols));
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_f16_kernel(const __grid_constant__ CUtensorMap mapA,   // B planes: MMA operand A
+                    const __grid_constant__ CUtensorMap mapB,   // A planes: MMA operand B
+                    const __grid_constant__ Plan pl, const Sched s, int8_t* __restrict__ res, int64_t ldr,
+                    int64_t n, unsigned int* status) {
+  const SingleWork W{&mapA, &mapB, s, res, ldr, n};
+  gemm_body<BN>(W, pl, status, false);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_f16_grouped_kernel(const GroupProblem* __restrict__ probs, int count, long long total,
+                            const __grid_constant__ Plan pl, unsigned int* status) {
+  const GroupWork W{probs, count, total};
+  gemm_body<BN>(W, pl, status, true);
 }
 
 // ------------------------------------------------------------------ host side
@@ -422,6 +528,9 @@ bool get_encoder() {
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
   });
   return g_encode != nullptr;
 }
@@ -438,27 +547,25 @@ bool make_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t kpad, 
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace
+template <int BN>
+cudaError_t set_smem_attrs() {
+  static cudaError_t err = [] {
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<BN>::kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_f16_grouped_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               Cfg<BN>::kSmemBytes);
+    return e;
+  }();
+  return err;
+}
 
-int g_f16_group = 16;   // tile rasterisation group (autotuned)
-
-cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
-                            const void* planesB, int8_t* res, int64_t ldr, int chunk_k, unsigned int* status,
-                            cudaStream_t st) {
-  if (m <= 0 || n <= 0) return cudaSuccess;
-  if (kpad % BK || ldr % 16 || chunk_k % BK || chunk_k < BK || chunk_k > 960) return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u)
-    return cudaErrorInvalidValue;
-  if (!get_encoder()) return cudaErrorNotSupported;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(gemm_f16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  });
-  if (attr_err != cudaSuccess) return attr_err;
+template <int BN>
+cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
+                          const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group,
+                          unsigned int* status, cudaStream_t st) {
+  cudaError_t e = set_smem_attrs<BN>();
+  if (e != cudaSuccess) return e;
   const int J = 3 * pl.N;
   CUtensorMap mapA, mapB;
   if (!make_map(&mapA, planesB, n, kpad, J, BM)) return cudaErrorInvalidValue;
@@ -469,14 +576,102 @@ cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, 
   s.TJ = static_cast<int>((n + BM - 1) / BM);
   s.TI = static_cast<int>((m + BN - 1) / BN);
   s.tiles = s.TJ * s.TI;
-  s.group = g_f16_group > 0 ? g_f16_group : 16;
+  s.group = group > 0 ? group : 16;
   s.nkb = static_cast<int>(kpad / BK);
   s.ck = chunk_k / BK;
   s.nch = (s.nkb + s.ck - 1) / s.ck;
   s.units = static_cast<long long>(s.pairs) * s.tiles;
   const long long grid = s.units < g_sms ? s.units : g_sms;
-  gemm_f16_kernel<<<static_cast<unsigned int>(grid), kThreads, kSmemBytes, st>>>(mapA, mapB, pl, s, m, n, res, ldr,
-                                                                                 status);
+  gemm_f16_kernel<BN><<<static_cast<unsigned int>(grid), kThreads, Cfg<BN>::kSmemBytes, st>>>(
+      mapA, mapB, pl, s, res, ldr, n, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int g_f16_group = 16;   // tile rasterisation group (autotuned)
+int g_f16_tile_n = 256; // output rows per tile of the single-GEMM launch (256, 128 or 64)
+
+cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
+                            const void* planesB, int8_t* res, int64_t ldr, int chunk_k, unsigned int* status,
+                            cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (kpad % BK || ldr % 16 || chunk_k % BK || chunk_k < BK || chunk_k > 960) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u)
+    return cudaErrorInvalidValue;
+  if (!get_encoder()) return cudaErrorNotSupported;
+  switch (g_f16_tile_n) {
+    case 64: return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, g_f16_group, status, st);
+    case 128: return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, g_f16_group, status, st);
+    default: return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, g_f16_group, status, st);
+  }
+}
+
+// ---------------------------------------------------------------- grouped
+size_t group_problem_bytes() { return sizeof(GroupProblem); }
+
+// Host set-up that must not happen inside a stream capture: the tensor-map
+// encoder and the shared-memory attributes of every tile width.
+cudaError_t prepare_gemm_f16() {
+  if (!get_encoder()) return cudaErrorNotSupported;
+  cudaError_t e = set_smem_attrs<64>();
+  if (e == cudaSuccess) e = set_smem_attrs<128>();
+  if (e == cudaSuccess) e = set_smem_attrs<256>();
+  return e;
+}
+
+// Fill the host-side descriptor of problem p of a grouped launch (tensor maps,
+// output, schedule); returns false on an invalid shape.  `unit_begin` is the
+// running unit count, advanced past this problem's units.
+bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, const void* planesA,
+                        const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,
+                        long long* unit_begin) {
+  if (!get_encoder()) return false;
+  GroupProblem& P = *static_cast<GroupProblem*>(desc);
+  std::memset(&P, 0, sizeof(P));
+  const int J = 3 * N;
+  if (!make_map(&P.mapA, planesB, n, kpad, J, BM)) return false;
+  if (!make_map(&P.mapB, planesA, m, kpad, J, tile_n)) return false;
+  P.res = res;
+  P.ldr = ldr;
+  P.n = n;
+  P.J = J;
+  P.TJ = static_cast<int>((n + BM - 1) / BM);
+  P.TI = static_cast<int>((m + tile_n - 1) / tile_n);
+  P.tiles = P.TJ * P.TI;
+  P.group = group > 0 ? group : 16;
+  P.nkb = static_cast<int>(kpad / BK);
+  P.ck = chunk_k / BK;
+  P.nch = (P.nkb + P.ck - 1) / P.ck;
+  P.unit_begin = *unit_begin;
+  *unit_begin += static_cast<long long>((J + 1) / 2) * P.tiles;
+  return true;
+}
+
+cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long total_units, const Plan& pl,
+                                    int tile_n, unsigned int* status, cudaStream_t st) {
+  if (count <= 0 || total_units <= 0) return cudaSuccess;
+  if (!get_encoder()) return cudaErrorNotSupported;
+  const GroupProblem* P = static_cast<const GroupProblem*>(probs_dev);
+  const long long grid = total_units < g_sms ? total_units : g_sms;
+  cudaError_t e;
+  switch (tile_n) {
+    case 64:
+      if ((e = set_smem_attrs<64>()) != cudaSuccess) return e;
+      gemm_f16_grouped_kernel<64><<<static_cast<unsigned int>(grid), kThreads, Cfg<64>::kSmemBytes, st>>>(
+          P, count, total_units, pl, status);
+      break;
+    case 128:
+      if ((e = set_smem_attrs<128>()) != cudaSuccess) return e;
+      gemm_f16_grouped_kernel<128><<<static_cast<unsigned int>(grid), kThreads, Cfg<128>::kSmemBytes, st>>>(
+          P, count, total_units, pl, status);
+      break;
+    default:
+      if ((e = set_smem_attrs<256>()) != cudaSuccess) return e;
+      gemm_f16_grouped_kernel<256><<<static_cast<unsigned int>(grid), kThreads, Cfg<256>::kSmemBytes, st>>>(
+          P, count, total_units, pl, status);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -101,20 +101,19 @@ __device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long l
   return E;
 }
 
-// ---- pass 1: max exponent and non-finite flag
+// ---- pass 1: max exponent and non-finite flag (one block: row block rb, h chunk hc)
 template <bool S, bool ROWS_CONTIG>
-__global__ void __launch_bounds__(kThreads) exp_max_kernel(const typename Bits<S>::V* __restrict__ X,
-                                                           int64_t rows, int64_t k, int64_t rs,
-                                                           int64_t hs, int* __restrict__ emax,
-                                                           unsigned int* __restrict__ flag) {
+__device__ __forceinline__ void exp_max_block(const typename Bits<S>::V* __restrict__ X, int64_t rows, int64_t k,
+                                              int64_t rs, int64_t hs, int* __restrict__ emax,
+                                              unsigned int* __restrict__ flag, int64_t rb, int64_t hc) {
   using B = Bits<S>;
   int best = 0;
   bool bad = false;
   int64_t r;
   if (ROWS_CONTIG) {
-    r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    r = rb * kThreads + threadIdx.x;
     if (r >= rows) return;
-    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0; h < h1; ++h) {
       const typename B::V v = X[r + h * hs];
@@ -125,9 +124,9 @@ __global__ void __launch_bounds__(kThreads) exp_max_kernel(const typename Bits<S
     }
   } else {
     const int lane = threadIdx.x & 31;
-    r = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+    r = rb * (kThreads / 32) + (threadIdx.x >> 5);
     if (r >= rows) return;
-    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0 + lane; h < h1; h += 32) {
       const typename B::V v = X[r * rs + h];
@@ -146,21 +145,28 @@ __global__ void __launch_bounds__(kThreads) exp_max_kernel(const typename Bits<S
   if (bad) atomicOr(flag + r, 1u);
 }
 
-// ---- pass 2: exact quantised sum of squares
 template <bool S, bool ROWS_CONTIG>
-__global__ void __launch_bounds__(kThreads) exp_sum_kernel(const typename Bits<S>::V* __restrict__ X,
+__global__ void __launch_bounds__(kThreads) exp_max_kernel(const typename Bits<S>::V* __restrict__ X,
                                                            int64_t rows, int64_t k, int64_t rs,
-                                                           int64_t hs, const int* __restrict__ emax,
-                                                           const unsigned int* __restrict__ flag,
-                                                           unsigned long long* __restrict__ sum) {
+                                                           int64_t hs, int* __restrict__ emax,
+                                                           unsigned int* __restrict__ flag) {
+  exp_max_block<S, ROWS_CONTIG>(X, rows, k, rs, hs, emax, flag, blockIdx.x, blockIdx.y);
+}
+
+// ---- pass 2: exact quantised sum of squares (one block)
+template <bool S, bool ROWS_CONTIG>
+__device__ __forceinline__ void exp_sum_block(const typename Bits<S>::V* __restrict__ X, int64_t rows, int64_t k,
+                                              int64_t rs, int64_t hs, const int* __restrict__ emax,
+                                              const unsigned int* __restrict__ flag,
+                                              unsigned long long* __restrict__ sum, int64_t rb, int64_t hc) {
   using B = Bits<S>;
   unsigned long long acc = 0;
   int64_t r;
   if (ROWS_CONTIG) {
-    r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    r = rb * kThreads + threadIdx.x;
     if (r >= rows || flag[r] || emax[r] == 0) return;
     const int e = emax[r] - 2048;
-    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0; h < h1; ++h) {
       const typename B::V v = X[r + h * hs];
@@ -169,10 +175,10 @@ __global__ void __launch_bounds__(kThreads) exp_sum_kernel(const typename Bits<S
     }
   } else {
     const int lane = threadIdx.x & 31;
-    r = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+    r = rb * (kThreads / 32) + (threadIdx.x >> 5);
     if (r >= rows || flag[r] || emax[r] == 0) return;
     const int e = emax[r] - 2048;
-    const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+    const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0 + lane; h < h1; h += 32) {
       const typename B::V v = X[r * rs + h];
@@ -185,19 +191,76 @@ __global__ void __launch_bounds__(kThreads) exp_sum_kernel(const typename Bits<S
   if (acc) atomicAdd(sum + r, acc);
 }
 
+template <bool S, bool ROWS_CONTIG>
+__global__ void __launch_bounds__(kThreads) exp_sum_kernel(const typename Bits<S>::V* __restrict__ X,
+                                                           int64_t rows, int64_t k, int64_t rs,
+                                                           int64_t hs, const int* __restrict__ emax,
+                                                           const unsigned int* __restrict__ flag,
+                                                           unsigned long long* __restrict__ sum) {
+  exp_sum_block<S, ROWS_CONTIG>(X, rows, k, rs, hs, emax, flag, sum, blockIdx.x, blockIdx.y);
+}
+
+__device__ __forceinline__ int16_t finalize_row(const Plan& pl, int em, unsigned int fl, unsigned long long S) {
+  if (fl) return kExpNonfinite;
+  const int e = em ? em - 2048 : 0;
+  return static_cast<int16_t>(exponent_from_sum(pl, S) - e);
+}
+
 __global__ void exp_finalize_kernel(int64_t rows, const int* __restrict__ emax,
                                     const unsigned int* __restrict__ flag,
                                     const unsigned long long* __restrict__ sum,
                                     const __grid_constant__ Plan pl, int16_t* __restrict__ xout) {
   const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  if (flag[r]) {
-    xout[r] = kExpNonfinite;
-    return;
+  xout[r] = finalize_row(pl, emax[r], flag[r], sum[r]);
+}
+
+// ---- grouped forms: one launch per pass over every segment of a grouped call
+__device__ __forceinline__ int find_seg(const ExpSeg* segs, int nseg, long long b) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
   }
-  const int e = emax[r] ? emax[r] - 2048 : 0;
-  const int E = exponent_from_sum(pl, sum[r]);
-  xout[r] = static_cast<int16_t>(E - e);
+  return lo;
+}
+
+template <bool S>
+__global__ void __launch_bounds__(kThreads) exp_max_grouped(const ExpSeg* __restrict__ segs, int nseg) {
+  const ExpSeg& g = segs[find_seg(segs, nseg, blockIdx.x)];
+  const long long local = blockIdx.x - g.block_begin;
+  const auto* X = static_cast<const typename Bits<S>::V*>(g.X);
+  if (g.rows_contig)
+    exp_max_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks);
+  else
+    exp_max_block<S, false>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks);
+}
+
+template <bool S>
+__global__ void __launch_bounds__(kThreads) exp_sum_grouped(const ExpSeg* __restrict__ segs, int nseg) {
+  const ExpSeg& g = segs[find_seg(segs, nseg, blockIdx.x)];
+  const long long local = blockIdx.x - g.block_begin;
+  const auto* X = static_cast<const typename Bits<S>::V*>(g.X);
+  if (g.rows_contig)
+    exp_sum_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks);
+  else
+    exp_sum_block<S, false>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks);
+}
+
+// one thread per row of every segment; row_begin holds the prefix sums of rows
+__global__ void exp_finalize_grouped(const ExpSeg* __restrict__ segs, int nseg,
+                                     const long long* __restrict__ row_begin, long long total,
+                                     const __grid_constant__ Plan pl) {
+  const long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= total) return;
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_begin[mid] <= r) lo = mid; else hi = mid - 1;
+  }
+  const ExpSeg& g = segs[lo];
+  const long long i = r - row_begin[lo];
+  g.xout[i] = finalize_row(pl, g.emax[i], g.flag[i], g.sum[i]);
 }
 
 template <bool S>
@@ -232,6 +295,36 @@ cudaError_t launch_t(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_
 }
 
 }  // namespace
+
+long long exp_seg_blocks(ExpSeg& g) {
+  g.rows_contig = (g.rs == 1) ? 1 : 0;
+  g.hchunks = static_cast<int>(g.k > 0 ? (g.k + kChunkH - 1) / kChunkH : 0);
+  const long long rb = g.rows_contig ? (g.rows + kThreads - 1) / kThreads : (g.rows + 7) / 8;
+  return g.hchunks ? rb * g.hchunks : 0;
+}
+
+cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, int nseg, long long blocks,
+                                     const long long* row_begin_dev, long long total_rows, const Plan& pl,
+                                     cudaStream_t st) {
+  if (nseg <= 0) return cudaSuccess;
+  if (blocks > 0) {
+    if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+    if (single) {
+      exp_max_grouped<true><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
+      exp_sum_grouped<true><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
+    } else {
+      exp_max_grouped<false><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
+      exp_sum_grouped<false><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
+    }
+    count_launches(2);
+  }
+  if (total_rows > 0) {
+    exp_finalize_grouped<<<static_cast<unsigned int>((total_rows + 255) / 256), 256, 0, st>>>(
+        segs_dev, nseg, row_begin_dev, total_rows, pl);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
 
 size_t exponents_scratch_bytes(int64_t rows) {
   return static_cast<size_t>(round_up(rows, 64)) * (4 + 4 + 8);

@@ -7,14 +7,19 @@
 //   plane 3l+0 = mod(a'_R, p_l), plane 3l+1 = mod(a'_I, p_l),
 //   plane 3l+2 = mod(plane 3l+0 + plane 3l+1, p_l)                 (Step V-i, eq. karatsuba)
 // mod is the symmetric remainder of Section II with ties rounded up, so every
-// residue fits int8 (and is exact in fp16).  Everything is integer arithmetic:
-// with v = +-m 2^elsb, a' = m 2^(elsb+x) when elsb+x >= 0 (residue
-// (m mod p)(2^s mod p) mod p) and m >> -(elsb+x) otherwise.
+// residue fits int8 (and is exact in fp16).
+//
+// Arithmetic: a' (< 2^97) is formed exactly from the IEEE bits with integer
+// shifts and cut once per entry into signed 13-bit chunks c_t (exact floats).
+// Per modulus, a' == sum_t c_t w_t (mod p) with w_t = 2^(13t) mod p in
+// [-128, 127]: every product is below 2^20 and the sum below 2^23, so the FP32
+// sum is exact; one rint-based reduction and a symmetric fix-up give the
+// residue.  This keeps the per-modulus work on the FP32 pipe.
 //
 // Output layout: planes[(3l+c) * rows * kpad + r * kpad + h]; h in [k, kpad)
-// is zero.  One block handles 32 rows x 64 h: the tile is staged through
-// shared memory so global reads are coalesced whichever of r or h is
-// contiguous, and every thread then writes 8 consecutive h of one row.
+// is zero.  A block handles 32 rows x 32 h: the tile goes through shared
+// memory so global reads are coalesced whichever of r or h is contiguous;
+// each thread then owns 4 consecutive h of one row, 8 threads per row.
 #include <cuda_fp16.h>
 
 #include "emu_internal.h"
@@ -23,127 +28,104 @@ namespace emu {
 namespace {
 
 constexpr int kTileR = 32;
-constexpr int kTileH = 64;
-constexpr int kThreads = 256;   // 8 warps: warp w owns h in [8w, 8w+8) of the tile
-constexpr int kPerThread = 8;
+constexpr int kTileH = 32;
+constexpr int kThreads = 256;
+constexpr int kPerThread = 4;
 
-__device__ __forceinline__ uint32_t mod32(uint32_t x, uint32_t p, uint32_t bar) {
-  const uint32_t q = __umulhi(x, bar);
-  uint32_t r = x - q * p;
-  return r >= p ? r - p : r;
-}
-
-// Decoded magnitude of one real part: residue base value V (< 2^53), shift s
-// (>= 0: multiply by 2^s; < 0: already shifted), sign.
-struct Part {
-  uint32_t lo, hi;
-  int s;        // >= 0: a' = V 2^s, V = m; < 0 means a' = V (already truncated)
-  bool neg;
-  bool zero;
+struct SplitSmem {
+  uint64_t tre[kTileR][kTileH + 1];     // raw bits of the tile, [r][h], one element of padding
+  uint64_t tim[kTileR][kTileH + 1];
 };
 
+// Signed 13-bit chunks of a' = trunc(v 2^x) (exact floats, least significant first).
 template <bool SINGLE>
-__device__ __forceinline__ Part decode(uint64_t bits, int x) {
-  Part pt;
+__device__ __forceinline__ void chunks(uint64_t bits, int x, int nchunk, float (&c)[kMaxChunks]) {
+  bool neg;
   int ex;
   uint64_t m;
   int elsb;
   if (SINGLE) {
     const uint32_t b = static_cast<uint32_t>(bits);
-    pt.neg = (b >> 31) != 0;
+    neg = (b >> 31) != 0;
     ex = (b >> 23) & 0xFF;
     const uint32_t fr = b & 0x7FFFFFu;
     m = ex ? (fr | 0x800000u) : fr;
     elsb = ex ? ex - 150 : -149;
   } else {
-    pt.neg = (bits >> 63) != 0;
+    neg = (bits >> 63) != 0;
     ex = static_cast<int>((bits >> 52) & 0x7FF);
     const uint64_t fr = bits & 0xFFFFFFFFFFFFFull;
     m = ex ? (fr | (1ull << 52)) : fr;
     elsb = ex ? ex - 1075 : -1074;
   }
-  const int s = elsb + x;
-  uint64_t V;
+  const int s = elsb + x;                       // a' = m 2^s (s >= 0) or m >> -s
+  uint64_t lo, hi;
   if (s >= 0) {
-    V = m;
-    pt.s = s;
+    // s < 44 whenever x comes from the exponent phase (|a'| < 2^(Emax+1) <= 2^97);
+    // larger shifts only occur for caller-supplied exponents and saturate to zero
+    lo = s < 64 ? (m << s) : 0ull;
+    hi = s == 0 ? 0ull : (s < 64 ? (m >> (64 - s)) : (s < 128 ? (m << (s - 64)) : 0ull));
   } else {
-    V = (-s >= 64) ? 0ull : (m >> (-s));
-    pt.s = -1;
+    lo = (-s >= 64) ? 0ull : (m >> (-s));
+    hi = 0ull;
   }
-  pt.zero = (V == 0);
-  pt.lo = static_cast<uint32_t>(V);
-  pt.hi = static_cast<uint32_t>(V >> 32);
-  return pt;
+  const float sg = neg ? -1.0f : 1.0f;
+#pragma unroll
+  for (int t = 0; t < kMaxChunks; ++t) {
+    const int b = kChunkBits * t;
+    uint32_t v;
+    if (b + kChunkBits <= 64) v = static_cast<uint32_t>(lo >> b);
+    else if (b >= 64) v = static_cast<uint32_t>(hi >> (b - 64));
+    else v = static_cast<uint32_t>((lo >> b) | (hi << (64 - b)));
+    v &= (1u << kChunkBits) - 1u;
+    // exact int -> float for v < 2^23 through the bit pattern of 2^23 + v
+    const float f = __int_as_float(static_cast<int>(0x4B000000u | v)) - 8388608.0f;
+    c[t] = (t < nchunk) ? sg * f : 0.0f;
+  }
 }
 
-// symmetric residue of one part modulo p (ties up)
-__device__ __forceinline__ int residue(const Part& pt, uint32_t p, uint32_t bar, uint32_t two32,
-                                       const uint8_t* pow2) {
-  if (pt.zero) return 0;
-  uint32_t r = mod32(pt.lo, p, bar);
-  r = mod32(pt.hi * two32 + r, p, bar);
-  // s < 128 whenever x comes from the exponent phase (|a'| < 2^(E+1)); the
-  // mask only keeps a caller-supplied exponent inside the table
-  if (pt.s >= 0) r = mod32(r * static_cast<uint32_t>(pow2[pt.s & (kPow2Table - 1)]), p, bar);
-  int v = static_cast<int>(r);
-  if (pt.neg && v) v = static_cast<int>(p) - v;
-  if (2 * v >= static_cast<int>(p)) v -= static_cast<int>(p);
-  return v;
+// Symmetric residue (ties up) of the exact float integer z, |z| < 2^23.
+__device__ __forceinline__ float sym_mod_f(float z, float p, float inv_p) {
+  float r = fmaf(-rintf(z * inv_p), p, z);      // exact; |r| <= p/2 + 2
+  if (2.0f * r >= p) r -= p;
+  if (2.0f * r < -p) r += p;
+  return r;
 }
 
-__device__ __forceinline__ int sym_small(int v, int p) {   // |v| <= 256
-  if (2 * v >= p) v -= p;
-  if (2 * v < -p) v += p;
-  return v;
+// magic-number float -> int8 byte (|r| <= 128, exact integer r)
+__device__ __forceinline__ uint32_t byte_of(float r) {
+  return static_cast<uint32_t>(__float_as_int(r + 12582912.0f)) & 0xFFu;
 }
 
 template <typename T>
-struct Store8;
+struct Store4;
 template <>
-struct Store8<int8_t> {
-  __device__ static void put(int8_t* dst, const int* v) {
-    uint2 w;
-    w.x = (v[0] & 0xFF) | ((v[1] & 0xFF) << 8) | ((v[2] & 0xFF) << 16) | ((v[3] & 0xFF) << 24);
-    w.y = (v[4] & 0xFF) | ((v[5] & 0xFF) << 8) | ((v[6] & 0xFF) << 16) | ((v[7] & 0xFF) << 24);
-    *reinterpret_cast<uint2*>(dst) = w;
+struct Store4<int8_t> {
+  __device__ static void put(int8_t* dst, const float (&v)[kPerThread]) {
+    *reinterpret_cast<uint32_t*>(dst) = byte_of(v[0]) | (byte_of(v[1]) << 8) | (byte_of(v[2]) << 16) |
+                                        (byte_of(v[3]) << 24);
   }
 };
 template <>
-struct Store8<__half> {
-  __device__ static void put(__half* dst, const int* v) {
-    uint4 w;
-    __half2 h0 = __halves2half2(__int2half_rn(v[0]), __int2half_rn(v[1]));
-    __half2 h1 = __halves2half2(__int2half_rn(v[2]), __int2half_rn(v[3]));
-    __half2 h2 = __halves2half2(__int2half_rn(v[4]), __int2half_rn(v[5]));
-    __half2 h3 = __halves2half2(__int2half_rn(v[6]), __int2half_rn(v[7]));
-    w.x = *reinterpret_cast<uint32_t*>(&h0);
-    w.y = *reinterpret_cast<uint32_t*>(&h1);
-    w.z = *reinterpret_cast<uint32_t*>(&h2);
-    w.w = *reinterpret_cast<uint32_t*>(&h3);
-    *reinterpret_cast<uint4*>(dst) = w;
+struct Store4<__half> {
+  __device__ static void put(__half* dst, const float (&v)[kPerThread]) {
+    __half2 a = __floats2half2_rn(v[0], v[1]);
+    __half2 b = __floats2half2_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(dst) =
+        make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
   }
 };
 
 template <bool SINGLE, bool ROWS_CONTIG, typename T>
-__global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict__ Xv, int64_t rows,
-                                                         int64_t k, int64_t rs, int64_t hs,
-                                                         bool conj, const int16_t* __restrict__ xexp,
-                                                         const __grid_constant__ Plan pl,
-                                                         int64_t kpad, T* __restrict__ planes) {
-  // raw bits of the tile, [h][r] with one element of padding per h-row
-  __shared__ uint64_t tre[kTileH][kTileR + 1];
-  __shared__ uint64_t tim[kTileH][kTileR + 1];
-  __shared__ uint8_t pow2s[kMaxModuli][kPow2Table];
-
+__device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restrict__ Xv, int64_t rows, int64_t k,
+                                            int64_t rs, int64_t hs, bool conj, const int16_t* __restrict__ xexp,
+                                            const Plan& pl, int64_t kpad, T* __restrict__ planes, int64_t rtile,
+                                            int64_t htile) {
   const int tid = threadIdx.x;
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kTileR;
-  const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kTileH;
+  const int64_t r0 = rtile * kTileR;
+  const int64_t h0 = htile * kTileH;
 
-  for (int i = tid; i < pl.N * kPow2Table; i += kThreads)
-    pow2s[i / kPow2Table][i % kPow2Table] = pl.pow2[i / kPow2Table][i % kPow2Table];
-
-  // load phase: 2048 elements, 8 per thread, coalesced along the contiguous index
+  // load phase: 1024 elements, 4 per thread, coalesced along the contiguous index
 #pragma unroll
   for (int it = 0; it < (kTileR * kTileH) / kThreads; ++it) {
     int rr, hh;
@@ -151,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict_
       rr = tid & 31;
       hh = (tid >> 5) + 8 * it;
     } else {
-      hh = tid & 63;
-      rr = (tid >> 6) + 4 * it;
+      hh = tid & 31;
+      rr = (tid >> 5) + 8 * it;
     }
     const int64_t r = r0 + rr, h = h0 + hh;
     uint64_t bre = 0, bim = 0;
@@ -168,54 +150,100 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict_
         bim = static_cast<uint64_t>(__double_as_longlong(conj ? -v.y : v.y));
       }
     }
-    tre[hh][rr] = bre;
-    tim[hh][rr] = bim;
+    sm.tre[rr][hh] = bre;
+    sm.tim[rr][hh] = bim;
   }
   __syncthreads();
 
-  const int rr = tid & 31;
-  const int hb = (tid >> 5) * kPerThread;
+  const int rr = tid >> 3;
+  const int hb = (tid & 7) * kPerThread;
   const int64_t r = r0 + rr;
   if (r >= rows) return;
   const int x = xexp[r];
   const bool flagged = (x == kExpNonfinite);
+  const int nch = pl.nchunk;
 
-  Part pre[kPerThread], pim[kPerThread];
+  float cre[kPerThread][kMaxChunks], cim[kPerThread][kMaxChunks];
 #pragma unroll
   for (int j = 0; j < kPerThread; ++j) {
-    uint64_t br = tre[hb + j][rr], bi = tim[hb + j][rr];
+    uint64_t br = sm.tre[rr][hb + j], bi = sm.tim[rr][hb + j];
     // a flagged row, or a non-finite entry, contributes zeros
     const bool bad = flagged ||
                      (SINGLE ? (((br >> 23) & 0xFF) == 0xFF || ((bi >> 23) & 0xFF) == 0xFF)
                              : (((br >> 52) & 0x7FF) == 0x7FF || ((bi >> 52) & 0x7FF) == 0x7FF));
     if (bad) br = bi = 0;
-    pre[j] = decode<SINGLE>(br, flagged ? 0 : x);
-    pim[j] = decode<SINGLE>(bi, flagged ? 0 : x);
+    chunks<SINGLE>(br, flagged ? 0 : x, nch, cre[j]);
+    chunks<SINGLE>(bi, flagged ? 0 : x, nch, cim[j]);
   }
   const int64_t plane_stride = rows * kpad;
   T* base = planes + r * kpad + h0 + hb;
   for (int l = 0; l < pl.N; ++l) {
-    const uint32_t p = static_cast<uint32_t>(pl.p[l]);
-    const uint32_t bar = pl.barrett[l], two32 = pl.two32[l];
-    const uint8_t* pw = pow2s[l];
-    int vr[kPerThread], vi[kPerThread], vs[kPerThread];
+    const float p = static_cast<float>(pl.p[l]);
+    const float ip = pl.inv_p[l];
+    float w[kMaxChunks];
+#pragma unroll
+    for (int t = 0; t < kMaxChunks; ++t) w[t] = pl.w13[l][t];
+    float vr[kPerThread], vi[kPerThread], vs[kPerThread];
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
-      vr[j] = residue(pre[j], p, bar, two32, pw);
-      vi[j] = residue(pim[j], p, bar, two32, pw);
-      vs[j] = sym_small(vr[j] + vi[j], static_cast<int>(p));
+      float zr = 0.0f, zi = 0.0f;
+#pragma unroll
+      for (int t = 0; t < kMaxChunks; ++t) {
+        if (t < nch) {
+          zr = fmaf(cre[j][t], w[t], zr);
+          zi = fmaf(cim[j][t], w[t], zi);
+        }
+      }
+      vr[j] = sym_mod_f(zr, p, ip);
+      vi[j] = sym_mod_f(zi, p, ip);
+      float sr = vr[j] + vi[j];
+      if (2.0f * sr >= p) sr -= p;
+      if (2.0f * sr < -p) sr += p;
+      vs[j] = sr;
     }
     T* dst = base + static_cast<int64_t>(3 * l) * plane_stride;
-    Store8<T>::put(dst, vr);
-    Store8<T>::put(dst + plane_stride, vi);
-    Store8<T>::put(dst + 2 * plane_stride, vs);
+    Store4<T>::put(dst, vr);
+    Store4<T>::put(dst + plane_stride, vi);
+    Store4<T>::put(dst + 2 * plane_stride, vs);
   }
+}
+
+template <bool SINGLE, bool ROWS_CONTIG, typename T>
+__global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict__ Xv, int64_t rows,
+                                                         int64_t k, int64_t rs, int64_t hs,
+                                                         bool conj, const int16_t* __restrict__ xexp,
+                                                         const __grid_constant__ Plan pl,
+                                                         int64_t kpad, T* __restrict__ planes) {
+  __shared__ SplitSmem sm;
+  split_block<SINGLE, ROWS_CONTIG, T>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x, blockIdx.y);
+}
+
+// one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
+template <bool SINGLE, typename T>
+__global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __restrict__ segs, int nseg,
+                                                          const __grid_constant__ Plan pl) {
+  __shared__ SplitSmem sm;
+  int lo = 0, hi = nseg - 1;
+  const long long b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  const SplitSeg& g = segs[lo];
+  const long long local = b - g.block_begin;
+  const int64_t rt = local / g.htiles, ht = local % g.htiles;
+  T* planes = static_cast<T*>(g.planes);
+  if (g.rows_contig)
+    split_block<SINGLE, true, T>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
+  else
+    split_block<SINGLE, false, T>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
 }
 
 template <bool SINGLE, typename T>
 cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                      const Plan& pl, const int16_t* xexp, int64_t kpad, void* planes,
                      cudaStream_t st) {
+  if ((rows + kTileR - 1) / kTileR > 2147483647LL || kpad / kTileH > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>((rows + kTileR - 1) / kTileR),
             static_cast<unsigned int>(kpad / kTileH));
   if (rs == 1)
@@ -230,11 +258,33 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
 
 }  // namespace
 
+long long split_seg_blocks(SplitSeg& g) {
+  g.rows_contig = (g.rs == 1) ? 1 : 0;
+  g.htiles = static_cast<int>(g.kpad / kTileH);
+  return ((g.rows + kTileR - 1) / kTileR) * g.htiles;
+}
+
+cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_dev, int nseg, long long blocks,
+                                 const Plan& pl, cudaStream_t st) {
+  if (nseg <= 0 || blocks <= 0) return cudaSuccess;
+  if (blocks > 2147483647LL) return cudaErrorInvalidValue;
+  const unsigned int gb = static_cast<unsigned int>(blocks);
+  if (single) {
+    if (fp16) split_grouped<true, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+    else split_grouped<true, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+  } else {
+    if (fp16) split_grouped<false, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+    else split_grouped<false, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp, bool fp16,
                          int64_t kpad, void* planes, cudaStream_t st) {
   if (rows <= 0 || kpad <= 0) return cudaSuccess;
-  if (kpad % kTileH) return cudaErrorInvalidValue;
+  if (kpad % 64) return cudaErrorInvalidValue;
   if (single)
     return fp16 ? launch_t<true, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st)
                 : launch_t<true, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st);

@@ -100,6 +100,10 @@ int gcd_int(int a, int b) {
   return a;
 }
 
+}  // namespace
+int plan_exponent(const Plan& pl, uint64_t S);
+namespace {
+
 void build(int N, Plan& pl) {
   std::memset(&pl, 0, sizeof(pl));
   pl.N = N;
@@ -141,6 +145,13 @@ void build(int N, Plan& pl) {
       pl.pow2[l][s] = static_cast<uint8_t>(v);
       v = (v * 2u) % p;
     }
+    for (int t = 0; t < kMaxChunks; ++t) {
+      const int e = kChunkBits * t;           // 2^e mod p, then symmetric
+      const int r = e < kPow2Table ? pl.pow2[l][e] : 0;
+      const int sr = 2 * r >= static_cast<int>(p) ? r - static_cast<int>(p) : r;
+      pl.w13[l][t] = static_cast<float>(sr);
+    }
+    pl.inv_p[l] = static_cast<float>(1.0 / static_cast<double>(p));
   }
   // negP = 2^(32L) - P, K = R0 P - 128 sum w (mod 2^(32L))
   Big zero;
@@ -163,6 +174,10 @@ void build(int N, Plan& pl) {
   const int bx = bitlen(X);
   pl.sX = bx > 63 ? bx - 63 : 0;
   pl.Xtop = extract64(X, pl.sX);
+  // the largest exponent E (S at its minimum) bounds every |a'| < 2^(E+1)
+  const int Emax = plan_exponent(pl, 0);
+  pl.nchunk = (Emax + 1 + kChunkBits - 1) / kChunkBits;
+  if (pl.nchunk < 1) pl.nchunk = 1;
 }
 
 std::mutex g_mu;

@@ -47,6 +47,18 @@ _SIGS = [
     ("emu_cgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
                            _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
                            _c_i64, _c_int, _c_ptr]),
+    ("emu_grouped_create", _c_int, [_c_int, _c_int, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                    _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_int,
+                                    ctypes.POINTER(_c_ptr)]),
+    ("emu_grouped_run", _c_int, [_c_ptr, _c_ptr]),
+    ("emu_grouped_tile", _c_int, [_c_ptr]),
+    ("emu_grouped_kernels", _c_int, [_c_ptr]),
+    ("emu_grouped_destroy", _c_int, [_c_ptr]),
+    ("emu_grouped_phase_times", _c_int, [_c_ptr, ctypes.POINTER(ctypes.c_float), _c_ptr]),
+    ("emu_zgemm_grouped", _c_int, [_c_int, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                   _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_ptr]),
+    ("emu_cgemm_grouped", _c_int, [_c_int, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
+                                   _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_ptr]),
     ("emu_workspace_bytes", ctypes.c_size_t, [_c_int, _c_i64, _c_i64, _c_i64, _c_int]),
     ("emu_set_workspace", _c_int, [_c_ptr, ctypes.c_size_t]),
     ("emu_set_engine", _c_int, [_c_int, _c_int]),
@@ -132,6 +144,83 @@ def emu_cgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_
     b = (ctypes.c_float * 2)(float(beta.real), float(beta.imag))
     return lib().emu_cgemm(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc,
                            num_moduli, _stream(stream))
+
+
+class GroupedArgs:
+    """Host arrays describing a grouped call (kept alive with the plan)."""
+
+    def __init__(self, problems, num_moduli):
+        # problems: list of dicts with transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc
+        c = len(problems)
+        I64 = ctypes.c_int64 * max(c, 1)
+        OPS_ = ctypes.c_int * max(c, 1)
+        P = ctypes.c_void_p * max(c, 1)
+        D = ctypes.c_double * max(2 * c, 2)
+        self.count = c
+        self.ta = OPS_(*[_op(p["transa"]) for p in problems])
+        self.tb = OPS_(*[_op(p["transb"]) for p in problems])
+        self.m = I64(*[p["m"] for p in problems])
+        self.n = I64(*[p["n"] for p in problems])
+        self.k = I64(*[p["k"] for p in problems])
+        self.lda = I64(*[p["lda"] for p in problems])
+        self.ldb = I64(*[p["ldb"] for p in problems])
+        self.ldc = I64(*[p["ldc"] for p in problems])
+        self.A = P(*[p["A"] for p in problems])
+        self.B = P(*[p["B"] for p in problems])
+        self.C = P(*[p["C"] for p in problems])
+        al, be = [], []
+        for p in problems:
+            a, b = complex(p.get("alpha", 1.0)), complex(p.get("beta", 0.0))
+            al += [a.real, a.imag]
+            be += [b.real, b.imag]
+        self.alpha = D(*al) if al else D()
+        self.beta = D(*be) if be else D()
+        self.N = num_moduli
+
+    def argv(self):
+        c = ctypes.cast
+        return (self.count, c(self.ta, _c_ptr), c(self.tb, _c_ptr), c(self.m, _c_ptr), c(self.n, _c_ptr),
+                c(self.k, _c_ptr), c(self.alpha, _c_ptr), c(self.A, _c_ptr), c(self.lda, _c_ptr),
+                c(self.B, _c_ptr), c(self.ldb, _c_ptr), c(self.beta, _c_ptr), c(self.C, _c_ptr),
+                c(self.ldc, _c_ptr))
+
+
+def emu_grouped_create(is_single, args, tile_n=0):
+    """Returns (status, plan handle)."""
+    h = _c_ptr()
+    st = lib().emu_grouped_create(int(is_single), *args.argv(), args.N, int(tile_n), ctypes.byref(h))
+    return st, h
+
+
+def emu_grouped_run(plan, stream=None):
+    return lib().emu_grouped_run(plan, _stream(stream))
+
+
+def emu_grouped_tile(plan):
+    return lib().emu_grouped_tile(plan)
+
+
+def emu_grouped_kernels(plan):
+    return lib().emu_grouped_kernels(plan)
+
+
+def emu_grouped_phase_times(plan, stream=None):
+    """(status, [exponents, split, residue products, CRT] milliseconds)."""
+    ms = (ctypes.c_float * 4)()
+    st = lib().emu_grouped_phase_times(plan, ms, _stream(stream))
+    return st, list(ms)
+
+
+def emu_grouped_destroy(plan):
+    return lib().emu_grouped_destroy(plan)
+
+
+def emu_zgemm_grouped(args, stream=None):
+    return lib().emu_zgemm_grouped(*args.argv(), args.N, _stream(stream))
+
+
+def emu_cgemm_grouped(args, stream=None):
+    return lib().emu_cgemm_grouped(*args.argv(), args.N, _stream(stream))
 
 
 def emu_workspace_bytes(is_single, m, n, k, num_moduli):
