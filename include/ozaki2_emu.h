@@ -139,6 +139,57 @@ emu_status_t emu_cgemm_grouped(int count, const emu_op_t* transa, const emu_op_t
                                const int64_t* ldb, const double* beta, void* const* C, const int64_t* ldc,
                                int num_moduli, void* stream);
 
+/* ----------------------------------------------------- moduli selection ---
+ * The paper chooses N from measured accuracy bands (Section IV-A).  This
+ * library adds (1) an a priori rule and (2) a small learned network that
+ * predicts, from features of A and B and the requested accuracy, the fewest
+ * moduli that meet it; the network's weights are loaded by the caller. */
+
+/* C = alpha op(A) op(B) + beta C with N chosen for the normalised accuracy
+ * target_err (max_ij |error| / ((|A_R|+|A_I|)(|B_R|+|B_I|))_ij): the loaded
+ * network's choice, else emu_moduli_apriori.  With a network loaded this
+ * synchronises `stream` once (the chosen N decides the launch configuration).
+ * *n_used (may be NULL) receives N. */
+emu_status_t emu_zgemm_tol(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                           const double* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                           const double* beta, void* C, int64_t ldc, double target_err, int* n_used,
+                           void* stream);
+emu_status_t emu_cgemm_tol(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                           const float* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                           const float* beta, void* C, int64_t ldc, double target_err, int* n_used,
+                           void* stream);
+
+/* A priori rule: the smallest N in [EMU_MIN_MODULI, EMU_MAX_MODULI] with
+ * 2^(1 - (P'_fast(N) - log2(8k)/2)) <= target, P'_fast = log2(P-1)/2 - 1.5
+ * (the fast-mode bound of Section III-B for rows of equal magnitude); host only. */
+int emu_moduli_apriori(int is_single, int64_t k, double target);
+
+/* Network: 39 features -> 64 -> 64 -> 21 logits (ReLU), logit t for N = 4 + t.
+ * Parameter vector (float): W1 (64x39 row major), b1, W2 (64x64), b2, W3 (21x64), b3. */
+int emu_mlp_param_count(void);
+/* Load (host pointer, count = emu_mlp_param_count()) or unload (NULL) the weights
+ * emu_zgemm_tol uses on the current device. */
+emu_status_t emu_mlp_set_weights(const float* params, int count);
+/* Features (39 floats, device) of op(A), op(B) and the target: 16-bin
+ * histograms of exponent spans of A-hat rows and B-hat columns, mean/max of
+ * 0.5 log2 of the quantised row sums, log2(k)/17, -log10(target)/16, dtype. */
+emu_status_t emu_moduli_features(int is_single, emu_op_t transa, emu_op_t transb, int64_t m, int64_t n,
+                                 int64_t k, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                 double target, float* features, void* stream);
+/* Training and inference kernels (all pointers device):
+ * forward: logits[batch][21] of X[batch][39];
+ * backward: grad (parameter-sized) and *loss of the mean binary cross-entropy
+ *   against Y[batch][21] (zeroed first, then accumulated);
+ * adam: one Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected; step >= 1);
+ * choose: smallest N whose probability, and that of every larger N, is >=
+ *   threshold, or -1, into *n_out. */
+emu_status_t emu_mlp_forward(const float* theta, const float* X, int batch, float* logits, void* stream);
+emu_status_t emu_mlp_backward(const float* theta, const float* X, const float* Y, int batch, float* grad,
+                              float* loss, void* stream);
+emu_status_t emu_mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, void* stream);
+emu_status_t emu_mlp_choose(const float* theta, const float* features, float threshold, int* n_out,
+                            void* stream);
+
 /* ------------------------------------------------------------ workspace --- */
 
 /* Bytes of device workspace one call of the given shape needs (is_single: 0

@@ -1,5 +1,6 @@
 // C ABI entry points: argument checks, workspace, the four phases in order.
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -24,6 +25,10 @@ struct DeviceState {
   size_t own_bytes = 0;
   void* user = nullptr;        // caller workspace (emu_set_workspace)
   size_t user_bytes = 0;
+  float* mlp = nullptr;        // moduli-selection weights (emu_mlp_set_weights)
+  bool mlp_loaded = false;
+  float* feat = nullptr;       // 39 features + chosen N (pinned host mirror below)
+  int* chosen_host = nullptr;
 };
 
 std::mutex g_mu;
@@ -430,6 +435,137 @@ emu_status_t emu_set_phase_events(void* const* events, int count) {
 }
 
 uint64_t emu_kernel_launches(void) { return emu::g_launches.load(); }
+
+// ------------------------------------------------------- moduli selection
+int emu_mlp_param_count(void) { return emu::kMlpParams; }
+
+int emu_moduli_apriori(int is_single, int64_t k, double target) {
+  (void)is_single;
+  if (!(target > 0.0) || k < 0) return EMU_MAX_MODULI;
+  // smallest N with 2^(1 - (P'_fast(N) - 0.5 log2(8k))) <= target,
+  // P'_fast = log2(P - 1)/2 - 1.5 (uniform-row Cauchy-Schwarz estimate)
+  const double need = 1.0 - std::log2(target);
+  const double lk = 0.5 * std::log2(8.0 * static_cast<double>(k > 1 ? k : 1));
+  for (int N = EMU_MIN_MODULI; N <= EMU_MAX_MODULI; ++N) {
+    const emu::Plan* pl = emu::get_plan(N);
+    double log2P = 0.0;
+    for (int l = 0; l < pl->N; ++l) log2P += std::log2(static_cast<double>(pl->p[l]));
+    const double Pf = log2P / 2.0 - 1.5;
+    if (Pf - lk >= need) return N;
+  }
+  return EMU_MAX_MODULI;
+}
+
+emu_status_t emu_mlp_set_weights(const float* params, int count) {
+  emu::DeviceState* ds = nullptr;
+  emu_status_t s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  std::lock_guard<std::mutex> lk(emu::g_mu);
+  if (!params) {
+    ds->mlp_loaded = false;
+    return EMU_OK;
+  }
+  if (count != emu::kMlpParams) return emu::bad(2);
+  if (!ds->mlp && cudaMalloc(&ds->mlp, sizeof(float) * emu::kMlpParams) != cudaSuccess) return EMU_ERR_ALLOC;
+  if (cudaMemcpy(ds->mlp, params, sizeof(float) * count, cudaMemcpyHostToDevice) != cudaSuccess) return EMU_ERR_CUDA;
+  ds->mlp_loaded = true;
+  return EMU_OK;
+}
+
+emu_status_t emu_mlp_forward(const float* theta, const float* X, int batch, float* logits, void* stream) {
+  if (!theta || !X || !logits || batch < 0) return emu::bad(batch < 0 ? 3 : 1);
+  return emu::cuda_status(emu::launch_mlp_forward(theta, X, batch, logits, static_cast<cudaStream_t>(stream)));
+}
+
+emu_status_t emu_mlp_backward(const float* theta, const float* X, const float* Y, int batch, float* grad, float* loss,
+                              void* stream) {
+  if (!theta || !X || !Y || !grad || !loss || batch < 0) return emu::bad(batch < 0 ? 4 : 1);
+  return emu::cuda_status(emu::launch_mlp_backward(theta, X, Y, batch, grad, loss, static_cast<cudaStream_t>(stream)));
+}
+
+emu_status_t emu_mlp_adam(float* theta, const float* grad, float* m, float* v, int step, float lr, void* stream) {
+  if (!theta || !grad || !m || !v || step < 1) return emu::bad(step < 1 ? 5 : 1);
+  return emu::cuda_status(emu::launch_mlp_adam(theta, grad, m, v, step, lr, static_cast<cudaStream_t>(stream)));
+}
+
+emu_status_t emu_mlp_choose(const float* theta, const float* features, float threshold, int* n_out, void* stream) {
+  if (!theta || !features || !n_out) return emu::bad(1);
+  return emu::cuda_status(emu::launch_mlp_choose(theta, features, threshold, n_out, static_cast<cudaStream_t>(stream)));
+}
+
+emu_status_t emu_moduli_features(int is_single, emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                                 const void* A, int64_t lda, const void* B, int64_t ldb, double target, float* features,
+                                 void* stream) {
+  emu_status_t s = emu::check_common(transa, transb, m, n, k, lda, ldb, 1, EMU_MIN_MODULI, false);
+  if (s != EMU_OK) return s;
+  if (!(target > 0.0) || !features) return emu::bad(!features ? 12 : 11);
+  emu::DeviceState* ds = nullptr;
+  s = emu::device_init(emu::current_device(), ds);
+  if (s != EMU_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t rmax = m > n ? m : n;
+  void* scr = nullptr;
+  if (cudaMallocAsync(&scr, emu::features_scratch_bytes(rmax > 0 ? rmax : 1), st) != cudaSuccess) return EMU_ERR_ALLOC;
+  int64_t rsa, hsa, rsb, hsb;
+  emu::strides_a(transa, lda, rsa, hsa);
+  emu::strides_b(transb, ldb, rsb, hsb);
+  const cudaError_t e = emu::launch_features(is_single != 0, A, m, rsa, hsa, B, n, rsb, hsb, k, target,
+                                             *emu::get_plan(EMU_MIN_MODULI), features, scr, st);
+  cudaFreeAsync(scr, st);
+  return emu::cuda_status(e);
+}
+
+static emu_status_t gemm_tol(int single, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar,
+                             double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
+                             void* C, int64_t ldc, double target, int* n_used, void* stream) {
+  emu_status_t s = emu::check_common(ta, tb, m, n, k, lda, ldb, ldc, EMU_MIN_MODULI, true);
+  if (s != EMU_OK) return s;
+  if (!(target > 0.0)) return emu::bad(14);
+  int N = emu_moduli_apriori(single, k, target);
+  if (m > 0 && n > 0 && k > 0) {
+    emu::DeviceState* ds = nullptr;
+    s = emu::device_init(emu::current_device(), ds);
+    if (s != EMU_OK) return s;
+    if (ds->mlp_loaded) {
+      cudaStream_t st = static_cast<cudaStream_t>(stream);
+      {
+        std::lock_guard<std::mutex> lk(emu::g_mu);
+        if (!ds->feat && cudaMalloc(&ds->feat, 64 * sizeof(float)) != cudaSuccess) return EMU_ERR_ALLOC;
+        if (!ds->chosen_host && cudaMallocHost(&ds->chosen_host, sizeof(int)) != cudaSuccess) return EMU_ERR_ALLOC;
+      }
+      s = emu_moduli_features(single, ta, tb, m, n, k, A, lda, B, ldb, target, ds->feat, stream);
+      if (s != EMU_OK) return s;
+      int* dn = reinterpret_cast<int*>(ds->feat + 48);
+      if (emu::launch_mlp_choose(ds->mlp, ds->feat, 0.99f, dn, st) != cudaSuccess) return EMU_ERR_CUDA;
+      if (cudaMemcpyAsync(ds->chosen_host, dn, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return EMU_ERR_CUDA;
+      const int Nm = *ds->chosen_host;
+      if (Nm >= EMU_MIN_MODULI && Nm <= EMU_MAX_MODULI) N = Nm;   // else: the a priori rule
+    }
+  }
+  if (n_used) *n_used = N;
+  return single ? emu::gemm<true>(ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream)
+                : emu::gemm<false>(ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream);
+}
+
+emu_status_t emu_zgemm_tol(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k, const double* alpha,
+                           const void* A, int64_t lda, const void* B, int64_t ldb, const double* beta, void* C,
+                           int64_t ldc, double target_err, int* n_used, void* stream) {
+  if (!alpha) return emu::bad(6);
+  if (!beta) return emu::bad(11);
+  return gemm_tol(0, transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0], beta[1], C, ldc,
+                  target_err, n_used, stream);
+}
+
+emu_status_t emu_cgemm_tol(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k, const float* alpha,
+                           const void* A, int64_t lda, const void* B, int64_t ldb, const float* beta, void* C,
+                           int64_t ldc, double target_err, int* n_used, void* stream) {
+  if (!alpha) return emu::bad(6);
+  if (!beta) return emu::bad(11);
+  return gemm_tol(1, transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0], beta[1], C, ldc,
+                  target_err, n_used, stream);
+}
 
 const char* emu_version(void) { return "ozaki2-emu 0.1 (sm_103a)"; }
 

@@ -17,6 +17,10 @@ constexpr int kChunkBits = 13;      // residue split: a' in signed 13-bit chunks
 constexpr int kMaxChunks = 8;       // 8 x 13 = 104 bits > every |a'| (< 2^97)
 constexpr int kSumFracBits = 15;    // row sums use ceil(|t| 2^15), Section III-B reading
 constexpr int16_t kExpNonfinite = EMU_EXP_NONFINITE;
+// moduli-selection network
+constexpr int kMlpIn = 39, kMlpHidden = 64, kMlpOut = 21, kMlpNmin = 4;
+constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
+                           kMlpOut * kMlpHidden + kMlpOut;
 
 // Per-N constants of Algorithm 1 Steps I-II and of the exact CRT, computed on
 // the host (plan.cpp) and passed to kernels by value.
@@ -126,6 +130,16 @@ bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, c
 cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long total_units, const Plan& pl,
                                     int tile_n, unsigned int* status, cudaStream_t st);
 cudaError_t prepare_gemm_f16();
+// moduli-selection network (mlp.cu) and its features (k_scale.cu)
+cudaError_t launch_mlp_forward(const float* th, const float* X, int batch, float* Z, cudaStream_t st);
+cudaError_t launch_mlp_backward(const float* th, const float* X, const float* Y, int batch, float* grad,
+                                float* loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* th, const float* g, float* m, float* v, int step, float lr, cudaStream_t st);
+cudaError_t launch_mlp_choose(const float* th, const float* x, float threshold, int* out, cudaStream_t st);
+size_t features_scratch_bytes(int64_t rows);
+cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, int64_t hsa, const void* B,
+                            int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, const Plan& pl,
+                            float* feat, void* scratch, cudaStream_t st);
 extern int g_f16_group;
 extern int g_f16_tile_n;
 

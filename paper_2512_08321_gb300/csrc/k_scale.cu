@@ -14,6 +14,7 @@
 // Element (r, h) of the source is X[r*rs + h*hs] (complex, in elements);
 // either rs == 1 (rows contiguous: one thread per row, coalesced along r) or
 // hs == 1 (entries of a row contiguous: one warp per row).
+#include <cmath>
 #include <mutex>
 
 #include "emu_internal.h"
@@ -294,7 +295,156 @@ cudaError_t launch_t(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_
   return cudaGetLastError();
 }
 
+// ---- features of the moduli-selection network
+// 16-bin histogram of exponent spans d = e_r - ilogb|v| (zero entries: bin 15)
+template <bool S, bool ROWS_CONTIG>
+__global__ void __launch_bounds__(kThreads) feat_hist_kernel(const typename Bits<S>::V* __restrict__ X, int64_t rows,
+                                                             int64_t k, int64_t rs, int64_t hs,
+                                                             const int* __restrict__ emax,
+                                                             unsigned long long* __restrict__ hist) {
+  using B = Bits<S>;
+  __shared__ unsigned int h[16];
+  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __syncthreads();
+  auto add = [&](typename B::U u, int e_off) {
+    int bin = 15;
+    if (u && !nonfinite<S>(u) && e_off) bin = min(e_off - ilogb_off<S>(u), 15);
+    atomicAdd(&h[bin], 1u);
+  };
+  if (ROWS_CONTIG) {
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    if (r < rows) {
+      const int e = emax[r];
+      const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+      const int64_t h1 = min(k, h0 + kChunkH);
+      for (int64_t c = h0; c < h1; ++c) {
+        const typename B::V v = X[r + c * hs];
+        add(B::re(v), e);
+        add(B::im(v), e);
+      }
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+    if (r < rows) {
+      const int e = emax[r];
+      const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+      const int64_t h1 = min(k, h0 + kChunkH);
+      for (int64_t c = h0 + lane; c < h1; c += 32) {
+        const typename B::V v = X[r * rs + c];
+        add(B::re(v), e);
+        add(B::im(v), e);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 16 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], static_cast<unsigned long long>(h[threadIdx.x]));
+}
+
+// mean and max over rows of L = 0.5 log2(max(S, 1)) - 15
+__global__ void __launch_bounds__(1024) feat_stats_kernel(const unsigned long long* __restrict__ sum, int64_t rows,
+                                                          float* __restrict__ out) {
+  __shared__ double ssum[32];
+  __shared__ float smax[32];
+  double acc = 0.0;
+  float mx = -1e30f;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) {
+    const unsigned long long S = sum[r] ? sum[r] : 1ull;
+    const float L = 0.5f * log2f(static_cast<float>(S)) - 15.0f;
+    acc += L;
+    mx = fmaxf(mx, L);
+  }
+  for (int o = 16; o; o >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    ssum[w] = acc;
+    smax[w] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    float b = -1e30f;
+    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) {
+      a += ssum[i];
+      b = fmaxf(b, smax[i]);
+    }
+    out[0] = static_cast<float>(a / static_cast<double>(rows > 0 ? rows : 1));
+    out[1] = rows > 0 ? b : 0.0f;
+  }
+}
+
+__global__ void feat_assemble_kernel(const unsigned long long* __restrict__ hist, const float* __restrict__ stats,
+                                     double total_a, double total_b, float logk, float tgt, float single,
+                                     float* __restrict__ f) {
+  const int i = threadIdx.x;
+  if (i < 16) f[i] = static_cast<float>(static_cast<double>(hist[i]) / total_a);
+  else if (i < 32) f[i] = static_cast<float>(static_cast<double>(hist[i]) / total_b);
+  else if (i < 36) f[i] = stats[i - 32];
+  else if (i == 36) f[i] = logk;
+  else if (i == 37) f[i] = tgt;
+  else if (i == 38) f[i] = single;
+}
+
+template <bool S>
+cudaError_t features_side(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_t hs, const Plan& pl,
+                          char* scr, unsigned long long* hist, float* stats, int16_t* xdummy, cudaStream_t st) {
+  using V = typename Bits<S>::V;
+  const V* X = static_cast<const V*>(Xv);
+  cudaError_t e = launch_t<S>(Xv, rows, k, rs, hs, pl, xdummy, scr, st);   // emax, flag, sums (+ exponents)
+  if (e != cudaSuccess) return e;
+  const int* emax = reinterpret_cast<const int*>(scr);
+  const unsigned long long* sum =
+      reinterpret_cast<const unsigned long long*>(scr + 8 * round_up(rows, 64));
+  const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
+  if (ychunks > 0) {
+    if (rs == 1) {
+      dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
+      feat_hist_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, hist);
+    } else {
+      dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
+      feat_hist_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, hist);
+    }
+    count_launches(1);
+  }
+  feat_stats_kernel<<<1, 1024, 0, st>>>(sum, rows, stats);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t features_scratch_bytes(int64_t rows) {
+  return exponents_scratch_bytes(rows) + static_cast<size_t>(round_up(rows, 64)) * 2 + 512;
+}
+
+// Feature vector (39 floats) of op(A) (m x k) and op(B) (k x n) into feat.
+cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, int64_t hsa, const void* B,
+                            int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, const Plan& pl,
+                            float* feat, void* scratch, cudaStream_t st) {
+  const int64_t rmax = m > n ? m : n;
+  char* scr = static_cast<char*>(scratch);
+  int16_t* xdummy = reinterpret_cast<int16_t*>(scr + exponents_scratch_bytes(rmax));
+  unsigned long long* hist = reinterpret_cast<unsigned long long*>(
+      scr + exponents_scratch_bytes(rmax) + round_up(rmax, 64) * 2);
+  float* stats = reinterpret_cast<float*>(hist + 32);
+  cudaError_t e = cudaMemsetAsync(hist, 0, 32 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  e = single ? features_side<true>(A, m, k, rsa, hsa, pl, scr, hist, stats, xdummy, st)
+             : features_side<false>(A, m, k, rsa, hsa, pl, scr, hist, stats, xdummy, st);
+  if (e != cudaSuccess) return e;
+  e = single ? features_side<true>(B, n, k, rsb, hsb, pl, scr, hist + 16, stats + 2, xdummy, st)
+             : features_side<false>(B, n, k, rsb, hsb, pl, scr, hist + 16, stats + 2, xdummy, st);
+  if (e != cudaSuccess) return e;
+  const double ta = m > 0 && k > 0 ? 2.0 * m * k : 1.0, tb = n > 0 && k > 0 ? 2.0 * k * n : 1.0;
+  const float logk = static_cast<float>(std::log2(static_cast<double>(k > 1 ? k : 1)) / 17.0);
+  const float tgt = static_cast<float>(-std::log10(target) / 16.0);
+  feat_assemble_kernel<<<1, 64, 0, st>>>(hist, stats, ta, tb, logk, tgt, single ? 1.0f : 0.0f, feat);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 long long exp_seg_blocks(ExpSeg& g) {
   g.rows_contig = (g.rs == 1) ? 1 : 0;

@@ -59,6 +59,21 @@ _SIGS = [
                                    _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_ptr]),
     ("emu_cgemm_grouped", _c_int, [_c_int, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                    _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_ptr]),
+    ("emu_zgemm_tol", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_double),
+                               _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_double), _c_ptr, _c_i64,
+                               ctypes.c_double, ctypes.POINTER(_c_int), _c_ptr]),
+    ("emu_cgemm_tol", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
+                               _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr, _c_i64,
+                               ctypes.c_double, ctypes.POINTER(_c_int), _c_ptr]),
+    ("emu_moduli_apriori", _c_int, [_c_int, _c_i64, ctypes.c_double]),
+    ("emu_mlp_param_count", _c_int, []),
+    ("emu_mlp_set_weights", _c_int, [ctypes.POINTER(ctypes.c_float), _c_int]),
+    ("emu_moduli_features", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64, _c_ptr,
+                                     _c_i64, ctypes.c_double, _c_ptr, _c_ptr]),
+    ("emu_mlp_forward", _c_int, [_c_ptr, _c_ptr, _c_int, _c_ptr, _c_ptr]),
+    ("emu_mlp_backward", _c_int, [_c_ptr, _c_ptr, _c_ptr, _c_int, _c_ptr, _c_ptr, _c_ptr]),
+    ("emu_mlp_adam", _c_int, [_c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, ctypes.c_float, _c_ptr]),
+    ("emu_mlp_choose", _c_int, [_c_ptr, _c_ptr, ctypes.c_float, _c_ptr, _c_ptr]),
     ("emu_workspace_bytes", ctypes.c_size_t, [_c_int, _c_i64, _c_i64, _c_i64, _c_int]),
     ("emu_set_workspace", _c_int, [_c_ptr, ctypes.c_size_t]),
     ("emu_set_engine", _c_int, [_c_int, _c_int]),
@@ -221,6 +236,62 @@ def emu_zgemm_grouped(args, stream=None):
 
 def emu_cgemm_grouped(args, stream=None):
     return lib().emu_cgemm_grouped(*args.argv(), args.N, _stream(stream))
+
+
+def emu_zgemm_tol(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, target, stream=None):
+    """Returns (status, N used)."""
+    a = (ctypes.c_double * 2)(float(complex(alpha).real), float(complex(alpha).imag))
+    b = (ctypes.c_double * 2)(float(complex(beta).real), float(complex(beta).imag))
+    nu = _c_int(0)
+    st = lib().emu_zgemm_tol(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc, float(target),
+                             ctypes.byref(nu), _stream(stream))
+    return st, nu.value
+
+
+def emu_cgemm_tol(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, target, stream=None):
+    a = (ctypes.c_float * 2)(float(complex(alpha).real), float(complex(alpha).imag))
+    b = (ctypes.c_float * 2)(float(complex(beta).real), float(complex(beta).imag))
+    nu = _c_int(0)
+    st = lib().emu_cgemm_tol(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc, float(target),
+                             ctypes.byref(nu), _stream(stream))
+    return st, nu.value
+
+
+def emu_moduli_apriori(is_single, k, target):
+    return lib().emu_moduli_apriori(int(is_single), int(k), float(target))
+
+
+def emu_mlp_param_count():
+    return lib().emu_mlp_param_count()
+
+
+def emu_mlp_set_weights(params):
+    """params: sequence of floats (or None to unload)."""
+    if params is None:
+        return lib().emu_mlp_set_weights(None, 0)
+    arr = (ctypes.c_float * len(params))(*[float(v) for v in params])
+    return lib().emu_mlp_set_weights(arr, len(params))
+
+
+def emu_moduli_features(is_single, transa, transb, m, n, k, A, lda, B, ldb, target, features, stream=None):
+    return lib().emu_moduli_features(int(is_single), _op(transa), _op(transb), m, n, k, A, lda, B, ldb,
+                                     float(target), features, _stream(stream))
+
+
+def emu_mlp_forward(theta, X, batch, logits, stream=None):
+    return lib().emu_mlp_forward(theta, X, batch, logits, _stream(stream))
+
+
+def emu_mlp_backward(theta, X, Y, batch, grad, loss, stream=None):
+    return lib().emu_mlp_backward(theta, X, Y, batch, grad, loss, _stream(stream))
+
+
+def emu_mlp_adam(theta, grad, m, v, step, lr, stream=None):
+    return lib().emu_mlp_adam(theta, grad, m, v, int(step), float(lr), _stream(stream))
+
+
+def emu_mlp_choose(theta, features, threshold, n_out, stream=None):
+    return lib().emu_mlp_choose(theta, features, float(threshold), n_out, _stream(stream))
 
 
 def emu_workspace_bytes(is_single, m, n, k, num_moduli):

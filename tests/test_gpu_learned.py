@@ -1,0 +1,140 @@
+"""Learned moduli selection: the network's CUDA forward/backward/Adam kernels
+and its feature kernel against the CPU oracle, and the trained network on
+held-out inputs, judged by the oracle's exact product against the a priori
+rule."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+from oracle.emulate import emulate_entries
+from oracle.exact import complex_product_entries
+from oracle.metrics import abs_bound_entries, max_normalised_error
+from paper_2512_08321_gb300 import emu, moduli
+from paper_2512_08321_gb300.workloads import paper_matrix, paper_matrix_device
+
+from .helpers import dev
+
+pytestmark = pytest.mark.gpu
+
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _rand(seed, batch):
+    rng = np.random.default_rng(seed)
+    theta = (rng.standard_normal(omlp.n_params()) * 0.2).astype(np.float32)
+    X = rng.standard_normal((batch, omlp.N_IN)).astype(np.float32)
+    Y = (rng.random((batch, omlp.N_OUT)) > 0.5).astype(np.float32)
+    return theta, X, Y
+
+
+def test_forward_backward_adam_vs_oracle():
+    theta, X, Y = _rand(1, 300)
+    th, Xd, Yd = _cuda(theta), _cuda(X), _cuda(Y)
+    Z = torch.zeros((300, 21), dtype=torch.float32, device="cuda")
+    emu.check(emu.emu_mlp_forward(th.data_ptr(), Xd.data_ptr(), 300, Z.data_ptr()), "forward")
+    z_ref, cache = omlp.forward(theta.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(Z.cpu().numpy(), z_ref, rtol=1e-4, atol=1e-4)
+    g = torch.zeros(omlp.n_params(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    emu.check(emu.emu_mlp_backward(th.data_ptr(), Xd.data_ptr(), Yd.data_ptr(), 300, g.data_ptr(),
+                                   loss.data_ptr()), "backward")
+    g_ref = omlp.backward(theta.astype(np.float64), cache, z_ref, Y.astype(np.float64))
+    assert abs(float(loss.item()) - omlp.loss(z_ref, Y)) <= 1e-4 * omlp.loss(z_ref, Y)
+    gg = g.cpu().numpy()
+    assert np.allclose(gg, g_ref, rtol=2e-3, atol=2e-6), float(np.max(np.abs(gg - g_ref)))
+    # Adam at step 3 from non-zero moments
+    rng = np.random.default_rng(5)
+    m0 = (rng.standard_normal(omlp.n_params()) * 1e-3).astype(np.float32)
+    v0 = (rng.random(omlp.n_params()) * 1e-5).astype(np.float32)
+    md, vd = _cuda(m0), _cuda(v0)
+    emu.check(emu.emu_mlp_adam(th.data_ptr(), g.data_ptr(), md.data_ptr(), vd.data_ptr(), 3, 0.01), "adam")
+    t_ref, m_ref, v_ref = omlp.adam_step(theta.astype(np.float64), gg.astype(np.float64), m0.astype(np.float64),
+                                         v0.astype(np.float64), 3, lr=0.01)
+    assert np.allclose(th.cpu().numpy(), t_ref, rtol=1e-5, atol=1e-6)
+    assert np.allclose(md.cpu().numpy(), m_ref, rtol=1e-5, atol=1e-9)
+
+
+def test_choose_vs_oracle():
+    theta, X, _ = _rand(7, 40)
+    th = _cuda(theta)
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for i in range(40):
+        x = _cuda(X[i] * 0.5)
+        for thr in (0.5, 0.99):
+            emu.check(emu.emu_mlp_choose(th.data_ptr(), x.data_ptr(), thr, out.data_ptr()), "choose")
+            z, _ = omlp.forward(theta.astype(np.float64), (X[i] * 0.5)[None].astype(np.float64))
+            want = omlp.choose(z[0], thr)
+            got = int(out.item())
+            # decisions within float32 rounding of the threshold may differ
+            p = 1 / (1 + np.exp(-z[0]))
+            if np.min(np.abs(p - thr)) > 1e-4:
+                assert got == (want if want is not None else -1)
+
+
+@pytest.mark.parametrize("opA,opB,phi", [("N", "N", 0.5), ("T", "C", 3.0), ("C", "N", 1.5)])
+def test_features_vs_oracle(opA, opB, phi):
+    m, n, k = 90, 70, 300
+    A = paper_matrix(m, k, phi, 3) if opA == "N" else paper_matrix(k, m, phi, 3)
+    B = paper_matrix(k, n, phi, 4) if opB == "N" else paper_matrix(n, k, phi, 4)
+    A[..., 5] = 0                       # a zero row or column of op(A)
+    dA, dB = dev(A), dev(B)
+    f = torch.zeros(64, dtype=torch.float32, device="cuda")
+    emu.check(emu.emu_moduli_features(False, opA, opB, m, n, k, dA.data_ptr(), dA.shape[1], dB.data_ptr(),
+                                      dB.shape[1], 1e-10, f.data_ptr()), "features")
+    from oracle.emulate import apply_op
+    ref = omlp.features(apply_op(A, opA), apply_op(B, opB), 1e-10)
+    assert np.allclose(f[:39].cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+
+
+def test_learned_selection_gain_over_apriori():
+    """Held-out inputs (not in the training set: 2048^3 and 2048 x 256 x 4096,
+    phi in {0.5, 1.5, 3}): the network's N must meet every target by the oracle's
+    check on sampled entries; the table of N and errors against the a priori
+    rule is recorded.  The gain: fewer moduli where the a priori rule is safe,
+    and the target still met where the a priori rule misses it."""
+    moduli.load()
+    rows = []
+    rng = np.random.default_rng(11)
+    for (m, n, k) in ((2048, 2048, 2048), (2048, 256, 4096)):
+        for phi in (0.5, 1.5, 3.0):
+            A = paper_matrix_device(m, k, phi, 900 + int(10 * phi) + k, torch.complex128)
+            B = paper_matrix_device(k, n, phi, 901 + int(10 * phi) + k, torch.complex128)
+            C = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+            ri = rng.integers(0, m, 24)
+            ci = rng.integers(0, n, 24)
+            Ar = A[:, torch.from_numpy(ri).cuda()].t().cpu().numpy()
+            Bc = B[torch.from_numpy(ci).cuda(), :].t().cpu().numpy()
+            idx = np.arange(24)
+            exact = complex_product_entries(Ar, Bc, idx, idx)
+            bound = abs_bound_entries(Ar, Bc, idx, idx)
+            for T in (1e-6, 1e-10, 1e-15):
+                st, Nm = emu.emu_zgemm_tol("N", "N", m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 0.0,
+                                           C.data_ptr(), m, T)
+                emu.check(st, "emu_zgemm_tol")
+                torch.cuda.synchronize()
+                got = C[torch.from_numpy(ci).cuda(), torch.from_numpy(ri).cuda()].cpu().numpy()
+                want = emulate_entries(Ar, Bc, Nm, idx, idx)
+                assert np.array_equal(got.view(np.float64), want.view(np.float64))
+                err_m = max_normalised_error(got, exact, bound)
+                Na = emu.emu_moduli_apriori(False, k, T)
+                err_a = max_normalised_error(emulate_entries(Ar, Bc, Na, idx, idx), exact, bound)
+                rows.append(dict(m=m, n=n, k=k, phi=phi, target=T, N_learned=Nm, N_apriori=Na,
+                                 err_learned=err_m, err_apriori=err_a))
+    moduli.unload()
+    if os.path.isdir(OUT):
+        with open(os.path.join(OUT, "learned_moduli_heldout.json"), "w") as f:
+            json.dump(rows, f, indent=1)
+    print(json.dumps(rows))
+    assert all(r["err_learned"] <= r["target"] for r in rows), [r for r in rows if r["err_learned"] > r["target"]]
+    safe = [r for r in rows if r["err_apriori"] <= r["target"]]
+    saved = sum(r["N_apriori"] - r["N_learned"] for r in safe)
+    rescued = [r for r in rows if r["err_apriori"] > r["target"]]
+    assert saved > 0 or rescued
