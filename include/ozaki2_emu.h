@@ -207,6 +207,17 @@ emu_status_t emu_set_workspace(void* ptr, size_t bytes);
  * 64..960; 0 keeps the default 512). */
 emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 
+/* CRT reconstruction used by emu_zgemm, emu_cgemm and emu_stage_crt (the
+ * grouped path always uses the exact one):
+ *   EMU_CRT_EXACT (default): exact multi-limb integer reconstruction, result
+ *     RN(c' 2^-(x+y)) with c' = A'B' exactly;
+ *   EMU_CRT_PAPER_FP64: the paper's floating-point reconstruction (Section II,
+ *     eq. CRTaccumulation): S1 = sum s_l1 E'_l exact, S2 = sum s_l2 E'_l, then
+ *     mod(S1 + S2, P) in double-double (complex128) or double (complex64). */
+#define EMU_CRT_EXACT 0
+#define EMU_CRT_PAPER_FP64 1
+emu_status_t emu_set_crt_mode(int mode);
+
 /* ----------------------------------------------------- stage entry points --
  * The four phases of one emulated GEMM on caller buffers, for stage-wise
  * checking and for composing other pipelines.  is_single selects complex64

@@ -213,7 +213,8 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
     if (s != EMU_OK) return s;
     phase(3, st);
   }
-  s = cuda_status(launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st));
+  s = cuda_status(g_crt_mode == 1 ? launch_crt_fp(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st)
+                                  : launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st));
   phase(4, st);
   return s;
 }
@@ -389,8 +390,18 @@ emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli, 
     const double* b = static_cast<const double*>(beta);
     ar = a[0]; ai = a[1]; br = b[0]; bi = b[1];
   }
-  return emu::cuda_status(emu::launch_crt(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi,
-                                          C, ldc, static_cast<cudaStream_t>(stream)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return emu::cuda_status(emu::g_crt_mode == 1
+                              ? emu::launch_crt_fp(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
+                                                   ldc, st)
+                              : emu::launch_crt(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
+                                                ldc, st));
+}
+
+emu_status_t emu_set_crt_mode(int mode) {
+  if (mode != EMU_CRT_EXACT && mode != EMU_CRT_PAPER_FP64) return emu::bad(1);
+  emu::g_crt_mode = mode;
+  return EMU_OK;
 }
 
 int emu_last_bad_param(void) { return emu::t_bad_param; }

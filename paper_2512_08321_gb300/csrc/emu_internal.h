@@ -41,6 +41,11 @@ struct Plan {
   int nchunk;                             // 13-bit chunks covering every |a'| (< 2^(Emax+1))
   float w13[kMaxModuli][kMaxChunks];      // 2^(13 t) mod p_l, symmetric, as float
   float inv_p[kMaxModuli];                // 1 / p_l rounded to float
+  // the paper's floating-point CRT (Section II, eq. CRTaccumulation)
+  double s1[kMaxModuli];                  // upper bits of w_l on the common grid 2^g
+  double s2[kMaxModuli];                  // RN(w_l - s1_l)
+  double wd[kMaxModuli];                  // RN(w_l)
+  double Ph, Pl;                          // P = Ph + Pl, Ph = RN(P), Pl = RN(P - Ph)
 };
 
 // Host: build (and cache) the plan of N moduli; nullptr when N is out of range.
@@ -72,6 +77,11 @@ cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        const int8_t* res, int64_t ldr, const int16_t* x, const int16_t* y,
                        double ar, double ai, double br, double bi,
                        void* C, int64_t ldc, cudaStream_t st);
+
+cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
+                          const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
+                          int64_t ldc, cudaStream_t st);
+extern int g_crt_mode;   // 0: exact integer CRT, 1: the paper's floating-point CRT
 
 cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* status,
                                          cudaStream_t st);

@@ -244,6 +244,124 @@ cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const in
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The paper's floating-point reconstruction (Section II, eq. CRTaccumulation;
+// Section IV-A): S1 = sum s_l1 E'_l (exact on the common grid), S2 = sum s_l2 E'_l
+// (fma, ascending l), then c' = mod(S1 + S2, P) in double-double for complex128
+// and S - P rint(S/P) in double for complex64.  Every step is an explicit IEEE
+// intrinsic, in the same order as the oracle, so results are bitwise stable.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// c' from the accumulated sums: mod(S1 + S2, P) in double-double (complex128).
+__device__ __forceinline__ double fp_reduce_z(double S1, double S2, const Plan& pl) {
+  const double r = rint(__ddiv_rn(__dadd_rn(S1, S2), pl.Ph));
+  const double ph = __dmul_rn(r, pl.Ph);
+  const double pe = __fma_rn(r, pl.Ph, -ph);
+  double hi, lo;
+  two_sum(S1, -ph, hi, lo);
+  lo = __dadd_rn(__fma_rn(-r, pl.Pl, __dsub_rn(lo, pe)), S2);
+  return __dadd_rn(hi, lo);
+}
+
+// c' = S - P rint(S / P) in double (complex64).
+__device__ __forceinline__ double fp_reduce_c(double S, const Plan& pl) {
+  const double r = rint(__ddiv_rn(S, pl.Ph));
+  return __fma_rn(-r, pl.Ph, S);
+}
+
+// RN(c 2^e2) of a double c by integer operations (subnormal results round once).
+__device__ __forceinline__ double scale_double(double c, int e2) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(c));
+  const int ex = static_cast<int>((b >> 52) & 0x7FF);
+  if (ex == 0x7FF) return c;
+  const unsigned long long fr = b & 0xFFFFFFFFFFFFFull;
+  const unsigned long long mm = ex ? (fr | (1ull << 52)) : fr;
+  if (mm == 0) return c;
+  const int elsb = ex ? ex - 1075 : -1074;
+  uint32_t limbs[3];
+  limbs[0] = static_cast<uint32_t>(mm);
+  limbs[1] = static_cast<uint32_t>(mm >> 32);
+  limbs[2] = 0;
+  if (b >> 63) {  // two's complement negate for round_limbs
+    uint32_t carry = 1;
+    for (int t = 0; t < 3; ++t) {
+      const uint64_t v = static_cast<uint64_t>(~limbs[t]) + carry;
+      limbs[t] = static_cast<uint32_t>(v);
+      carry = static_cast<uint32_t>(v >> 32);
+    }
+  }
+  return round_limbs<3>(limbs, elsb + e2);
+}
+
+template <bool SINGLE>
+__global__ void __launch_bounds__(kThreads) crt_fp_kernel(int64_t m, int64_t n, const __grid_constant__ Plan pl,
+                                                          const int8_t* __restrict__ res, int64_t ldr,
+                                                          const int16_t* __restrict__ x, const int16_t* __restrict__ y,
+                                                          double ar, double ai, double br, double bi,
+                                                          void* __restrict__ Cv, int64_t ldc) {
+  const int64_t j = blockIdx.x;
+  const int64_t i = static_cast<int64_t>(blockIdx.y) * kThreads + threadIdx.x;
+  if (i >= m) return;
+  const int N = pl.N;
+  const int64_t js = n * ldr;
+  const int8_t* base = res + j * ldr + i;
+  // S1 = sum s_l1 E'_l (exact), S2 = sum s_l2 E'_l (fma), ascending l, both parts at once
+  double s1r = 0.0, s2r = 0.0, s1i = 0.0, s2i = 0.0;
+  for (int l = 0; l < N; ++l) {
+    const int p = pl.p[l];
+    const int d = base[(3 * l) * js], e = base[(3 * l + 1) * js], f = base[(3 * l + 2) * js];
+    const double er = static_cast<double>(sym_small(d - e, p));
+    const double ei = static_cast<double>(sym_small(f - d - e, p));
+    if (SINGLE) {
+      s1r = __fma_rn(pl.wd[l], er, s1r);
+      s1i = __fma_rn(pl.wd[l], ei, s1i);
+    } else {
+      s1r = __dadd_rn(s1r, __dmul_rn(pl.s1[l], er));
+      s1i = __dadd_rn(s1i, __dmul_rn(pl.s1[l], ei));
+      s2r = __fma_rn(pl.s2[l], er, s2r);
+      s2i = __fma_rn(pl.s2[l], ei, s2i);
+    }
+  }
+  const int xi = x[i], yj = y[j];
+  double orr, oi;
+  if (xi == kExpNonfinite || yj == kExpNonfinite) {
+    orr = oi = __longlong_as_double(0x7FF8000000000000ll);
+  } else {
+    const int e2 = -(xi + yj);
+    orr = scale_double(SINGLE ? fp_reduce_c(s1r, pl) : fp_reduce_z(s1r, s2r, pl), e2);
+    oi = scale_double(SINGLE ? fp_reduce_c(s1i, pl) : fp_reduce_z(s1i, s2i, pl), e2);
+  }
+  const int64_t ci = j * ldc + i;
+  if (!(ar == 1.0 && ai == 0.0 && br == 0.0 && bi == 0.0)) {
+    double tr = __fma_rn(ar, orr, -__dmul_rn(ai, oi));
+    double ti = __fma_rn(ar, oi, __dmul_rn(ai, orr));
+    if (!(br == 0.0 && bi == 0.0)) {
+      double cr, cim;
+      if (SINGLE) {
+        const float2 cv = static_cast<const float2*>(Cv)[ci];
+        cr = cv.x;
+        cim = cv.y;
+      } else {
+        const double2 cv = static_cast<const double2*>(Cv)[ci];
+        cr = cv.x;
+        cim = cv.y;
+      }
+      tr = __fma_rn(br, cr, __fma_rn(-bi, cim, tr));
+      ti = __fma_rn(br, cim, __fma_rn(bi, cr, ti));
+    }
+    orr = tr;
+    oi = ti;
+  }
+  if (SINGLE)
+    static_cast<float2*>(Cv)[ci] = make_float2(__double2float_rn(orr), __double2float_rn(oi));
+  else
+    static_cast<double2*>(Cv)[ci] = make_double2(orr, oi);
+}
+
 template <int L>
 cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long long blocks, const Plan& pl,
                              cudaStream_t st) {
@@ -274,6 +392,22 @@ cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob,
     case 6: return launch_grouped_l<6>(single, probs_dev, nprob, blocks, pl, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+int g_crt_mode = 0;
+
+cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
+                          const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
+                          int64_t ldc, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (n > 2147483647LL || (m + kThreads - 1) / kThreads > 65535) return cudaErrorInvalidValue;
+  dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + kThreads - 1) / kThreads));
+  if (single)
+    crt_fp_kernel<true><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  else
+    crt_fp_kernel<false><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,

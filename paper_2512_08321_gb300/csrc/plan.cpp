@@ -8,6 +8,7 @@
 // The CRT is evaluated exactly in L 32-bit limbs modulo 2^(32L) > 8|c'|:
 //   c' = sum_l w_l u_l + r' (2^(32L) - P) + K,  u_l = E'_l + 128,
 //   r' = r + R0 with r = round(S/P) and K = R0 P - 128 sum_l w_l.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -91,6 +92,47 @@ uint64_t extract64(const Big& a, int s) {  // floor(a / 2^s) truncated to 64 bit
   return r;
 }
 
+// Round a non-negative integer to the nearest double (ties to even).
+double big_to_double(const Big& a) {
+  const int b = bitlen(a);
+  if (b == 0) return 0.0;
+  if (b <= 64) {
+    uint64_t v = extract64(a, 0);
+    if (b <= 53) return static_cast<double>(v);
+    // round the 64-bit value: the conversion is RN
+    return static_cast<double>(v);
+  }
+  const int sh = b - 64;
+  uint64_t top = extract64(a, sh);
+  bool sticky = false;
+  for (int i = 0; i < sh; ++i)
+    if ((a.v[i / 32] >> (i % 32)) & 1u) sticky = true;
+  if (sticky) top |= 1u;                   // the 11 extra bits below the 53 keep the rounding correct
+  return std::ldexp(static_cast<double>(top), sh);
+}
+
+// Exact difference a - b of a non-negative Big and a double holding an integer, as a double (RN).
+double big_minus_double(const Big& a, double d) {
+  // d is an integer-valued double >= 0 with at most 53 significant bits
+  int e;
+  const double f = std::frexp(d, &e);                   // d = f 2^e, 0.5 <= f < 1
+  const uint64_t mant = static_cast<uint64_t>(std::ldexp(f, 53));
+  const int sh = e - 53;
+  Big bd(mant);
+  if (sh > 0) shl(bd, sh);
+  // compare a and bd
+  bool a_ge = true;
+  for (int i = kBigLimbs - 1; i >= 0; --i)
+    if (a.v[i] != bd.v[i]) {
+      a_ge = a.v[i] > bd.v[i];
+      break;
+    }
+  Big diff = a_ge ? a : bd;
+  sub(diff, a_ge ? bd : a);
+  const double r = big_to_double(diff);
+  return a_ge ? r : -r;
+}
+
 int gcd_int(int a, int b) {
   while (b) {
     int t = a % b;
@@ -152,6 +194,40 @@ void build(int N, Plan& pl) {
       pl.w13[l][t] = static_cast<float>(sr);
     }
     pl.inv_p[l] = static_cast<float>(1.0 / static_cast<double>(p));
+  }
+  // the paper's floating-point CRT: s1 on the grid 2^g, s2 = RN(w - s1)
+  {
+    int cl = 0;
+    while ((1 << cl) < N) ++cl;                                 // ceil(log2 N)
+    const int g = bitsP - (46 - cl);
+    for (int l = 0; l < N; ++l) {
+      Big w;
+      for (int t = 0; t < kMaxLimbs; ++t) w.v[t] = pl.w[l][t];
+      // w itself may need more limbs than L stores: recompute from P
+      w = P;
+      divmod_small(w, static_cast<uint32_t>(pl.p[l]));
+      uint32_t q = 0;
+      {
+        Big Mc = w;
+        const uint32_t mmod = divmod_small(Mc, static_cast<uint32_t>(pl.p[l]));
+        for (uint32_t t = 1; t < static_cast<uint32_t>(pl.p[l]); ++t)
+          if ((mmod * t) % static_cast<uint32_t>(pl.p[l]) == 1u) {
+            q = t;
+            break;
+          }
+      }
+      mul_small(w, q);
+      Big hi = w;
+      if (g > 0) {
+        // hi = floor(w / 2^g) 2^g
+        for (int i = 0; i < g; ++i) hi.v[i / 32] &= ~(1u << (i % 32));
+      }
+      pl.s1[l] = big_to_double(hi);                             // <= 46 significant bits: exact
+      pl.s2[l] = big_minus_double(w, pl.s1[l]);
+      pl.wd[l] = big_to_double(w);
+    }
+    pl.Ph = big_to_double(P);
+    pl.Pl = big_minus_double(P, pl.Ph);
   }
   // negP = 2^(32L) - P, K = R0 P - 128 sum w (mod 2^(32L))
   Big zero;

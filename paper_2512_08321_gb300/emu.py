@@ -77,6 +77,7 @@ _SIGS = [
     ("emu_workspace_bytes", ctypes.c_size_t, [_c_int, _c_i64, _c_i64, _c_i64, _c_int]),
     ("emu_set_workspace", _c_int, [_c_ptr, ctypes.c_size_t]),
     ("emu_set_engine", _c_int, [_c_int, _c_int]),
+    ("emu_set_crt_mode", _c_int, [_c_int]),
     ("emu_stage_exponents", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
                                      _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_ptr]),
     ("emu_stage_exponents_static", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
@@ -304,6 +305,13 @@ def emu_set_workspace(ptr, nbytes):
 
 def emu_set_engine(engine, chunk_k=0):
     return lib().emu_set_engine(int(engine), int(chunk_k))
+
+
+EMU_CRT_EXACT, EMU_CRT_PAPER_FP64 = 0, 1
+
+
+def emu_set_crt_mode(mode):
+    return lib().emu_set_crt_mode(int(mode))
 
 
 def emu_stage_exponents(is_single, transa, transb, m, n, k, A, lda, B, ldb, num_moduli, x, y, stream=None):

@@ -235,3 +235,25 @@ def test_bounded_wait_reports_timeout():
     # the context is still usable
     A = paper_matrix(8, 8, 0.5, 91)
     assert same_bits(run_gemm(A, A, 8), emulate(A, A, 8).out)
+
+
+@pytest.mark.parametrize("single,N", [(False, 14), (False, 20), (True, 7)])
+def test_paper_fp64_crt_bitexact(single, N):
+    """The paper's floating-point CRT (EMU_CRT_PAPER_FP64) against the oracle's
+    restatement of the same IEEE sequence, bit for bit, with alpha/beta."""
+    from oracle import crt_fp
+    m, n, k = 70, 45, 200
+    dt = np.complex64 if single else np.complex128
+    A = paper_matrix(m, k, 1.0, 301).astype(dt)
+    B = paper_matrix(k, n, 1.0, 302).astype(dt)
+    C = paper_matrix(m, n, 1.0, 303).astype(dt)
+    em = emulate(A.astype(np.complex128), B.astype(np.complex128), N, keep_residue_planes=False)
+    al, be = complex(0.5, -1.5), complex(2.0, 0.25)
+    want = crt_fp.outputs(em, single=single, alpha=(al.real, al.imag), beta=(be.real, be.imag),
+                          C_in=C.astype(np.complex128))
+    emu.check(emu.emu_set_crt_mode(emu.EMU_CRT_PAPER_FP64), "crt mode")
+    try:
+        got = run_gemm(A, B, N, alpha=al, beta=be, C=C, single=single)
+    finally:
+        emu.emu_set_crt_mode(emu.EMU_CRT_EXACT)
+    assert same_bits(got, want), mismatch_report(got, want)
