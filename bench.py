@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the unfused cuBLAS-INT8 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     return ap.parse_args()
 
 
@@ -238,6 +239,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    tuned = None
+    if not args.no_autotune:
+        st_t, tuned = emu.emu_autotune_gemm(single, m, n, k, N)
+        emu.check(st_t, "emu_autotune_gemm")
     for _ in range(args.warmup):
         step()
     barrier()
@@ -291,7 +296,9 @@ def main():
                       "io": "complex64" if single else "complex128", "num_moduli": N, "phi": wl["phi"],
                       "engine": "tcgen05 kind::f16 (exact residues), integer CRT",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
-                      "seed": wl["seed"]},
+                      "seed": wl["seed"],
+                      "tuning": dict(zip(["tile_n", "group", "chunk_k", "crt_rows", "split_elems"], tuned))
+                      if tuned else "defaults"},
            "roofline": roofline, "phases_ms": phases, "memory_phases": mem_phases,
            "gpu_launches": int(launches), "device_status": emu.STATUS_NAMES.get(status, status),
            "clocks": clk.summary()}

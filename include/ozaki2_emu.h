@@ -207,6 +207,30 @@ emu_status_t emu_set_workspace(void* ptr, size_t bytes);
  * 64..960; 0 keeps the default 512). */
 emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 
+/* Launch-configuration knobs of emu_zgemm/emu_cgemm (no effect on results):
+ *   EMU_TUNE_TILE_N      residue products: rows of op(A) per tile, 64/128/256
+ *   EMU_TUNE_GROUP       residue products: tile rasterisation group, 1..64
+ *   EMU_TUNE_CHUNK_K     residue products: k between in-TMEM reductions, 64..960, multiple of 64
+ *   EMU_TUNE_CRT_ROWS    CRT: rows per thread, 1/2/4
+ *   EMU_TUNE_SPLIT_ELEMS residue split: entries per thread, 2/4
+ * emu_set_tuning sets the process default; emu_autotune_gemm times the
+ * candidates of every knob for one shape on synthetic data (phases timed
+ * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
+ * use the winners.  The table is kept in the file EMU_AUTOTUNE_CACHE names, if
+ * set.  Tuning state is per process; emu_autotune_gemm allocates its own
+ * temporary buffers (inputs, planes, residues of the shape), synchronises, and
+ * frees them.  best (may be NULL) receives the 5 chosen values in key order. */
+#define EMU_TUNE_TILE_N 1
+#define EMU_TUNE_GROUP 2
+#define EMU_TUNE_CHUNK_K 3
+#define EMU_TUNE_CRT_ROWS 4
+#define EMU_TUNE_SPLIT_ELEMS 5
+emu_status_t emu_set_tuning(int key, int value);
+int emu_get_tuning(int key);
+emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli, int* best);
+/* Forget the autotuned entries (the defaults stay). */
+emu_status_t emu_autotune_clear(void);
+
 /* CRT reconstruction used by emu_zgemm, emu_cgemm and emu_stage_crt (the
  * grouped path always uses the exact one):
  *   EMU_CRT_EXACT (default): exact multi-limb integer reconstruction, result

@@ -41,7 +41,6 @@ void phase(int i, cudaStream_t st) {
   if (g_phase_on) cudaEventRecord(g_phase_ev[i], st);
 }
 emu_engine_t g_engine = EMU_ENGINE_AUTO;
-int g_chunk_k = 512;
 
 emu_status_t bad(int idx) {
   t_bad_param = idx;
@@ -150,11 +149,12 @@ emu_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? EMU_OK : EMU
 
 emu_status_t run_residue_gemm(emu_engine_t eng, int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                               const void* pa, const void* pb, int8_t* res, int64_t ldr,
-                              DeviceState* ds, cudaStream_t st) {
+                              DeviceState* ds, cudaStream_t st, const Tune& t) {
   if (eng == EMU_ENGINE_I8)
     return cuda_status(launch_gemm_i8(m, n, kpad, pl, static_cast<const int8_t*>(pa),
                                       static_cast<const int8_t*>(pb), res, ldr, st));
-  const cudaError_t e = launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, g_chunk_k, ds->status, st);
+  const cudaError_t e =
+      launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, t.chunk_k, ds->status, st, t.tile_n, t.group);
   if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
   return cuda_status(e);
 }
@@ -192,6 +192,7 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
   int64_t rsa, hsa, rsb, hsb;
   strides_a(ta, lda, rsa, hsa);
   strides_b(tb, ldb, rsb, hsb);
+  const Tune tn = tune_for(SINGLE, N, m, n, k);
   cudaError_t e;
   phase(0, st);
   if (k == 0) {
@@ -204,17 +205,20 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
     if ((e = launch_exponents(SINGLE, A, m, k, rsa, hsa, *pl, x, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = launch_exponents(SINGLE, B, n, k, rsb, hsb, *pl, y, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
     phase(1, st);
-    if ((e = launch_split(SINGLE, ta == EMU_OP_C, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st)) != cudaSuccess)
+    if ((e = launch_split(SINGLE, ta == EMU_OP_C, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st,
+                          tn.split_elems)) != cudaSuccess)
       return EMU_ERR_CUDA;
-    if ((e = launch_split(SINGLE, tb == EMU_OP_C, B, n, k, rsb, hsb, *pl, y, fp16, L.kpad, pb, st)) != cudaSuccess)
+    if ((e = launch_split(SINGLE, tb == EMU_OP_C, B, n, k, rsb, hsb, *pl, y, fp16, L.kpad, pb, st,
+                          tn.split_elems)) != cudaSuccess)
       return EMU_ERR_CUDA;
     phase(2, st);
-    s = run_residue_gemm(eng, m, n, L.kpad, *pl, pa, pb, res, L.ldr, ds, st);
+    s = run_residue_gemm(eng, m, n, L.kpad, *pl, pa, pb, res, L.ldr, ds, st, tn);
     if (s != EMU_OK) return s;
     phase(3, st);
   }
   s = cuda_status(g_crt_mode == 1 ? launch_crt_fp(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st)
-                                  : launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st));
+                                  : launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st,
+                                               tn.crt_rows));
   phase(4, st);
   return s;
 }
@@ -296,7 +300,7 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k) {
   if (engine != EMU_ENGINE_AUTO && engine != EMU_ENGINE_F16 && engine != EMU_ENGINE_I8) return emu::bad(1);
   if (chunk_k != 0 && (chunk_k < 64 || chunk_k > 960 || chunk_k % 64)) return emu::bad(2);
   emu::g_engine = engine;
-  if (chunk_k) emu::g_chunk_k = chunk_k;
+  if (chunk_k) emu::set_default_tuning(EMU_TUNE_CHUNK_K, chunk_k);
   return EMU_OK;
 }
 
@@ -362,7 +366,7 @@ emu_status_t emu_stage_residue_gemm(emu_engine_t engine, int64_t m, int64_t n, i
   if (s != EMU_OK) return s;
   const emu::Plan* pl = emu::get_plan(num_moduli);
   return emu::run_residue_gemm(emu::resolve(engine), m, n, kpad, *pl, planesA, planesB, residues, ldr, ds,
-                               static_cast<cudaStream_t>(stream));
+                               static_cast<cudaStream_t>(stream), emu::tune_for(false, num_moduli, m, n, kpad));
 }
 
 emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli, const int8_t* residues,

@@ -61,9 +61,23 @@ cudaError_t launch_exponents(bool single, const void* X, int64_t rows, int64_t k
                              void* scratch, cudaStream_t st);
 size_t exponents_scratch_bytes(int64_t rows);
 
+// Launch-configuration knobs of one GEMM (process defaults, autotuned per shape bucket).
+struct Tune {
+  int tile_n = 256;      // residue products: output rows per tile (64, 128, 256)
+  int group = 16;        // residue products: tile rasterisation group
+  int chunk_k = 512;     // residue products: k between in-TMEM reductions (64..960)
+  int crt_rows = 4;      // CRT: rows per thread (1, 2, 4)
+  int split_elems = 4;   // split: entries per thread (2, 4)
+};
+
+// Tuning of a call of this shape: the autotuned entry of its (dtype, N, shape
+// bucket) if one exists, else the process defaults (tune.cu).
+Tune tune_for(bool single, int N, int64_t m, int64_t n, int64_t k);
+void set_default_tuning(int key, int value);
+
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp,
-                         bool fp16, int64_t kpad, void* planes, cudaStream_t st);
+                         bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems = 4);
 
 cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                            const int8_t* planesA, const int8_t* planesB, int8_t* res,
@@ -71,12 +85,13 @@ cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
 
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                             const void* planesA, const void* planesB, int8_t* res,
-                            int64_t ldr, int chunk_k, unsigned int* status, cudaStream_t st);
+                            int64_t ldr, int chunk_k, unsigned int* status, cudaStream_t st,
+                            int tile_n = 256, int group = 16);
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        const int8_t* res, int64_t ldr, const int16_t* x, const int16_t* y,
                        double ar, double ai, double br, double bi,
-                       void* C, int64_t ldc, cudaStream_t st);
+                       void* C, int64_t ldc, cudaStream_t st, int rows_per_thread = 4);
 
 cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                           const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
@@ -151,7 +166,6 @@ cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, 
                             int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, const Plan& pl,
                             float* feat, void* scratch, cudaStream_t st);
 extern int g_f16_group;
-extern int g_f16_tile_n;
 
 // Launch accounting (api.cu): launchers report each kernel they enqueue.
 void count_launches(int n);

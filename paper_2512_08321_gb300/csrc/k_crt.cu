@@ -26,7 +26,6 @@ namespace emu {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kRowsPerThread = 4;
 
 __device__ __forceinline__ int sym_small(int v, int p) {   // |v| <= 3 p / 2 + 1
   if (2 * v >= p) v -= p;
@@ -108,7 +107,23 @@ __device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, co
   return round_limbs<L>(c, e2);
 }
 
-template <int L, bool SINGLE>
+// residue words of R consecutive rows: 8, 16 or 32 bits
+template <int R>
+struct Word;
+template <>
+struct Word<1> {
+  __device__ static uint32_t load(const int8_t* p) { return static_cast<uint8_t>(__ldg(p)); }
+};
+template <>
+struct Word<2> {
+  __device__ static uint32_t load(const int8_t* p) { return __ldg(reinterpret_cast<const unsigned short*>(p)); }
+};
+template <>
+struct Word<4> {
+  __device__ static uint32_t load(const int8_t* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+};
+
+template <int L, bool SINGLE, int kRowsPerThread>
 __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
                                           int64_t ldr, const int16_t* __restrict__ x, const int16_t* __restrict__ y,
                                           double ar, double ai, double br, double bi, void* __restrict__ Cv,
@@ -128,7 +143,7 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
 #pragma unroll
     for (int t = 0; t < L; ++t) accR[q][t] = accI[q][t] = pl.K[t];
   }
-  auto word = [&](int q) { return __ldg(reinterpret_cast<const unsigned int*>(base + q * job_stride)); };
+  auto word = [&](int q) { return Word<kRowsPerThread>::load(base + q * job_stride); };
   // the residue words of modulus l+1 are loaded while modulus l is processed
   uint32_t nd = word(0), ne = word(1), nf = word(2);
   for (int l = 0; l < N; ++l) {
@@ -203,7 +218,7 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
 }
 
 
-template <int L, bool SINGLE>
+template <int L, bool SINGLE, int R>
 __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
                                                        const __grid_constant__ Plan pl,
                                                        const int8_t* __restrict__ res, int64_t ldr,
@@ -211,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
                                                        const int16_t* __restrict__ y, double ar,
                                                        double ai, double br, double bi,
                                                        void* __restrict__ Cv, int64_t ldc) {
-  crt_block<L, SINGLE>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, Cv, ldc, blockIdx.x, blockIdx.y);
+  crt_block<L, SINGLE, R>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, Cv, ldc, blockIdx.x, blockIdx.y);
 }
 
 // one launch over every problem of a grouped call: blocks are (column, row block) of each problem
@@ -226,22 +241,34 @@ __global__ void __launch_bounds__(kThreads) crt_grouped(const CrtProb* __restric
   }
   const CrtProb& c = probs[lo];
   const long long local = b - c.block_begin;
-  crt_block<L, SINGLE>(c.m, c.n, pl, c.res, c.ldr, c.x, c.y, c.ar, c.ai, c.br, c.bi, c.C, c.ldc,
-                       local / c.iblocks, local % c.iblocks);
+  crt_block<L, SINGLE, 4>(c.m, c.n, pl, c.res, c.ldr, c.x, c.y, c.ar, c.ai, c.br, c.bi, c.C, c.ldc,
+                          local / c.iblocks, local % c.iblocks);
+}
+
+template <int L, int R>
+cudaError_t launch_lr(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
+                      const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
+                      int64_t ldc, cudaStream_t st) {
+  const int64_t per_block = static_cast<int64_t>(kThreads) * R;
+  if ((m + per_block - 1) / per_block > 65535) return cudaErrorInvalidValue;
+  dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + per_block - 1) / per_block));
+  if (single)
+    crt_kernel<L, true, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  else
+    crt_kernel<L, false, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 template <int L>
 cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                      int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
-                     double br, double bi, void* C, int64_t ldc, cudaStream_t st) {
-  const int64_t per_block = static_cast<int64_t>(kThreads) * kRowsPerThread;
-  dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + per_block - 1) / per_block));
-  if (single)
-    crt_kernel<L, true><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
-  else
-    crt_kernel<L, false><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
-  count_launches(1);
-  return cudaGetLastError();
+                     double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows) {
+  switch (rows) {
+    case 1: return launch_lr<L, 1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 2: return launch_lr<L, 2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    default: return launch_lr<L, 4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +402,7 @@ cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long 
 }  // namespace
 
 long long crt_prob_blocks(CrtProb& c) {
-  const int64_t per_block = static_cast<int64_t>(kThreads) * kRowsPerThread;
+  const int64_t per_block = static_cast<int64_t>(kThreads) * 4;
   c.iblocks = static_cast<int>((c.m + per_block - 1) / per_block);
   return static_cast<long long>(c.n) * c.iblocks;
 }
@@ -412,15 +439,15 @@ cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, con
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                        int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
-                       double br, double bi, void* C, int64_t ldc, cudaStream_t st) {
+                       double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  if (ldr % 16 || n > 2147483647LL || (m + 511) / 512 > 65535) return cudaErrorInvalidValue;
+  if (ldr % 16 || n > 2147483647LL) return cudaErrorInvalidValue;
   switch (pl.L) {
-    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
-    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
-    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
-    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
-    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
+    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
+    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
+    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
+    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -590,21 +590,20 @@ cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, co
 
 }  // namespace
 
-int g_f16_group = 16;   // tile rasterisation group (autotuned)
-int g_f16_tile_n = 256; // output rows per tile of the single-GEMM launch (256, 128 or 64)
+int g_f16_group = 16;   // tile rasterisation group of grouped launches
 
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                             const void* planesB, int8_t* res, int64_t ldr, int chunk_k, unsigned int* status,
-                            cudaStream_t st) {
+                            cudaStream_t st, int tile_n, int group) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (kpad % BK || ldr % 16 || chunk_k % BK || chunk_k < BK || chunk_k > 960) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u)
     return cudaErrorInvalidValue;
   if (!get_encoder()) return cudaErrorNotSupported;
-  switch (g_f16_tile_n) {
-    case 64: return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, g_f16_group, status, st);
-    case 128: return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, g_f16_group, status, st);
-    default: return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, g_f16_group, status, st);
+  switch (tile_n) {
+    case 64: return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st);
+    case 128: return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st);
+    default: return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st);
   }
 }
 

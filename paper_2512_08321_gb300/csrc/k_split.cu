@@ -30,7 +30,6 @@ namespace {
 constexpr int kTileR = 32;
 constexpr int kTileH = 32;
 constexpr int kThreads = 256;
-constexpr int kPerThread = 4;
 
 struct SplitSmem {
   uint64_t tre[kTileR][kTileH + 1];     // raw bits of the tile, [r][h], one element of padding
@@ -97,26 +96,40 @@ __device__ __forceinline__ uint32_t byte_of(float r) {
   return static_cast<uint32_t>(__float_as_int(r + 12582912.0f)) & 0xFFu;
 }
 
-template <typename T>
-struct Store4;
+// store E consecutive residues (exact small integers held as floats)
+template <typename T, int E>
+struct StoreE;
 template <>
-struct Store4<int8_t> {
-  __device__ static void put(int8_t* dst, const float (&v)[kPerThread]) {
+struct StoreE<int8_t, 4> {
+  __device__ static void put(int8_t* dst, const float (&v)[4]) {
     *reinterpret_cast<uint32_t*>(dst) = byte_of(v[0]) | (byte_of(v[1]) << 8) | (byte_of(v[2]) << 16) |
                                         (byte_of(v[3]) << 24);
   }
 };
 template <>
-struct Store4<__half> {
-  __device__ static void put(__half* dst, const float (&v)[kPerThread]) {
+struct StoreE<int8_t, 2> {
+  __device__ static void put(int8_t* dst, const float (&v)[2]) {
+    *reinterpret_cast<uint16_t*>(dst) = static_cast<uint16_t>(byte_of(v[0]) | (byte_of(v[1]) << 8));
+  }
+};
+template <>
+struct StoreE<__half, 4> {
+  __device__ static void put(__half* dst, const float (&v)[4]) {
     __half2 a = __floats2half2_rn(v[0], v[1]);
     __half2 b = __floats2half2_rn(v[2], v[3]);
     *reinterpret_cast<uint2*>(dst) =
         make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
   }
 };
+template <>
+struct StoreE<__half, 2> {
+  __device__ static void put(__half* dst, const float (&v)[2]) {
+    __half2 a = __floats2half2_rn(v[0], v[1]);
+    *reinterpret_cast<uint32_t*>(dst) = *reinterpret_cast<uint32_t*>(&a);
+  }
+};
 
-template <bool SINGLE, bool ROWS_CONTIG, typename T>
+template <bool SINGLE, bool ROWS_CONTIG, typename T, int kPerThread>
 __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restrict__ Xv, int64_t rows, int64_t k,
                                             int64_t rs, int64_t hs, bool conj, const int16_t* __restrict__ xexp,
                                             const Plan& pl, int64_t kpad, T* __restrict__ planes, int64_t rtile,
@@ -155,10 +168,16 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   }
   __syncthreads();
 
-  const int rr = tid >> 3;
-  const int hb = (tid & 7) * kPerThread;
+  // compute phase: each thread owns kPerThread consecutive h of one row; the
+  // block covers kTileR rows x kTileH h in 1024 / (256 kPerThread) passes
+  constexpr int kThreadsPerRow = kTileH / kPerThread;
+  constexpr int kRowsPerPass = kThreads / kThreadsPerRow;
+#pragma unroll 1
+  for (int pass = 0; pass < kTileR / kRowsPerPass; ++pass) {
+  const int rr = pass * kRowsPerPass + tid / kThreadsPerRow;
+  const int hb = (tid % kThreadsPerRow) * kPerThread;
   const int64_t r = r0 + rr;
-  if (r >= rows) return;
+  if (r >= rows) continue;
   const int x = xexp[r];
   const bool flagged = (x == kExpNonfinite);
   const int nch = pl.nchunk;
@@ -202,20 +221,22 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
       vs[j] = sr;
     }
     T* dst = base + static_cast<int64_t>(3 * l) * plane_stride;
-    Store4<T>::put(dst, vr);
-    Store4<T>::put(dst + plane_stride, vi);
-    Store4<T>::put(dst + 2 * plane_stride, vs);
+    StoreE<T, kPerThread>::put(dst, vr);
+    StoreE<T, kPerThread>::put(dst + plane_stride, vi);
+    StoreE<T, kPerThread>::put(dst + 2 * plane_stride, vs);
+  }
   }
 }
 
-template <bool SINGLE, bool ROWS_CONTIG, typename T>
+template <bool SINGLE, bool ROWS_CONTIG, typename T, int E>
 __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict__ Xv, int64_t rows,
                                                          int64_t k, int64_t rs, int64_t hs,
                                                          bool conj, const int16_t* __restrict__ xexp,
                                                          const __grid_constant__ Plan pl,
                                                          int64_t kpad, T* __restrict__ planes) {
   __shared__ SplitSmem sm;
-  split_block<SINGLE, ROWS_CONTIG, T>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x, blockIdx.y);
+  split_block<SINGLE, ROWS_CONTIG, T, E>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x,
+                                         blockIdx.y);
 }
 
 // one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
@@ -234,24 +255,26 @@ __global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __rest
   const int64_t rt = local / g.htiles, ht = local % g.htiles;
   T* planes = static_cast<T*>(g.planes);
   if (g.rows_contig)
-    split_block<SINGLE, true, T>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
+    split_block<SINGLE, true, T, 4>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
   else
-    split_block<SINGLE, false, T>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
+    split_block<SINGLE, false, T, 4>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
 }
 
 template <bool SINGLE, typename T>
 cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                      const Plan& pl, const int16_t* xexp, int64_t kpad, void* planes,
-                     cudaStream_t st) {
+                     cudaStream_t st, int elems) {
   if ((rows + kTileR - 1) / kTileR > 2147483647LL || kpad / kTileH > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>((rows + kTileR - 1) / kTileR),
             static_cast<unsigned int>(kpad / kTileH));
-  if (rs == 1)
-    split_kernel<SINGLE, true, T><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl,
-                                                             kpad, static_cast<T*>(planes));
-  else
-    split_kernel<SINGLE, false, T><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl,
-                                                              kpad, static_cast<T*>(planes));
+  T* P = static_cast<T*>(planes);
+  if (elems == 2) {
+    if (rs == 1) split_kernel<SINGLE, true, T, 2><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    else split_kernel<SINGLE, false, T, 2><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+  } else {
+    if (rs == 1) split_kernel<SINGLE, true, T, 4><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    else split_kernel<SINGLE, false, T, 4><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+  }
   count_launches(1);
   return cudaGetLastError();
 }
@@ -282,14 +305,14 @@ cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_de
 
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp, bool fp16,
-                         int64_t kpad, void* planes, cudaStream_t st) {
+                         int64_t kpad, void* planes, cudaStream_t st, int elems) {
   if (rows <= 0 || kpad <= 0) return cudaSuccess;
   if (kpad % 64) return cudaErrorInvalidValue;
   if (single)
-    return fp16 ? launch_t<true, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st)
-                : launch_t<true, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st);
-  return fp16 ? launch_t<false, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st)
-              : launch_t<false, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st);
+    return fp16 ? launch_t<true, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems)
+                : launch_t<true, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems);
+  return fp16 ? launch_t<false, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems)
+              : launch_t<false, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems);
 }
 
 }  // namespace emu

@@ -1,0 +1,315 @@
+// Autotuner of the single-GEMM launch configuration.  For one problem shape it
+// times, on synthetic data of that shape and with CUDA events, every
+// candidate of each phase's knobs (the phases are independent, so each is
+// timed on its own): the residue-product tile width, rasterisation group and
+// reduction chunk; the CRT rows per thread; the split entries per thread.  The
+// winners are kept per (dtype, N, ceil(log2) of m, n, k) and used by later
+// calls in that bucket; EMU_AUTOTUNE_CACHE names a file that keeps the table
+// across processes.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "emu_internal.h"
+
+namespace emu {
+namespace {
+
+using Key = std::tuple<int, int, int, int, int>;
+
+std::mutex g_mu;
+Tune g_default;
+std::map<Key, Tune> g_table;
+bool g_loaded = false;
+
+int bucket(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << b) < v && b < 62) ++b;
+  return b;
+}
+
+Key key_of(bool single, int N, int64_t m, int64_t n, int64_t k) {
+  return Key(single ? 1 : 0, N, bucket(m), bucket(n), bucket(k));
+}
+
+void load_locked() {
+  if (g_loaded) return;
+  g_loaded = true;
+  const char* path = std::getenv("EMU_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char tag[64];
+  int s, N, bm, bn, bk;
+  Tune t;
+  while (std::fscanf(f, "%63s", tag) == 1) {
+    if (std::string(tag) != "gemm") {   // other tables share the file: skip the line
+      int c;
+      while ((c = std::fgetc(f)) != EOF && c != '\n') {
+      }
+      continue;
+    }
+    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n, &t.group, &t.chunk_k,
+                    &t.crt_rows, &t.split_elems) != 10)
+      break;
+    g_table[Key(s, N, bm, bn, bk)] = t;
+  }
+  std::fclose(f);
+}
+
+void save_locked() {
+  const char* path = std::getenv("EMU_AUTOTUNE_CACHE");
+  if (!path) return;
+  // keep lines of other tables that share the file
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(path, "r")) {
+    char line[4096];
+    while (std::fgets(line, sizeof(line), f))
+      if (std::string(line).rfind("gemm ", 0) != 0) keep.push_back(line);
+    std::fclose(f);
+  }
+  FILE* f = std::fopen(path, "w");
+  if (!f) return;
+  for (const auto& l : keep) std::fputs(l.c_str(), f);
+  for (const auto& kv : g_table) {
+    const Key& k = kv.first;
+    const Tune& t = kv.second;
+    std::fprintf(f, "gemm %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                 std::get<3>(k), std::get<4>(k), t.tile_n, t.group, t.chunk_k, t.crt_rows, t.split_elems);
+  }
+  std::fclose(f);
+}
+
+bool valid(int key, int v) {
+  switch (key) {
+    case EMU_TUNE_TILE_N: return v == 64 || v == 128 || v == 256;
+    case EMU_TUNE_GROUP: return v >= 1 && v <= 64;
+    case EMU_TUNE_CHUNK_K: return v >= 64 && v <= 960 && v % 64 == 0;
+    case EMU_TUNE_CRT_ROWS: return v == 1 || v == 2 || v == 4;
+    case EMU_TUNE_SPLIT_ELEMS: return v == 2 || v == 4;
+    default: return false;
+  }
+}
+
+void set(Tune& t, int key, int v) {
+  switch (key) {
+    case EMU_TUNE_TILE_N: t.tile_n = v; break;
+    case EMU_TUNE_GROUP: t.group = v; break;
+    case EMU_TUNE_CHUNK_K: t.chunk_k = v; break;
+    case EMU_TUNE_CRT_ROWS: t.crt_rows = v; break;
+    case EMU_TUNE_SPLIT_ELEMS: t.split_elems = v; break;
+    default: break;
+  }
+}
+
+// synthetic inputs for timing: (u - 1/2) 2^(s) with u and s from a hash of the index
+__global__ void fill_kernel(double* p, int64_t count) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint64_t h = static_cast<uint64_t>(i) * 0x9E3779B97F4A7C15ull;
+  h ^= h >> 29;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 32;
+  const double u = static_cast<double>(h & 0xFFFFFFull) * (1.0 / 16777216.0) - 0.5;
+  const int s = static_cast<int>((h >> 24) & 7) - 3;
+  p[i] = u * static_cast<double>(1 << (s + 3)) * 0.125;
+}
+
+__global__ void fill_kernel_f(float* p, int64_t count) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint64_t h = static_cast<uint64_t>(i) * 0x9E3779B97F4A7C15ull;
+  h ^= h >> 29;
+  h *= 0xBF58476D1CE4E5B9ull;
+  h ^= h >> 32;
+  p[i] = static_cast<float>(static_cast<double>(h & 0xFFFFFFull) * (1.0 / 16777216.0) - 0.5);
+}
+
+// Time fn() on st: one warm-up, then the minimum of `reps` runs (ms).
+template <class F>
+float time_min(cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int reps, F fn) {
+  fn();
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, st);
+    fn();
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) best = ms;
+  }
+  return best;
+}
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+Tune tune_for(bool single, int N, int64_t m, int64_t n, int64_t k) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  load_locked();
+  auto it = g_table.find(key_of(single, N, m, n, k));
+  return it != g_table.end() ? it->second : g_default;
+}
+
+void set_default_tuning(int key, int value) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (valid(key, value)) set(g_default, key, value);
+}
+
+}  // namespace emu
+
+extern "C" {
+
+emu_status_t emu_set_tuning(int key, int value) {
+  if (!emu::valid(key, value)) return EMU_ERR_INVALID_ARG;
+  emu::set_default_tuning(key, value);
+  return EMU_OK;
+}
+
+int emu_get_tuning(int key) {
+  std::lock_guard<std::mutex> lk(emu::g_mu);
+  const emu::Tune& t = emu::g_default;
+  switch (key) {
+    case EMU_TUNE_TILE_N: return t.tile_n;
+    case EMU_TUNE_GROUP: return t.group;
+    case EMU_TUNE_CHUNK_K: return t.chunk_k;
+    case EMU_TUNE_CRT_ROWS: return t.crt_rows;
+    case EMU_TUNE_SPLIT_ELEMS: return t.split_elems;
+    default: return -1;
+  }
+}
+
+emu_status_t emu_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(emu::g_mu);
+  emu::g_table.clear();
+  return EMU_OK;
+}
+
+emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli, int* best) {
+  using namespace emu;
+  if (m <= 0 || n <= 0 || k <= 0 || k > EMU_MAX_K) return EMU_ERR_INVALID_ARG;
+  if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
+  unsigned int* status = device_status_ptr();
+  if (!status) return EMU_ERR_UNSUPPORTED;
+  const bool single = is_single != 0;
+  const Plan* pl = get_plan(num_moduli);
+  const int J = 3 * num_moduli;
+  const int64_t kpad = round_up(k, 64), ldr = round_up(m, 16);
+  const size_t esz = single ? 8 : 16;
+  // one buffer: A, B, x, y, exponent scratch, fp16 planes, residues, C
+  size_t o = 0;
+  const size_t oA = o; o += al(esz * static_cast<size_t>(m) * k);
+  const size_t oB = o; o += al(esz * static_cast<size_t>(k) * n);
+  const size_t ox = o; o += al(2 * static_cast<size_t>(m));
+  const size_t oy = o; o += al(2 * static_cast<size_t>(n));
+  const size_t os = o; o += al(exponents_scratch_bytes(m > n ? m : n));
+  const size_t opa = o; o += al(static_cast<size_t>(J) * m * kpad * 2);
+  const size_t opb = o; o += al(static_cast<size_t>(J) * n * kpad * 2);
+  const size_t ores = o; o += al(static_cast<size_t>(J) * n * ldr);
+  const size_t oC = o; o += al(esz * static_cast<size_t>(m) * n);
+  char* M = nullptr;
+  if (cudaMalloc(&M, o) != cudaSuccess) {
+    cudaGetLastError();
+    return EMU_ERR_ALLOC;
+  }
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+  const int64_t cntA = 2 * m * k, cntB = 2 * k * n;   // complex128: 2 doubles per entry
+  if (ok && !single) {
+    fill_kernel<<<static_cast<unsigned int>((cntA + 255) / 256), 256, 0, st>>>(reinterpret_cast<double*>(M + oA), cntA);
+    fill_kernel<<<static_cast<unsigned int>((cntB + 255) / 256), 256, 0, st>>>(reinterpret_cast<double*>(M + oB), cntB);
+  } else if (ok) {
+    const int64_t fa = 2 * m * k, fb = 2 * k * n;   // complex64: 2 floats per entry
+    fill_kernel_f<<<static_cast<unsigned int>((fa + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(M + oA), fa);
+    fill_kernel_f<<<static_cast<unsigned int>((fb + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(M + oB), fb);
+  }
+  int16_t* x = reinterpret_cast<int16_t*>(M + ox);
+  int16_t* y = reinterpret_cast<int16_t*>(M + oy);
+  Tune t = tune_for(single, num_moduli, m, n, k);
+  if (ok) {
+    ok = launch_exponents(single, M + oA, m, k, 1, m, *pl, x, M + os, st) == cudaSuccess &&
+         launch_exponents(single, M + oB, n, k, k, 1, *pl, y, M + os, st) == cudaSuccess;
+  }
+  const int reps = (static_cast<double>(m) * n * k > 1e12) ? 2 : 3;
+  if (ok) {
+    // split: entries per thread
+    float bt = 1e30f;
+    for (int e : {4, 2}) {
+      const float ms = time_min(st, a, b, reps, [&] {
+        launch_split(single, false, M + oA, m, k, 1, m, *pl, x, true, kpad, M + opa, st, e);
+        launch_split(single, false, M + oB, n, k, k, 1, *pl, y, true, kpad, M + opb, st, e);
+      });
+      if (ms < bt) {
+        bt = ms;
+        t.split_elems = e;
+      }
+    }
+    // residue products: tile width x group x chunk
+    bt = 1e30f;
+    const bool big = static_cast<double>(m) * n * k * num_moduli > 4e13;
+    const std::vector<int> tiles = m <= 256 ? std::vector<int>{64, 128, 256} : std::vector<int>{128, 256};
+    const std::vector<int> groups = big ? std::vector<int>{16, 32} : std::vector<int>{8, 16, 32};
+    const std::vector<int> chunks = big ? std::vector<int>{512} : std::vector<int>{512, 960};
+    if (prepare_gemm_f16() != cudaSuccess) ok = false;
+    for (int tn : tiles)
+      for (int g : groups)
+        for (int c : chunks) {
+          if (!ok) break;
+          const float ms = time_min(st, a, b, reps, [&] {
+            launch_gemm_f16(m, n, kpad, *pl, M + opa, M + opb, reinterpret_cast<int8_t*>(M + ores), ldr, c, status,
+                            st, tn, g);
+          });
+          if (ms < bt) {
+            bt = ms;
+            t.tile_n = tn;
+            t.group = g;
+            t.chunk_k = c;
+          }
+        }
+    // CRT: rows per thread
+    bt = 1e30f;
+    for (int r : {4, 2, 1}) {
+      const float ms = time_min(st, a, b, reps, [&] {
+        launch_crt(single, m, n, *pl, reinterpret_cast<int8_t*>(M + ores), ldr, x, y, 1.0, 0.0, 0.0, 0.0, M + oC, m,
+                   st, r);
+      });
+      if (ms < bt) {
+        bt = ms;
+        t.crt_rows = r;
+      }
+    }
+    ok = cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  if (b) cudaEventDestroy(b);
+  if (a) cudaEventDestroy(a);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(M);
+  if (!ok) {
+    cudaGetLastError();
+    return EMU_ERR_CUDA;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    g_table[key_of(single, num_moduli, m, n, k)] = t;
+    save_locked();
+  }
+  if (best) {
+    best[0] = t.tile_n;
+    best[1] = t.group;
+    best[2] = t.chunk_k;
+    best[3] = t.crt_rows;
+    best[4] = t.split_elems;
+  }
+  return EMU_OK;
+}
+
+}  // extern "C"

@@ -78,6 +78,10 @@ _SIGS = [
     ("emu_set_workspace", _c_int, [_c_ptr, ctypes.c_size_t]),
     ("emu_set_engine", _c_int, [_c_int, _c_int]),
     ("emu_set_crt_mode", _c_int, [_c_int]),
+    ("emu_set_tuning", _c_int, [_c_int, _c_int]),
+    ("emu_get_tuning", _c_int, [_c_int]),
+    ("emu_autotune_gemm", _c_int, [_c_int, _c_i64, _c_i64, _c_i64, _c_int, ctypes.POINTER(_c_int)]),
+    ("emu_autotune_clear", _c_int, []),
     ("emu_stage_exponents", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
                                      _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_ptr]),
     ("emu_stage_exponents_static", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
@@ -308,6 +312,26 @@ def emu_set_engine(engine, chunk_k=0):
 
 
 EMU_CRT_EXACT, EMU_CRT_PAPER_FP64 = 0, 1
+EMU_TUNE_TILE_N, EMU_TUNE_GROUP, EMU_TUNE_CHUNK_K, EMU_TUNE_CRT_ROWS, EMU_TUNE_SPLIT_ELEMS = 1, 2, 3, 4, 5
+
+
+def emu_set_tuning(key, value):
+    return lib().emu_set_tuning(int(key), int(value))
+
+
+def emu_get_tuning(key):
+    return lib().emu_get_tuning(int(key))
+
+
+def emu_autotune_gemm(is_single, m, n, k, num_moduli):
+    """Returns (status, [tile_n, group, chunk_k, crt_rows, split_elems])."""
+    best = (_c_int * 5)()
+    st = lib().emu_autotune_gemm(int(is_single), m, n, k, num_moduli, best)
+    return st, list(best)
+
+
+def emu_autotune_clear():
+    return lib().emu_autotune_clear()
 
 
 def emu_set_crt_mode(mode):
