@@ -116,4 +116,22 @@ def outputs(em, single=False, alpha=(1.0, 0.0), beta=(0.0, 0.0), C_in=None):
     return o.astype(np.complex64) if single else o
 
 
-__all__ = ["split_weights", "reconstruct_z", "reconstruct_c", "outputs", "Plan"]
+def outputs_real(em, single=False, alpha=1.0, beta=0.0, C_in=None):
+    """Steps V-v..VI of the floating-point CRT for a real emulation `em`
+    (oracle.emulate_real.RealEmulation): the DGEMM form (S1 + S2, double-double
+    reduction) for binary64 output, the single double sum for binary32."""
+    from .emulate_real import finish_real
+    plan = em.plan
+    rec = reconstruct_c if single else reconstruct_z
+    o = np.zeros((em.m, em.n), dtype=np.float64)
+    for i in range(em.m):
+        for j in range(em.n):
+            if em.flag_a[i] or em.flag_b[j]:
+                o[i, j] = np.nan
+                continue
+            c = rec([int(v) for v in em.Eprime[:, i, j]], plan)
+            o[i, j] = unscale(c, -(int(em.x[i]) + int(em.y[j])))
+    return finish_real(o, alpha, beta, C_in, fp.BINARY32 if single else fp.BINARY64)
+
+
+__all__ = ["split_weights", "reconstruct_z", "reconstruct_c", "outputs", "outputs_real", "Plan"]

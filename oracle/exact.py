@@ -91,3 +91,14 @@ def complex_product_entries(A, B, rows, cols):
         im = math.fsum(np.concatenate([p3, e3, p4, e4]))
         out[t] = complex(re, im)
     return out
+
+
+def real_product_entries(A, B, rows, cols):
+    """Correctly rounded (AB)_ij of real matrices at (rows[t], cols[t])."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    out = np.zeros(len(rows), dtype=np.float64)
+    for t, (i, j) in enumerate(zip(rows, cols)):
+        p, e = _two_product(A[i].copy(), B[:, j].copy())
+        out[t] = math.fsum(np.concatenate([p, e]))
+    return out

@@ -51,3 +51,25 @@ def paper_matrix_device(rows, cols, phi, seed, dtype, device="cuda"):
         n = torch.randn((cols, rows), generator=g, device=device, dtype=real_t)
         parts.append((u - 0.5) * torch.exp(n * phi))
     return torch.complex(parts[0], parts[1])
+
+
+def paper_matrix_real(rows, cols, phi, seed, dtype=np.float64):
+    """rows x cols real matrix, entries (U(0,1] - 0.5) * exp(phi * N(0,1)),
+    column-major."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    u = 1.0 - rng.random((rows, cols))
+    g = rng.standard_normal((rows, cols))
+    return np.asfortranarray(((u - 0.5) * np.exp(g * phi)).astype(dtype))
+
+
+def paper_matrix_real_device(rows, cols, phi, seed, dtype, device="cuda"):
+    """Same distribution as paper_matrix_real, drawn on the GPU; returns the
+    column-major rows x cols matrix as a C-contiguous (cols x rows) tensor."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    single = dtype in (np.float32, "float32", torch.float32)
+    real_t = torch.float32 if single else torch.float64
+    u = 1.0 - torch.rand((cols, rows), generator=g, device=device, dtype=real_t)
+    n = torch.randn((cols, rows), generator=g, device=device, dtype=real_t)
+    return (u - 0.5) * torch.exp(n * phi)
