@@ -9,6 +9,8 @@ IV-A, drawn on the GPU from a fixed seed):
   zgemm16384  complex128, m = n = k = 16384, phi = 1, N = 15 moduli (default; the
               fewest moduli whose error is no worse than native cuBLAS ZGEMM here)
   cgemm8192   complex64,  m = n = k = 8192,  phi = 0.5, N = 8 moduli
+  dgemm16384  float64, m = n = k = 16384, phi = 1 (the paper's real-valued comparison)
+  sgemm16384  float32, m = n = k = 16384, phi = 0.5
 
 Inputs are larger than L2 (8.6 GB / 1.1 GB), so no flush is needed between
 steps.  `--impl reference` times the CPU oracle on a bounded sample of the
@@ -28,9 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "emulated ZGEMM/CGEMM TFLOPS (8mnk/s) vs cuBLAS native at matched accuracy"
+METRIC_REAL = "emulated DGEMM/SGEMM TFLOPS (2mnk/s) vs cuBLAS native at matched accuracy"
 WORKLOADS = {
     "zgemm16384": dict(single=False, m=16384, n=16384, k=16384, phi=1.0, N=15, seed=20251208),
     "cgemm8192": dict(single=True, m=8192, n=8192, k=8192, phi=0.5, N=8, seed=20251209),
+    # real matrices (one residue product per modulus)
+    "dgemm16384": dict(single=False, real=True, m=16384, n=16384, k=16384, phi=1.0, N=16, seed=20251215),
+    "sgemm16384": dict(single=True, real=True, m=16384, n=16384, k=16384, phi=0.5, N=8, seed=20251216),
     # 512 uneven problems, m, n, k log-uniform in [64, 2048]: one grouped plan replayed from a CUDA graph
     "grouped512": dict(single=False, grouped=True, count=512, lo=64, hi=2048, phi=1.0, N=16, seed=20251212,
                        m=0, n=0, k=0),
@@ -129,23 +135,36 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle (CPU baseline only)
+def flops_per_entry(wl):
+    """Real flops of one output entry per unit of k: 8 complex, 2 real."""
+    return 2.0 if wl.get("real") else 8.0
+
+
 def cpu_baseline(wl, repeat=1):
     """The CPU oracle as it stands, timed on a CPU_SAMPLE x CPU_SAMPLE output block
     of the workload at full k; throughput in the metric's unit (TFLOPS)."""
     import numpy as np
-    from oracle.emulate import emulate
-    from paper_2512_08321_gb300.workloads import paper_matrix
+    from paper_2512_08321_gb300.workloads import paper_matrix, paper_matrix_real
     s = CPU_SAMPLE
-    dt = np.complex64 if wl["single"] else np.complex128
-    A = paper_matrix(s, wl["k"], wl["phi"], wl["seed"], dt).astype(np.complex128)
-    B = paper_matrix(wl["k"], s, wl["phi"], wl["seed"] + 1, dt).astype(np.complex128)
+    if wl.get("real"):
+        from oracle.emulate_real import RealEmulation
+        dt = np.float32 if wl["single"] else np.float64
+        A = paper_matrix_real(s, wl["k"], wl["phi"], wl["seed"], dt).astype(np.float64)
+        B = paper_matrix_real(wl["k"], s, wl["phi"], wl["seed"] + 1, dt).astype(np.float64)
+        run = lambda: RealEmulation(A, B, wl["N"])
+    else:
+        from oracle.emulate import emulate
+        dt = np.complex64 if wl["single"] else np.complex128
+        A = paper_matrix(s, wl["k"], wl["phi"], wl["seed"], dt).astype(np.complex128)
+        B = paper_matrix(wl["k"], s, wl["phi"], wl["seed"] + 1, dt).astype(np.complex128)
+        run = lambda: emulate(A, B, wl["N"], keep_residue_planes=False)
     times = []
     for _ in range(repeat):
         t0 = time.perf_counter()
-        emulate(A, B, wl["N"], keep_residue_planes=False)
+        run()
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
-    return {"value": 8.0 * s * s * wl["k"] / t * 1e-12, "unit": "TFLOPS", "cores": os.cpu_count(),
+    return {"value": flops_per_entry(wl) * s * s * wl["k"] / t * 1e-12, "unit": "TFLOPS", "cores": os.cpu_count(),
             "kind": "oracle", "seconds_per_sample": t,
             "sample": f"{s}x{s} output block of the {wl['m']}x{wl['n']}x{wl['k']} workload at full k "
                       f"(N={wl['N']}, numpy float64 BLAS for the residue products, Python integers for the CRT)"}
@@ -160,10 +179,10 @@ def run_reference(args, wl, rank):
         if i >= args.warmup:
             steps.append(r)
     t = statistics.mean(x["seconds_per_sample"] for x in steps)
-    value = 8.0 * CPU_SAMPLE * CPU_SAMPLE * wl["k"] / t * 1e-12
+    value = flops_per_entry(wl) * CPU_SAMPLE * CPU_SAMPLE * wl["k"] / t * 1e-12
     cb = dict(steps[-1])
     cb["value"] = value
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": args.gpus,
+    out = {"impl": "reference", "metric": METRIC_REAL if wl.get("real") else METRIC, "value": value, "unit": "TFLOPS", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int", "data": "synthetic",
            "config": {"workload": args.workload, "m": wl["m"], "n": wl["n"], "k": wl["k"], "num_moduli": wl["N"],
@@ -211,7 +230,7 @@ def main():
 
     import torch
     from paper_2512_08321_gb300 import emu
-    from paper_2512_08321_gb300.workloads import paper_matrix_device
+    from paper_2512_08321_gb300.workloads import paper_matrix_device, paper_matrix_real_device
 
     torch.cuda.set_device(local)
     dist = None
@@ -221,13 +240,23 @@ def main():
     emu.lib()
     m, n, k, N = wl["m"], wl["n"], wl["k"], wl["N"]
     single = wl["single"]
-    cdt = torch.complex64 if single else torch.complex128
-    esz = 8 if single else 16
-    A = paper_matrix_device(m, k, wl["phi"], wl["seed"] + 1000 * rank, cdt)   # (k, m): lda = m
-    B = paper_matrix_device(k, n, wl["phi"], wl["seed"] + 1 + 1000 * rank, cdt)
+    real = bool(wl.get("real"))
+    ppm = 1 if real else 3                      # residue products per modulus
+    if real:
+        cdt = torch.float32 if single else torch.float64
+        gen = paper_matrix_real_device
+        f = emu.emu_sgemm if single else emu.emu_dgemm
+        dtype_code = emu.EMU_DTYPE_S if single else emu.EMU_DTYPE_D
+    else:
+        cdt = torch.complex64 if single else torch.complex128
+        gen = paper_matrix_device
+        f = emu.emu_cgemm if single else emu.emu_zgemm
+        dtype_code = emu.EMU_DTYPE_C if single else emu.EMU_DTYPE_Z
+    esz = torch.empty((), dtype=cdt).element_size()
+    A = gen(m, k, wl["phi"], wl["seed"] + 1000 * rank, cdt)   # (k, m): lda = m
+    B = gen(k, n, wl["phi"], wl["seed"] + 1 + 1000 * rank, cdt)
     C = torch.zeros((n, m), dtype=cdt, device="cuda")
     st = torch.cuda.current_stream()
-    f = emu.emu_cgemm if single else emu.emu_zgemm
 
     def step(a=A, b=B, c=C):
         s = f("N", "N", m, n, k, 1.0, a.data_ptr(), m, b.data_ptr(), k, 0.0, c.data_ptr(), m, N, st)
@@ -241,7 +270,7 @@ def main():
 
     tuned = None
     if not args.no_autotune:
-        st_t, tuned = emu.emu_autotune_gemm(single, m, n, k, N)
+        st_t, tuned = emu.emu_autotune_gemm(dtype_code, m, n, k, N)
         emu.check(st_t, "emu_autotune_gemm")
     for _ in range(args.warmup):
         step()
@@ -268,14 +297,14 @@ def main():
     status = emu.emu_stream_status(st)
     total_ms = t0e.elapsed_time(t1e)
     ms = max_over_ranks(total_ms / args.steps, dist)
-    flops = 8.0 * m * n * k
+    flops = flops_per_entry(wl) * m * n * k
     value = world * flops / (ms * 1e-3) * 1e-12
     phase_names = ["exponents", "split", "residue_gemm", "crt"]
     phases = {nm: statistics.mean(evs[i][p].elapsed_time(evs[i][p + 1]) for i in range(args.steps))
               for p, nm in enumerate(phase_names)}
     pk, pk_src = peaks()
     t_gemm = phases["residue_gemm"] * 1e-3
-    gemm_flops = 6.0 * N * m * n * k
+    gemm_flops = 2.0 * ppm * N * m * n * k
     achieved = gemm_flops / t_gemm * 1e-12
     peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
     traffic = profile_traffic("k_gemm_f16.cu", f"gemm_f16_{args.workload}.txt")
@@ -284,16 +313,17 @@ def main():
                 "traffic": traffic, "peak_source": f"{pk_src} bf16_tflops_sustained (fp16 = bf16 rate)",
                 "algorithmic_flops_per_launch": gemm_flops}
     hbm = float(pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
-    byts = {"exponents": 2 * esz * k * (m + n), "split": esz * k * (m + n) + 3 * N * 2 * k * (m + n),
-            "crt": 3 * N * m * n + esz * m * n}
+    byts = {"exponents": 2 * esz * k * (m + n), "split": esz * k * (m + n) + ppm * N * 2 * k * (m + n),
+            "crt": ppm * N * m * n + esz * m * n}
     mem_phases = {nm: {"ms": phases[nm], "algorithmic_bytes": byts[nm],
                        "GBps": byts[nm] / (phases[nm] * 1e-3) * 1e-9,
                        "frac_of_hbm": byts[nm] / (phases[nm] * 1e-3) * 1e-9 / hbm} for nm in byts}
-    out = {"metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world, "steps": args.steps,
+    out = {"metric": METRIC_REAL if real else METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world,
+           "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "k": k,
-                      "io": "complex64" if single else "complex128", "num_moduli": N, "phi": wl["phi"],
+                      "io": str(cdt).replace("torch.", ""), "num_moduli": N, "phi": wl["phi"],
                       "engine": "tcgen05 kind::f16 (exact residues), integer CRT",
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "seed": wl["seed"],
@@ -353,12 +383,14 @@ def main():
         nb.record()
         torch.cuda.synchronize()
         nms = na.elapsed_time(nb)
-        out["native_cublas"] = {"routine": "cublasCgemm" if single else "cublasZgemm (torch.matmul)",
+        routine = {torch.complex64: "cublasCgemm", torch.complex128: "cublasZgemm",
+                   torch.float32: "cublasSgemm", torch.float64: "cublasDgemm"}[cdt]
+        out["native_cublas"] = {"routine": routine + " (torch.matmul)",
                                 "ms": nms, "tflops": flops / (nms * 1e-3) * 1e-12,
                                 "speedup_of_emulation": nms / ms,
                                 "math_mode": "default (CUBLAS_EMULATION_STRATEGY %s)"
                                              % os.environ.get("CUBLAS_EMULATION_STRATEGY", "unset")}
-    if rank == 0 and not args.no_plain:
+    if rank == 0 and not args.no_plain and not real:
         out["plain_emulation"] = plain_emulation(emu, torch, A, B, wl, C)
 
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -1,6 +1,7 @@
 /*
  * ozaki2_emu.h -- C ABI of the GB300 (sm_103a) Ozaki-II emulation of complex
- * matrix multiplication (ZGEMM / CGEMM) through the Chinese Remainder Theorem.
+ * matrix multiplication (ZGEMM / CGEMM) through the Chinese Remainder Theorem,
+ * with the real analogues (DGEMM / SGEMM) of the paper's supplemental study.
  *
  * Method (arXiv 2512.08321): Algorithm 1 (Ozaki-II outline, Section II) with
  * the Karatsuba complex product (Section III-A, eq. karatsuba) and fast-mode
@@ -89,6 +90,39 @@ emu_status_t emu_cgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
                        const float* alpha, const void* A, int64_t lda,
                        const void* B, int64_t ldb, const float* beta,
                        void* C, int64_t ldc, int num_moduli, void* stream);
+
+/* Real analogues (the paper's supplemental real-valued comparison, Section
+ * IV): Algorithm 1 on real matrices, one residue product per modulus
+ * (E'_l = mod(A'_l B'_l, p_l)), fast-mode scaling on the k entries of each
+ * row of op(A) / column of op(B), the same exact CRT.  C = alpha op(A) op(B)
+ * + beta C with host scalars alpha and beta; with (alpha, beta) != (1, 0) the
+ * result is fma(beta, C, RN(alpha o)) in binary64 (beta = 0: RN(alpha o)),
+ * then rounded once to binary32 for emu_sgemm.  EMU_OP_C equals EMU_OP_T. */
+emu_status_t emu_dgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                       const double* alpha, const double* A, int64_t lda,
+                       const double* B, int64_t ldb, const double* beta,
+                       double* C, int64_t ldc, int num_moduli, void* stream);
+emu_status_t emu_sgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                       const float* alpha, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, const float* beta,
+                       float* C, int64_t ldc, int num_moduli, void* stream);
+
+/* Element-type codes of emu_workspace_bytes and emu_autotune_gemm. */
+#define EMU_DTYPE_Z 0   /* complex128 */
+#define EMU_DTYPE_C 1   /* complex64 */
+#define EMU_DTYPE_D 2   /* float64 */
+#define EMU_DTYPE_S 3   /* float32 */
+
+/* Column blocking (all four GEMMs).  The output columns can be processed in
+ * blocks of nb: the exponents and residue planes of op(A) are formed once,
+ * those of op(B), the residue products and the CRT once per block of nb
+ * columns of op(B) and C (the paper's n-blocking, Section III-A).  Results
+ * are bit-identical for every nb, since each scaling exponent depends on one
+ * row or one column only.  nb is the EMU_TUNE_NBLOCK setting when nonzero;
+ * otherwise n when the whole workspace (emu_workspace_bytes) fits -- in the
+ * caller's workspace if one is set, else in the library's workspace plus the
+ * device's free memory less 256 MiB -- and else the widest multiple of 128
+ * columns that fits. */
 
 /* --------------------------------------------------------- grouped GEMMs ---
  * Many complex GEMMs of uneven shapes on one moduli count.  Every phase of
@@ -192,9 +226,10 @@ emu_status_t emu_mlp_choose(const float* theta, const float* features, float thr
 
 /* ------------------------------------------------------------ workspace --- */
 
-/* Bytes of device workspace one call of the given shape needs (is_single: 0
- * for ZGEMM, 1 for CGEMM).  0 on invalid arguments. */
-size_t emu_workspace_bytes(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli);
+/* Bytes of device workspace one unblocked call of the given shape needs
+ * (dtype: an EMU_DTYPE_* code; 0 and 1 keep their old meaning of ZGEMM and
+ * CGEMM).  Column blocking needs less.  0 on invalid arguments. */
+size_t emu_workspace_bytes(int dtype, int64_t m, int64_t n, int64_t k, int num_moduli);
 
 /* Use caller-owned device memory [ptr, ptr+bytes) as the workspace of this
  * device (the current device) for subsequent calls; NULL/0 returns to the
@@ -207,37 +242,42 @@ emu_status_t emu_set_workspace(void* ptr, size_t bytes);
  * 64..960; 0 keeps the default 512). */
 emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 
-/* Launch-configuration knobs of emu_zgemm/emu_cgemm (no effect on results):
+/* Launch-configuration knobs of emu_zgemm/cgemm/dgemm/sgemm (no effect on results):
  *   EMU_TUNE_TILE_N      residue products: rows of op(A) per tile, 64/128/256
  *   EMU_TUNE_GROUP       residue products: tile rasterisation group, 1..64
  *   EMU_TUNE_CHUNK_K     residue products: k between in-TMEM reductions, 64..960, multiple of 64
  *   EMU_TUNE_CRT_ROWS    CRT: rows per thread, 1/2/4
  *   EMU_TUNE_SPLIT_ELEMS residue split: entries per thread, 2/4
+ *   EMU_TUNE_NBLOCK      output columns per block, 0 (automatic) or a multiple of 128;
+ *                        a process setting only, never autotuned
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
  * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
  * use the winners.  The table is kept in the file EMU_AUTOTUNE_CACHE names, if
  * set.  Tuning state is per process; emu_autotune_gemm allocates its own
  * temporary buffers (inputs, planes, residues of the shape), synchronises, and
- * frees them.  best (may be NULL) receives the 5 chosen values in key order. */
+ * frees them.  dtype is an EMU_DTYPE_* code.  best (may be NULL) receives the
+ * first 5 knobs' chosen values in key order. */
 #define EMU_TUNE_TILE_N 1
 #define EMU_TUNE_GROUP 2
 #define EMU_TUNE_CHUNK_K 3
 #define EMU_TUNE_CRT_ROWS 4
 #define EMU_TUNE_SPLIT_ELEMS 5
+#define EMU_TUNE_NBLOCK 6
 emu_status_t emu_set_tuning(int key, int value);
 int emu_get_tuning(int key);
-emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli, int* best);
+emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int num_moduli, int* best);
 /* Forget the autotuned entries (the defaults stay). */
 emu_status_t emu_autotune_clear(void);
 
-/* CRT reconstruction used by emu_zgemm, emu_cgemm and emu_stage_crt (the
- * grouped path always uses the exact one):
+/* CRT reconstruction used by emu_zgemm/cgemm/dgemm/sgemm and emu_stage_crt
+ * (the grouped path always uses the exact one):
  *   EMU_CRT_EXACT (default): exact multi-limb integer reconstruction, result
  *     RN(c' 2^-(x+y)) with c' = A'B' exactly;
  *   EMU_CRT_PAPER_FP64: the paper's floating-point reconstruction (Section II,
  *     eq. CRTaccumulation): S1 = sum s_l1 E'_l exact, S2 = sum s_l2 E'_l, then
- *     mod(S1 + S2, P) in double-double (complex128) or double (complex64). */
+ *     mod(S1 + S2, P) in double-double (complex128, float64) or one double
+ *     sum (complex64, float32). */
 #define EMU_CRT_EXACT 0
 #define EMU_CRT_PAPER_FP64 1
 emu_status_t emu_set_crt_mode(int mode);
@@ -336,9 +376,10 @@ emu_status_t emu_stream_status(void* stream);
  * bounded-wait path without faulting or hanging the GPU. */
 emu_status_t emu_selftest_bounded_wait(int64_t limit_cycles, void* stream);
 
-/* Phase timing: when set, every following emu_zgemm/emu_cgemm records
+/* Phase timing: when set, every following emu_zgemm/cgemm/dgemm/sgemm records
  * events[0..4] (cudaEvent_t passed as void*) on its stream at the start of
  * the call and after the exponent, split, residue-product and CRT phases.
+ * With column blocking, events 1-3 mark the phases of the last block.
  * count must be 5, or 0 with events NULL to stop.  The caller owns the events.
  * Host state of the calling process, not per thread. */
 emu_status_t emu_set_phase_events(void* const* events, int count);

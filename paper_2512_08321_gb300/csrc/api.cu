@@ -68,7 +68,8 @@ emu_status_t device_init(int dev, DeviceState*& ds) {
   return EMU_OK;
 }
 
-// Workspace layout of one GEMM.
+// Workspace layout of one GEMM whose output columns are processed nb at a time
+// (nb == n: one pass).  ppm = residue planes per modulus (3 complex, 1 real).
 struct Layout {
   int64_t kpad, ldr;
   size_t off_x, off_y, off_scr, off_pa, off_pb, off_res, total;
@@ -76,7 +77,8 @@ struct Layout {
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
-Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16) {
+Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm = 3, int64_t nb = -1) {
+  if (nb < 0 || nb > n) nb = n;
   Layout L;
   L.kpad = round_up(k > 0 ? k : 1, 64);
   L.ldr = round_up(m, 16);
@@ -84,10 +86,10 @@ Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16) {
   size_t o = 0;
   L.off_x = o;   o += al(static_cast<size_t>(m) * 2);
   L.off_y = o;   o += al(static_cast<size_t>(n) * 2);
-  L.off_scr = o; o += al(exponents_scratch_bytes(m > n ? m : n));
-  L.off_pa = o;  o += al(static_cast<size_t>(3 * N) * m * L.kpad * esz);
-  L.off_pb = o;  o += al(static_cast<size_t>(3 * N) * n * L.kpad * esz);
-  L.off_res = o; o += al(static_cast<size_t>(3 * N) * n * L.ldr);
+  L.off_scr = o; o += al(exponents_scratch_bytes(m > nb ? m : nb));
+  L.off_pa = o;  o += al(static_cast<size_t>(ppm * N) * m * L.kpad * esz);
+  L.off_pb = o;  o += al(static_cast<size_t>(ppm * N) * nb * L.kpad * esz);
+  L.off_res = o; o += al(static_cast<size_t>(ppm * N) * nb * L.ldr);
   L.total = o;
   return L;
 }
@@ -147,20 +149,58 @@ emu_status_t check_common(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_
 
 emu_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA; }
 
+
 emu_status_t run_residue_gemm(emu_engine_t eng, int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                               const void* pa, const void* pb, int8_t* res, int64_t ldr,
-                              DeviceState* ds, cudaStream_t st, const Tune& t) {
+                              DeviceState* ds, cudaStream_t st, const Tune& t, int ppm) {
   if (eng == EMU_ENGINE_I8)
     return cuda_status(launch_gemm_i8(m, n, kpad, pl, static_cast<const int8_t*>(pa),
-                                      static_cast<const int8_t*>(pb), res, ldr, st));
+                                      static_cast<const int8_t*>(pb), res, ldr, st, ppm));
   const cudaError_t e =
-      launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, t.chunk_k, ds->status, st, t.tile_n, t.group);
+      launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, t.chunk_k, ds->status, st, t.tile_n, t.group, ppm);
   if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
   return cuda_status(e);
 }
 
-template <bool SINGLE>
-emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
+// Element type of a GEMM: complex128 (Z), complex64 (C), float64 (D), float32 (S).
+struct Dt {
+  bool single, real;
+  int ppm() const { return real ? 1 : 3; }
+  int code() const { return (real ? 2 : 0) + (single ? 1 : 0); }
+};
+
+constexpr size_t kFreeMargin = size_t(256) << 20;   // device memory left to others when blocking
+
+// Output columns per block.  The knob (if set) wins; otherwise one block when
+// the whole workspace fits (the caller's buffer, or the library's plus free
+// device memory), else the widest multiple of 128 columns that fits.
+int64_t choose_nblock(const DeviceState* ds, int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm,
+                      const Tune& t) {
+  if (t.nblock > 0) return t.nblock < n ? t.nblock : n;
+  const size_t full = layout(m, n, k, N, fp16, ppm, n).total;
+  size_t limit;
+  if (ds->user) {
+    limit = ds->user_bytes;
+  } else {
+    if (full <= ds->own_bytes) return n;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      return n;
+    }
+    limit = fr + ds->own_bytes;
+    limit = limit > kFreeMargin ? limit - kFreeMargin : 0;
+  }
+  if (full <= limit || n <= 128) return n;
+  int64_t lo = 0, hi = (n - 1) / 128;     // widths 128 * [1, hi] are candidates
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (layout(m, n, k, N, fp16, ppm, 128 * mid).total <= limit) lo = mid; else hi = mid - 1;
+  }
+  return lo > 0 ? 128 * lo : n;            // nothing fits: one block, and the workspace check reports it
+}
+
+emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
                   const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
                   void* C, int64_t ldc, int N, void* stream) {
   emu_status_t s = check_common(ta, tb, m, n, k, lda, ldb, ldc, N, true);
@@ -175,10 +215,15 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
   const Plan* pl = get_plan(N);
   const emu_engine_t eng = resolve(g_engine);
   const bool fp16 = (eng == EMU_ENGINE_F16);
-  const Layout L = layout(m, n, k, N, fp16);
+  const int ppm = dt.ppm();
+  const Tune tn = tune_for(dt.code(), N, m, n, k);
   char* ws = nullptr;
+  int64_t nb;
+  Layout L;
   {
     std::lock_guard<std::mutex> lk(g_mu);
+    nb = choose_nblock(ds, m, n, k, N, fp16, ppm, tn);
+    L = layout(m, n, k, N, fp16, ppm, nb);
     s = get_workspace(ds, L.total, &ws);
   }
   if (s != EMU_OK) return s;
@@ -192,35 +237,51 @@ emu_status_t gemm(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, dou
   int64_t rsa, hsa, rsb, hsb;
   strides_a(ta, lda, rsa, hsa);
   strides_b(tb, ldb, rsb, hsb);
-  const Tune tn = tune_for(SINGLE, N, m, n, k);
+  // element sizes of B and C, to step to a column block
+  const size_t in_esz = (dt.real ? 1 : 2) * (dt.single ? 4 : 8);
+  const bool conj_a = !dt.real && ta == EMU_OP_C, conj_b = !dt.real && tb == EMU_OP_C;
   cudaError_t e;
   phase(0, st);
   if (k == 0) {
     // empty inner dimension: the product is zero
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = cudaMemsetAsync(y, 0, static_cast<size_t>(n) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
-    if ((e = cudaMemsetAsync(res, 0, static_cast<size_t>(3 * N) * n * L.ldr, st)) != cudaSuccess)
-      return EMU_ERR_CUDA;
   } else {
-    if ((e = launch_exponents(SINGLE, A, m, k, rsa, hsa, *pl, x, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
-    if ((e = launch_exponents(SINGLE, B, n, k, rsb, hsb, *pl, y, scr, st)) != cudaSuccess) return EMU_ERR_CUDA;
-    phase(1, st);
-    if ((e = launch_split(SINGLE, ta == EMU_OP_C, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st,
-                          tn.split_elems)) != cudaSuccess)
+    if ((e = launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, st, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
-    if ((e = launch_split(SINGLE, tb == EMU_OP_C, B, n, k, rsb, hsb, *pl, y, fp16, L.kpad, pb, st,
-                          tn.split_elems)) != cudaSuccess)
-      return EMU_ERR_CUDA;
-    phase(2, st);
-    s = run_residue_gemm(eng, m, n, L.kpad, *pl, pa, pb, res, L.ldr, ds, st, tn);
-    if (s != EMU_OK) return s;
-    phase(3, st);
   }
-  s = cuda_status(g_crt_mode == 1 ? launch_crt_fp(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st)
-                                  : launch_crt(SINGLE, m, n, *pl, res, L.ldr, x, y, ar, ai, br, bi, C, ldc, st,
-                                               tn.crt_rows));
+  for (int64_t j0 = 0; j0 < n; j0 += nb) {
+    const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
+    const void* Bj = k > 0 ? static_cast<const char*>(B) + static_cast<size_t>(j0) * rsb * in_esz : B;
+    void* Cj = static_cast<char*>(C) + static_cast<size_t>(j0) * ldc * in_esz;
+    int16_t* yj = y + j0;
+    if (k == 0) {
+      if ((e = cudaMemsetAsync(res, 0, static_cast<size_t>(ppm * N) * nj * L.ldr, st)) != cudaSuccess)
+        return EMU_ERR_CUDA;
+    } else {
+      if ((e = launch_exponents(dt.single, Bj, nj, k, rsb, hsb, *pl, yj, scr, st, dt.real)) != cudaSuccess)
+        return EMU_ERR_CUDA;
+      phase(1, st);
+      if (j0 == 0 &&
+          (e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st, tn.split_elems,
+                            dt.real)) != cudaSuccess)
+        return EMU_ERR_CUDA;
+      if ((e = launch_split(dt.single, conj_b, Bj, nj, k, rsb, hsb, *pl, yj, fp16, L.kpad, pb, st, tn.split_elems,
+                            dt.real)) != cudaSuccess)
+        return EMU_ERR_CUDA;
+      phase(2, st);
+      s = run_residue_gemm(eng, m, nj, L.kpad, *pl, pa, pb, res, L.ldr, ds, st, tn, ppm);
+      if (s != EMU_OK) return s;
+      phase(3, st);
+    }
+    s = cuda_status(g_crt_mode == 1
+                        ? launch_crt_fp(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st, dt.real)
+                        : launch_crt(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st,
+                                     tn.crt_rows, dt.real));
+    if (s != EMU_OK) return s;
+  }
   phase(4, st);
-  return s;
+  return EMU_OK;
 }
 
 }  // namespace
@@ -266,7 +327,7 @@ emu_status_t emu_zgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
                        const double* beta, void* C, int64_t ldc, int num_moduli, void* stream) {
   if (!alpha) return emu::bad(6);
   if (!beta) return emu::bad(11);
-  return emu::gemm<false>(transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0],
+  return emu::gemm(emu::Dt{false, false}, transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0],
                           beta[1], C, ldc, num_moduli, stream);
 }
 
@@ -275,14 +336,33 @@ emu_status_t emu_cgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
                        const float* beta, void* C, int64_t ldc, int num_moduli, void* stream) {
   if (!alpha) return emu::bad(6);
   if (!beta) return emu::bad(11);
-  return emu::gemm<true>(transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0],
-                         beta[1], C, ldc, num_moduli, stream);
+  return emu::gemm(emu::Dt{true, false}, transa, transb, m, n, k, alpha[0], alpha[1], A, lda, B, ldb, beta[0],
+                   beta[1], C, ldc, num_moduli, stream);
 }
 
-size_t emu_workspace_bytes(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli) {
-  (void)is_single;
+emu_status_t emu_dgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k, const double* alpha,
+                       const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C,
+                       int64_t ldc, int num_moduli, void* stream) {
+  if (!alpha) return emu::bad(6);
+  if (!beta) return emu::bad(11);
+  return emu::gemm(emu::Dt{false, true}, transa, transb, m, n, k, *alpha, 0.0, A, lda, B, ldb, *beta, 0.0, C, ldc,
+                   num_moduli, stream);
+}
+
+emu_status_t emu_sgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k, const float* alpha,
+                       const float* A, int64_t lda, const float* B, int64_t ldb, const float* beta, float* C,
+                       int64_t ldc, int num_moduli, void* stream) {
+  if (!alpha) return emu::bad(6);
+  if (!beta) return emu::bad(11);
+  return emu::gemm(emu::Dt{true, true}, transa, transb, m, n, k, *alpha, 0.0, A, lda, B, ldb, *beta, 0.0, C, ldc,
+                   num_moduli, stream);
+}
+
+size_t emu_workspace_bytes(int dtype, int64_t m, int64_t n, int64_t k, int num_moduli) {
   if (m < 0 || n < 0 || k < 0 || num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return 0;
-  return emu::layout(m, n, k, num_moduli, emu::resolve(emu::g_engine) == EMU_ENGINE_F16).total;
+  if (dtype < EMU_DTYPE_Z || dtype > EMU_DTYPE_S) return 0;
+  const int ppm = dtype >= EMU_DTYPE_D ? 1 : 3;
+  return emu::layout(m, n, k, num_moduli, emu::resolve(emu::g_engine) == EMU_ENGINE_F16, ppm).total;
 }
 
 emu_status_t emu_set_workspace(void* ptr, size_t bytes) {
@@ -366,7 +446,7 @@ emu_status_t emu_stage_residue_gemm(emu_engine_t engine, int64_t m, int64_t n, i
   if (s != EMU_OK) return s;
   const emu::Plan* pl = emu::get_plan(num_moduli);
   return emu::run_residue_gemm(emu::resolve(engine), m, n, kpad, *pl, planesA, planesB, residues, ldr, ds,
-                               static_cast<cudaStream_t>(stream), emu::tune_for(false, num_moduli, m, n, kpad));
+                               static_cast<cudaStream_t>(stream), emu::tune_for(0, num_moduli, m, n, kpad), 3);
 }
 
 emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli, const int8_t* residues,
@@ -560,8 +640,7 @@ static emu_status_t gemm_tol(int single, emu_op_t ta, emu_op_t tb, int64_t m, in
     }
   }
   if (n_used) *n_used = N;
-  return single ? emu::gemm<true>(ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream)
-                : emu::gemm<false>(ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream);
+  return emu::gemm(emu::Dt{single != 0, false}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream);
 }
 
 emu_status_t emu_zgemm_tol(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k, const double* alpha,

@@ -58,7 +58,7 @@ unsigned int* device_status_ptr();
 // Launchers (one per translation unit).
 cudaError_t launch_exponents(bool single, const void* X, int64_t rows, int64_t k,
                              int64_t rs, int64_t hs, const Plan& pl, int16_t* xout,
-                             void* scratch, cudaStream_t st);
+                             void* scratch, cudaStream_t st, bool real = false);
 size_t exponents_scratch_bytes(int64_t rows);
 
 // Launch-configuration knobs of one GEMM (process defaults, autotuned per shape bucket).
@@ -68,34 +68,37 @@ struct Tune {
   int chunk_k = 512;     // residue products: k between in-TMEM reductions (64..960)
   int crt_rows = 4;      // CRT: rows per thread (1, 2, 4)
   int split_elems = 4;   // split: entries per thread (2, 4)
+  int nblock = 0;        // output columns per block (0: automatic, by workspace size)
 };
 
 // Tuning of a call of this shape: the autotuned entry of its (dtype, N, shape
-// bucket) if one exists, else the process defaults (tune.cu).
-Tune tune_for(bool single, int N, int64_t m, int64_t n, int64_t k);
+// bucket) if one exists, else the process defaults (tune.cu).  dtype is an
+// EMU_DTYPE_* code.
+Tune tune_for(int dtype, int N, int64_t m, int64_t n, int64_t k);
 void set_default_tuning(int key, int value);
 
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp,
-                         bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems = 4);
+                         bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems = 4,
+                         bool real = false);
 
 cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                            const int8_t* planesA, const int8_t* planesB, int8_t* res,
-                           int64_t ldr, cudaStream_t st);
+                           int64_t ldr, cudaStream_t st, int ppm = 3);
 
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                             const void* planesA, const void* planesB, int8_t* res,
                             int64_t ldr, int chunk_k, unsigned int* status, cudaStream_t st,
-                            int tile_n = 256, int group = 16);
+                            int tile_n = 256, int group = 16, int ppm = 3);
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        const int8_t* res, int64_t ldr, const int16_t* x, const int16_t* y,
                        double ar, double ai, double br, double bi,
-                       void* C, int64_t ldc, cudaStream_t st, int rows_per_thread = 4);
+                       void* C, int64_t ldc, cudaStream_t st, int rows_per_thread = 4, bool real = false);
 
 cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                           const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
-                          int64_t ldc, cudaStream_t st);
+                          int64_t ldc, cudaStream_t st, bool real = false);
 extern int g_crt_mode;   // 0: exact integer CRT, 1: the paper's floating-point CRT
 
 cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* status,

@@ -18,6 +18,9 @@
 // operations (subnormals included).  complex64 output rounds that binary64
 // value (after alpha/beta) once more to binary32.
 //
+// Real input (DGEMM/SGEMM emulation) has one residue plane per modulus and
+// one output component (crt_real_kernel).
+//
 // Thread mapping: 4 consecutive rows i of one column j; the residue bytes of
 // those rows are one 32-bit word per job.
 #include "emu_internal.h"
@@ -218,6 +221,70 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
 }
 
 
+// Real input (DGEMM/SGEMM emulation): E'_l is the residue of job l itself; one
+// accumulator per row.  alpha/beta: t = RN(alpha o), then fma(beta, c, t).
+template <int L, bool SINGLE, int kRowsPerThread>
+__device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
+                                               int64_t ldr, const int16_t* __restrict__ x,
+                                               const int16_t* __restrict__ y, double ar, double br,
+                                               void* __restrict__ Cv, int64_t ldc, int64_t j, int64_t iblock) {
+  const int64_t i0 = (iblock * kThreads + threadIdx.x) * kRowsPerThread;
+  if (i0 >= m) return;
+  const int N = pl.N;
+  const int64_t job_stride = n * ldr;
+  const int8_t* base = res + j * ldr + i0;
+  uint64_t acc[kRowsPerThread][L];
+  float est[kRowsPerThread];
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    est[q] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < L; ++t) acc[q][t] = pl.K[t];
+  }
+  uint32_t nw = Word<kRowsPerThread>::load(base);
+  for (int l = 0; l < N; ++l) {
+    const float qp = pl.qp[l];
+    const uint32_t wv = nw;
+    if (l + 1 < N) nw = Word<kRowsPerThread>::load(base + (l + 1) * job_stride);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int e = static_cast<int8_t>(wv >> (8 * q));
+      const uint32_t u = static_cast<uint32_t>(e + 128);
+#pragma unroll
+      for (int t = 0; t < L; ++t) acc[q][t] += u * static_cast<uint64_t>(pl.w[l][t]);
+      est[q] = fmaf(static_cast<float>(e), qp, est[q]);
+    }
+  }
+  const int yj = y[j];
+  const bool plain = (ar == 1.0 && br == 0.0);
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    const int64_t i = i0 + q;
+    if (i >= m) break;
+    const int xi = x[i];
+    double o = (xi == kExpNonfinite || yj == kExpNonfinite) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                            : finish<L>(acc[q], est[q], pl, -(xi + yj));
+    const int64_t ci = j * ldc + i;
+    if (!plain) {
+      double t = __dmul_rn(ar, o);
+      if (br != 0.0) t = __fma_rn(br, SINGLE ? static_cast<double>(static_cast<const float*>(Cv)[ci])
+                                             : static_cast<const double*>(Cv)[ci], t);
+      o = t;
+    }
+    if (SINGLE) static_cast<float*>(Cv)[ci] = __double2float_rn(o);
+    else static_cast<double*>(Cv)[ci] = o;
+  }
+}
+
+template <int L, bool SINGLE, int R>
+__global__ void __launch_bounds__(kThreads) crt_real_kernel(int64_t m, int64_t n, const __grid_constant__ Plan pl,
+                                                            const int8_t* __restrict__ res, int64_t ldr,
+                                                            const int16_t* __restrict__ x,
+                                                            const int16_t* __restrict__ y, double ar, double br,
+                                                            void* __restrict__ Cv, int64_t ldc) {
+  crt_block_real<L, SINGLE, R>(m, n, pl, res, ldr, x, y, ar, br, Cv, ldc, blockIdx.x, blockIdx.y);
+}
+
 template <int L, bool SINGLE, int R>
 __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
                                                        const __grid_constant__ Plan pl,
@@ -248,11 +315,14 @@ __global__ void __launch_bounds__(kThreads) crt_grouped(const CrtProb* __restric
 template <int L, int R>
 cudaError_t launch_lr(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                       const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
-                      int64_t ldc, cudaStream_t st) {
+                      int64_t ldc, cudaStream_t st, bool real) {
   const int64_t per_block = static_cast<int64_t>(kThreads) * R;
   if ((m + per_block - 1) / per_block > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + per_block - 1) / per_block));
-  if (single)
+  if (real) {
+    if (single) crt_real_kernel<L, true, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+    else crt_real_kernel<L, false, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+  } else if (single)
     crt_kernel<L, true, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   else
     crt_kernel<L, false, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
@@ -263,11 +333,11 @@ cudaError_t launch_lr(bool single, int64_t m, int64_t n, const Plan& pl, const i
 template <int L>
 cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                      int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
-                     double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows) {
+                     double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real) {
   switch (rows) {
-    case 1: return launch_lr<L, 1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
-    case 2: return launch_lr<L, 2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
-    default: return launch_lr<L, 4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+    case 1: return launch_lr<L, 1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real);
+    case 2: return launch_lr<L, 2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real);
+    default: return launch_lr<L, 4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real);
   }
 }
 
@@ -389,6 +459,45 @@ __global__ void __launch_bounds__(kThreads) crt_fp_kernel(int64_t m, int64_t n, 
     static_cast<double2*>(Cv)[ci] = make_double2(orr, oi);
 }
 
+// The paper's floating-point CRT for real input: the DGEMM form (S1 + S2 and
+// the double-double reduction) for binary64 output, one double sum for binary32.
+template <bool SINGLE>
+__global__ void __launch_bounds__(kThreads) crt_fp_real_kernel(int64_t m, int64_t n, const __grid_constant__ Plan pl,
+                                                               const int8_t* __restrict__ res, int64_t ldr,
+                                                               const int16_t* __restrict__ x,
+                                                               const int16_t* __restrict__ y, double ar, double br,
+                                                               void* __restrict__ Cv, int64_t ldc) {
+  const int64_t j = blockIdx.x;
+  const int64_t i = static_cast<int64_t>(blockIdx.y) * kThreads + threadIdx.x;
+  if (i >= m) return;
+  const int N = pl.N;
+  const int64_t js = n * ldr;
+  const int8_t* base = res + j * ldr + i;
+  double s1 = 0.0, s2 = 0.0;
+  for (int l = 0; l < N; ++l) {
+    const double e = static_cast<double>(base[l * js]);
+    if (SINGLE) {
+      s1 = __fma_rn(pl.wd[l], e, s1);
+    } else {
+      s1 = __dadd_rn(s1, __dmul_rn(pl.s1[l], e));
+      s2 = __fma_rn(pl.s2[l], e, s2);
+    }
+  }
+  const int xi = x[i], yj = y[j];
+  double o;
+  if (xi == kExpNonfinite || yj == kExpNonfinite) o = __longlong_as_double(0x7FF8000000000000ll);
+  else o = scale_double(SINGLE ? fp_reduce_c(s1, pl) : fp_reduce_z(s1, s2, pl), -(xi + yj));
+  const int64_t ci = j * ldc + i;
+  if (!(ar == 1.0 && br == 0.0)) {
+    double t = __dmul_rn(ar, o);
+    if (br != 0.0) t = __fma_rn(br, SINGLE ? static_cast<double>(static_cast<const float*>(Cv)[ci])
+                                           : static_cast<const double*>(Cv)[ci], t);
+    o = t;
+  }
+  if (SINGLE) static_cast<float*>(Cv)[ci] = __double2float_rn(o);
+  else static_cast<double*>(Cv)[ci] = o;
+}
+
 template <int L>
 cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long long blocks, const Plan& pl,
                              cudaStream_t st) {
@@ -425,11 +534,14 @@ int g_crt_mode = 0;
 
 cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                           const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
-                          int64_t ldc, cudaStream_t st) {
+                          int64_t ldc, cudaStream_t st, bool real) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (n > 2147483647LL || (m + kThreads - 1) / kThreads > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + kThreads - 1) / kThreads));
-  if (single)
+  if (real) {
+    if (single) crt_fp_real_kernel<true><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+    else crt_fp_real_kernel<false><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+  } else if (single)
     crt_fp_kernel<true><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   else
     crt_fp_kernel<false><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
@@ -439,15 +551,15 @@ cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, con
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                        int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
-                       double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows) {
+                       double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ldr % 16 || n > 2147483647LL) return cudaErrorInvalidValue;
   switch (pl.L) {
-    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
-    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
-    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
-    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
-    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows);
+    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
+    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
+    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
+    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
+    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -172,6 +172,7 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // (jb < 0 when the job count is odd and this is the last pair).
 struct Unit {
   int ja, jb, tj, ti;
+  int ppm;                          // planes (jobs) per modulus: 3 complex, 1 real
   int nkb, ck, nch;                 // k-blocks, k-blocks per chunk, chunks
   const CUtensorMap* mapA;          // B planes of the problem (MMA operand A)
   const CUtensorMap* mapB;          // A planes of the problem (MMA operand B)
@@ -192,7 +193,8 @@ __device__ __forceinline__ void tile_coords(int t, int TJ, int TI, int group, in
 }
 
 struct Sched {
-  int J;          // jobs = 3N
+  int J;          // jobs = ppm N
+  int ppm;        // jobs per modulus: 3 (D, E, F of eq. karatsuba) or 1 (real)
   int pairs;      // ceil(J / 2)
   int TJ, TI;     // tiles along output columns (BM) and rows (BN)
   int tiles;
@@ -217,6 +219,7 @@ struct SingleWork {
     const int t = static_cast<int>(u % s.tiles);
     w.ja = 2 * pair;
     w.jb = (2 * pair + 1 < s.J) ? 2 * pair + 1 : -1;
+    w.ppm = s.ppm;
     tile_coords(t, s.TJ, s.TI, s.group, w.tj, w.ti);
     w.nkb = s.nkb;
     w.ck = s.ck;
@@ -237,7 +240,7 @@ struct GroupProblem {  // CUtensorMap members give it 64-byte alignment
   int8_t* res;
   int64_t ldr, n;
   long long unit_begin;             // first unit of this problem
-  int TJ, TI, tiles, group, nkb, ck, nch, J;
+  int TJ, TI, tiles, group, nkb, ck, nch, J, ppm;
 };
 
 struct GroupWork {
@@ -258,6 +261,7 @@ struct GroupWork {
     const int t = static_cast<int>(v % P.tiles);
     w.ja = 2 * pair;
     w.jb = (2 * pair + 1 < P.J) ? 2 * pair + 1 : -1;
+    w.ppm = P.ppm;
     tile_coords(t, P.TJ, P.TI, P.group, w.tj, w.ti);
     w.nkb = P.nkb;
     w.ck = P.ck;
@@ -419,7 +423,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
           const int job = which ? U.jb : U.ja;
           if (job < 0) continue;
           const int slot = which;
-          const int l = job / 3;
+          const int l = job / U.ppm;
           const float p = static_cast<float>(pl.p[l]);
           const float inv_p = 1.0f / p;
           const int pi = pl.p[l];
@@ -563,15 +567,16 @@ cudaError_t set_smem_attrs() {
 template <int BN>
 cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                           const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group,
-                          unsigned int* status, cudaStream_t st) {
+                          unsigned int* status, cudaStream_t st, int ppm) {
   cudaError_t e = set_smem_attrs<BN>();
   if (e != cudaSuccess) return e;
-  const int J = 3 * pl.N;
+  const int J = ppm * pl.N;
   CUtensorMap mapA, mapB;
   if (!make_map(&mapA, planesB, n, kpad, J, BM)) return cudaErrorInvalidValue;
   if (!make_map(&mapB, planesA, m, kpad, J, BN)) return cudaErrorInvalidValue;
   Sched s;
   s.J = J;
+  s.ppm = ppm;
   s.pairs = (J + 1) / 2;
   s.TJ = static_cast<int>((n + BM - 1) / BM);
   s.TI = static_cast<int>((m + BN - 1) / BN);
@@ -594,16 +599,17 @@ int g_f16_group = 16;   // tile rasterisation group of grouped launches
 
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                             const void* planesB, int8_t* res, int64_t ldr, int chunk_k, unsigned int* status,
-                            cudaStream_t st, int tile_n, int group) {
+                            cudaStream_t st, int tile_n, int group, int ppm) {
   if (m <= 0 || n <= 0) return cudaSuccess;
+  if (ppm != 1 && ppm != 3) return cudaErrorInvalidValue;
   if (kpad % BK || ldr % 16 || chunk_k % BK || chunk_k < BK || chunk_k > 960) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u)
     return cudaErrorInvalidValue;
   if (!get_encoder()) return cudaErrorNotSupported;
   switch (tile_n) {
-    case 64: return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st);
-    case 128: return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st);
-    default: return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st);
+    case 64: return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm);
+    case 128: return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm);
+    default: return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm);
   }
 }
 
@@ -636,6 +642,7 @@ bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, c
   P.ldr = ldr;
   P.n = n;
   P.J = J;
+  P.ppm = 3;
   P.TJ = static_cast<int>((n + BM - 1) / BM);
   P.TI = static_cast<int>((m + tile_n - 1) / tile_n);
   P.tiles = P.TJ * P.TI;

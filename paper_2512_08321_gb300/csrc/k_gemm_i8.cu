@@ -1,7 +1,8 @@
 // K3 (INT8 engine): residue products on the INT8 tensor path of sm_103a,
 // warp-level mma.sync.m16n8k32 s8 x s8 -> s32 (Algorithm 1 Steps V-iii/iv).
 //
-// For job j = 3l + c (c: D, E or F of eq. karatsuba) and output (row, col):
+// For job j = 3l + c (c: D, E or F of eq. karatsuba; real input: j = l) and
+// output (row, col):
 //   res[j][col][row] = mod(sum_h A_j[row][h] B_j[col][h], p_l)
 // INT32 accumulation is exact for k <= 2^17 (Section II).  Both operands are
 // K-major int8 planes ([rows][kpad]); the output is int8 with `row`
@@ -53,13 +54,13 @@ __global__ void __launch_bounds__(kThreads) gemm_i8_kernel(int64_t m, int64_t n,
                                                            const __grid_constant__ Plan pl,
                                                            const int8_t* __restrict__ PA,
                                                            const int8_t* __restrict__ PB,
-                                                           int8_t* __restrict__ res, int64_t ldr) {
+                                                           int8_t* __restrict__ res, int64_t ldr, int ppm) {
   __shared__ __align__(16) int8_t sA[2][BM][kRowPad];
   __shared__ __align__(16) int8_t sB[2][BN][kRowPad];
   __shared__ __align__(16) int8_t sOut[BN][BM + 16];
 
   const int job = blockIdx.z;
-  const int l = job / 3;
+  const int l = job / ppm;
   const uint32_t p = static_cast<uint32_t>(pl.p[l]);
   const uint32_t bar = pl.barrett[l];
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * BM;
@@ -156,12 +157,12 @@ __global__ void __launch_bounds__(kThreads) gemm_i8_kernel(int64_t m, int64_t n,
 
 cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                            const int8_t* planesA, const int8_t* planesB, int8_t* res, int64_t ldr,
-                           cudaStream_t st) {
+                           cudaStream_t st, int ppm) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  if (kpad % BK || ldr % 16) return cudaErrorInvalidValue;
+  if (kpad % BK || ldr % 16 || (ppm != 1 && ppm != 3)) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>((m + BM - 1) / BM), static_cast<unsigned int>((n + BN - 1) / BN),
-            static_cast<unsigned int>(3 * pl.N));
-  gemm_i8_kernel<<<grid, kThreads, 0, st>>>(m, n, kpad, pl, planesA, planesB, res, ldr);
+            static_cast<unsigned int>(ppm * pl.N));
+  gemm_i8_kernel<<<grid, kThreads, 0, st>>>(m, n, kpad, pl, planesA, planesB, res, ldr, ppm);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -1,7 +1,7 @@
 // K1: fast-mode scaling exponents (Section III-B, eqs. mu-fast / nu-fast).
 //
 // For every row r of A-hat (2k real entries Re/Im of one row of op(A)) or
-// column of B-hat:
+// column of B-hat (for real matrices: the k entries of the row or column):
 //   e_r = max_h ilogb|v_rh|                                   (pass 1)
 //   S_r = sum_h ceil(|v_rh| 2^(15 - e_r))^2   (exact uint64)  (pass 2)
 //   E_r = max{E : 4^E max(2^32, S_r) <= (P-1) 2^27}           (finalize)
@@ -43,6 +43,23 @@ struct Bits<true> {
   __device__ static U re(const V& v) { return __float_as_uint(v.x) & 0x7FFFFFFFu; }
   __device__ static U im(const V& v) { return __float_as_uint(v.y) & 0x7FFFFFFFu; }
 };
+
+// Magnitude bits of the two real entries a complex element contributes to a
+// row of A-hat (Re, Im), or of the one entry of a real element (b = 0).
+template <bool S, bool R>
+__device__ __forceinline__ void load_mag(const void* __restrict__ X, int64_t off, typename Bits<S>::U& a,
+                                         typename Bits<S>::U& b) {
+  using B = Bits<S>;
+  if constexpr (R) {
+    if constexpr (S) a = __float_as_uint(static_cast<const float*>(X)[off]) & 0x7FFFFFFFu;
+    else a = __double_as_longlong(static_cast<const double*>(X)[off]) & 0x7FFFFFFFFFFFFFFFull;
+    b = 0;
+  } else {
+    const typename B::V v = static_cast<const typename B::V*>(X)[off];
+    a = B::re(v);
+    b = B::im(v);
+  }
+}
 
 // magnitude bits u (sign cleared): nonfinite?
 template <bool S>
@@ -103,8 +120,8 @@ __device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long l
 }
 
 // ---- pass 1: max exponent and non-finite flag (one block: row block rb, h chunk hc)
-template <bool S, bool ROWS_CONTIG>
-__device__ __forceinline__ void exp_max_block(const typename Bits<S>::V* __restrict__ X, int64_t rows, int64_t k,
+template <bool S, bool ROWS_CONTIG, bool R = false>
+__device__ __forceinline__ void exp_max_block(const void* __restrict__ X, int64_t rows, int64_t k,
                                               int64_t rs, int64_t hs, int* __restrict__ emax,
                                               unsigned int* __restrict__ flag, int64_t rb, int64_t hc) {
   using B = Bits<S>;
@@ -117,8 +134,8 @@ __device__ __forceinline__ void exp_max_block(const typename Bits<S>::V* __restr
     const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0; h < h1; ++h) {
-      const typename B::V v = X[r + h * hs];
-      const typename B::U a = B::re(v), b = B::im(v);
+      typename B::U a, b;
+      load_mag<S, R>(X, r + h * hs, a, b);
       bad |= nonfinite<S>(a) | nonfinite<S>(b);
       if (a && !nonfinite<S>(a)) best = max(best, ilogb_off<S>(a));
       if (b && !nonfinite<S>(b)) best = max(best, ilogb_off<S>(b));
@@ -130,8 +147,8 @@ __device__ __forceinline__ void exp_max_block(const typename Bits<S>::V* __restr
     const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0 + lane; h < h1; h += 32) {
-      const typename B::V v = X[r * rs + h];
-      const typename B::U a = B::re(v), b = B::im(v);
+      typename B::U a, b;
+      load_mag<S, R>(X, r * rs + h, a, b);
       bad |= nonfinite<S>(a) | nonfinite<S>(b);
       if (a && !nonfinite<S>(a)) best = max(best, ilogb_off<S>(a));
       if (b && !nonfinite<S>(b)) best = max(best, ilogb_off<S>(b));
@@ -146,17 +163,17 @@ __device__ __forceinline__ void exp_max_block(const typename Bits<S>::V* __restr
   if (bad) atomicOr(flag + r, 1u);
 }
 
-template <bool S, bool ROWS_CONTIG>
-__global__ void __launch_bounds__(kThreads) exp_max_kernel(const typename Bits<S>::V* __restrict__ X,
+template <bool S, bool ROWS_CONTIG, bool R>
+__global__ void __launch_bounds__(kThreads) exp_max_kernel(const void* __restrict__ X,
                                                            int64_t rows, int64_t k, int64_t rs,
                                                            int64_t hs, int* __restrict__ emax,
                                                            unsigned int* __restrict__ flag) {
-  exp_max_block<S, ROWS_CONTIG>(X, rows, k, rs, hs, emax, flag, blockIdx.x, blockIdx.y);
+  exp_max_block<S, ROWS_CONTIG, R>(X, rows, k, rs, hs, emax, flag, blockIdx.x, blockIdx.y);
 }
 
 // ---- pass 2: exact quantised sum of squares (one block)
-template <bool S, bool ROWS_CONTIG>
-__device__ __forceinline__ void exp_sum_block(const typename Bits<S>::V* __restrict__ X, int64_t rows, int64_t k,
+template <bool S, bool ROWS_CONTIG, bool R = false>
+__device__ __forceinline__ void exp_sum_block(const void* __restrict__ X, int64_t rows, int64_t k,
                                               int64_t rs, int64_t hs, const int* __restrict__ emax,
                                               const unsigned int* __restrict__ flag,
                                               unsigned long long* __restrict__ sum, int64_t rb, int64_t hc) {
@@ -170,8 +187,9 @@ __device__ __forceinline__ void exp_sum_block(const typename Bits<S>::V* __restr
     const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0; h < h1; ++h) {
-      const typename B::V v = X[r + h * hs];
-      const unsigned long long a = ceil_q<S>(B::re(v), e), b = ceil_q<S>(B::im(v), e);
+      typename B::U ua, ub;
+      load_mag<S, R>(X, r + h * hs, ua, ub);
+      const unsigned long long a = ceil_q<S>(ua, e), b = ceil_q<S>(ub, e);
       acc += a * a + b * b;
     }
   } else {
@@ -182,8 +200,9 @@ __device__ __forceinline__ void exp_sum_block(const typename Bits<S>::V* __restr
     const int64_t h0 = hc * kChunkH;
     const int64_t h1 = min(k, h0 + kChunkH);
     for (int64_t h = h0 + lane; h < h1; h += 32) {
-      const typename B::V v = X[r * rs + h];
-      const unsigned long long a = ceil_q<S>(B::re(v), e), b = ceil_q<S>(B::im(v), e);
+      typename B::U ua, ub;
+      load_mag<S, R>(X, r * rs + h, ua, ub);
+      const unsigned long long a = ceil_q<S>(ua, e), b = ceil_q<S>(ub, e);
       acc += a * a + b * b;
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -192,13 +211,13 @@ __device__ __forceinline__ void exp_sum_block(const typename Bits<S>::V* __restr
   if (acc) atomicAdd(sum + r, acc);
 }
 
-template <bool S, bool ROWS_CONTIG>
-__global__ void __launch_bounds__(kThreads) exp_sum_kernel(const typename Bits<S>::V* __restrict__ X,
+template <bool S, bool ROWS_CONTIG, bool R>
+__global__ void __launch_bounds__(kThreads) exp_sum_kernel(const void* __restrict__ X,
                                                            int64_t rows, int64_t k, int64_t rs,
                                                            int64_t hs, const int* __restrict__ emax,
                                                            const unsigned int* __restrict__ flag,
                                                            unsigned long long* __restrict__ sum) {
-  exp_sum_block<S, ROWS_CONTIG>(X, rows, k, rs, hs, emax, flag, sum, blockIdx.x, blockIdx.y);
+  exp_sum_block<S, ROWS_CONTIG, R>(X, rows, k, rs, hs, emax, flag, sum, blockIdx.x, blockIdx.y);
 }
 
 __device__ __forceinline__ int16_t finalize_row(const Plan& pl, int em, unsigned int fl, unsigned long long S) {
@@ -230,7 +249,7 @@ template <bool S>
 __global__ void __launch_bounds__(kThreads) exp_max_grouped(const ExpSeg* __restrict__ segs, int nseg) {
   const ExpSeg& g = segs[find_seg(segs, nseg, blockIdx.x)];
   const long long local = blockIdx.x - g.block_begin;
-  const auto* X = static_cast<const typename Bits<S>::V*>(g.X);
+  const void* X = g.X;
   if (g.rows_contig)
     exp_max_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks);
   else
@@ -241,7 +260,7 @@ template <bool S>
 __global__ void __launch_bounds__(kThreads) exp_sum_grouped(const ExpSeg* __restrict__ segs, int nseg) {
   const ExpSeg& g = segs[find_seg(segs, nseg, blockIdx.x)];
   const long long local = blockIdx.x - g.block_begin;
-  const auto* X = static_cast<const typename Bits<S>::V*>(g.X);
+  const void* X = g.X;
   if (g.rows_contig)
     exp_sum_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks);
   else
@@ -264,11 +283,9 @@ __global__ void exp_finalize_grouped(const ExpSeg* __restrict__ segs, int nseg,
   g.xout[i] = finalize_row(pl, g.emax[i], g.flag[i], g.sum[i]);
 }
 
-template <bool S>
-cudaError_t launch_t(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_t hs,
+template <bool S, bool R = false>
+cudaError_t launch_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                      const Plan& pl, int16_t* xout, void* scratch, cudaStream_t st) {
-  using V = typename Bits<S>::V;
-  const V* X = static_cast<const V*>(Xv);
   int* emax = static_cast<int*>(scratch);
   unsigned int* flag = reinterpret_cast<unsigned int*>(emax + round_up(rows, 64));
   unsigned long long* sum = reinterpret_cast<unsigned long long*>(flag + round_up(rows, 64));
@@ -279,13 +296,13 @@ cudaError_t launch_t(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_
     const bool rows_contig = (rs == 1);
     if (rows_contig) {
       dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
-      exp_max_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
-      exp_sum_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
+      exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
+      exp_sum_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
       count_launches(2);
     } else {
       dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
-      exp_max_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
-      exp_sum_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
+      exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
+      exp_sum_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
       count_launches(2);
     }
   }
@@ -482,8 +499,11 @@ size_t exponents_scratch_bytes(int64_t rows) {
 
 cudaError_t launch_exponents(bool single, const void* X, int64_t rows, int64_t k, int64_t rs,
                              int64_t hs, const Plan& pl, int16_t* xout, void* scratch,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool real) {
   if (rows <= 0) return cudaSuccess;
+  if (real)
+    return single ? launch_t<true, true>(X, rows, k, rs, hs, pl, xout, scratch, st)
+                  : launch_t<false, true>(X, rows, k, rs, hs, pl, xout, scratch, st);
   return single ? launch_t<true>(X, rows, k, rs, hs, pl, xout, scratch, st)
                 : launch_t<false>(X, rows, k, rs, hs, pl, xout, scratch, st);
 }

@@ -16,8 +16,11 @@
 // sum is exact; one rint-based reduction and a symmetric fix-up give the
 // residue.  This keeps the per-modulus work on the FP32 pipe.
 //
-// Output layout: planes[(3l+c) * rows * kpad + r * kpad + h]; h in [k, kpad)
-// is zero.  A block handles 32 rows x 32 h: the tile goes through shared
+// Real input (DGEMM/SGEMM emulation) has one plane per modulus:
+// plane l = mod(trunc(v 2^x_r), p_l).
+//
+// Output layout: planes[(3l+c) * rows * kpad + r * kpad + h] (real: plane l);
+// h in [k, kpad) is zero.  A block handles 32 rows x 32 h: the tile goes through shared
 // memory so global reads are coalesced whichever of r or h is contiguous;
 // each thread then owns 4 consecutive h of one row, 8 threads per row.
 #include <cuda_fp16.h>
@@ -129,7 +132,7 @@ struct StoreE<__half, 2> {
   }
 };
 
-template <bool SINGLE, bool ROWS_CONTIG, typename T, int kPerThread>
+template <bool SINGLE, bool ROWS_CONTIG, typename T, int kPerThread, bool R = false>
 __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restrict__ Xv, int64_t rows, int64_t k,
                                             int64_t rs, int64_t hs, bool conj, const int16_t* __restrict__ xexp,
                                             const Plan& pl, int64_t kpad, T* __restrict__ planes, int64_t rtile,
@@ -153,7 +156,10 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
     uint64_t bre = 0, bim = 0;
     if (r < rows && h < k) {
       const int64_t off = r * rs + h * hs;
-      if (SINGLE) {
+      if constexpr (R) {
+        bre = SINGLE ? static_cast<uint64_t>(__float_as_uint(static_cast<const float*>(Xv)[off]))
+                     : static_cast<uint64_t>(__double_as_longlong(static_cast<const double*>(Xv)[off]));
+      } else if (SINGLE) {
         const float2 v = static_cast<const float2*>(Xv)[off];
         bre = __float_as_uint(v.x);
         bim = __float_as_uint(conj ? -v.y : v.y);
@@ -192,7 +198,7 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
                              : (((br >> 52) & 0x7FF) == 0x7FF || ((bi >> 52) & 0x7FF) == 0x7FF));
     if (bad) br = bi = 0;
     chunks<SINGLE>(br, flagged ? 0 : x, nch, cre[j]);
-    chunks<SINGLE>(bi, flagged ? 0 : x, nch, cim[j]);
+    if constexpr (!R) chunks<SINGLE>(bi, flagged ? 0 : x, nch, cim[j]);
   }
   const int64_t plane_stride = rows * kpad;
   T* base = planes + r * kpad + h0 + hb;
@@ -202,6 +208,20 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
     float w[kMaxChunks];
 #pragma unroll
     for (int t = 0; t < kMaxChunks; ++t) w[t] = pl.w13[l][t];
+    if constexpr (R) {
+      // real input: one plane per modulus
+      float vr[kPerThread];
+#pragma unroll
+      for (int j = 0; j < kPerThread; ++j) {
+        float zr = 0.0f;
+#pragma unroll
+        for (int t = 0; t < kMaxChunks; ++t)
+          if (t < nch) zr = fmaf(cre[j][t], w[t], zr);
+        vr[j] = sym_mod_f(zr, p, ip);
+      }
+      StoreE<T, kPerThread>::put(base + static_cast<int64_t>(l) * plane_stride, vr);
+      continue;
+    }
     float vr[kPerThread], vi[kPerThread], vs[kPerThread];
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
@@ -228,15 +248,15 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   }
 }
 
-template <bool SINGLE, bool ROWS_CONTIG, typename T, int E>
+template <bool SINGLE, bool ROWS_CONTIG, typename T, int E, bool R>
 __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict__ Xv, int64_t rows,
                                                          int64_t k, int64_t rs, int64_t hs,
                                                          bool conj, const int16_t* __restrict__ xexp,
                                                          const __grid_constant__ Plan pl,
                                                          int64_t kpad, T* __restrict__ planes) {
   __shared__ SplitSmem sm;
-  split_block<SINGLE, ROWS_CONTIG, T, E>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x,
-                                         blockIdx.y);
+  split_block<SINGLE, ROWS_CONTIG, T, E, R>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x,
+                                            blockIdx.y);
 }
 
 // one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __rest
     split_block<SINGLE, false, T, 4>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
 }
 
-template <bool SINGLE, typename T>
+template <bool SINGLE, typename T, bool R>
 cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                      const Plan& pl, const int16_t* xexp, int64_t kpad, void* planes,
                      cudaStream_t st, int elems) {
@@ -269,14 +289,21 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
             static_cast<unsigned int>(kpad / kTileH));
   T* P = static_cast<T*>(planes);
   if (elems == 2) {
-    if (rs == 1) split_kernel<SINGLE, true, T, 2><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
-    else split_kernel<SINGLE, false, T, 2><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    if (rs == 1) split_kernel<SINGLE, true, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    else split_kernel<SINGLE, false, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
   } else {
-    if (rs == 1) split_kernel<SINGLE, true, T, 4><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
-    else split_kernel<SINGLE, false, T, 4><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    if (rs == 1) split_kernel<SINGLE, true, T, 4, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    else split_kernel<SINGLE, false, T, 4, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
   }
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <bool SINGLE, bool R>
+cudaError_t launch_s(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs, const Plan& pl,
+                     const int16_t* xexp, bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems) {
+  return fp16 ? launch_t<SINGLE, __half, R>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems)
+              : launch_t<SINGLE, int8_t, R>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems);
 }
 
 }  // namespace
@@ -305,14 +332,14 @@ cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_de
 
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp, bool fp16,
-                         int64_t kpad, void* planes, cudaStream_t st, int elems) {
+                         int64_t kpad, void* planes, cudaStream_t st, int elems, bool real) {
   if (rows <= 0 || kpad <= 0) return cudaSuccess;
   if (kpad % 64) return cudaErrorInvalidValue;
-  if (single)
-    return fp16 ? launch_t<true, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems)
-                : launch_t<true, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems);
-  return fp16 ? launch_t<false, __half>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems)
-              : launch_t<false, int8_t>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems);
+  if (real)
+    return single ? launch_s<true, true>(false, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems)
+                  : launch_s<false, true>(false, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems);
+  return single ? launch_s<true, false>(conj, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems)
+                : launch_s<false, false>(conj, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems);
 }
 
 }  // namespace emu

@@ -32,8 +32,8 @@ int bucket(int64_t v) {
   return b;
 }
 
-Key key_of(bool single, int N, int64_t m, int64_t n, int64_t k) {
-  return Key(single ? 1 : 0, N, bucket(m), bucket(n), bucket(k));
+Key key_of(int dtype, int N, int64_t m, int64_t n, int64_t k) {
+  return Key(dtype, N, bucket(m), bucket(n), bucket(k));
 }
 
 void load_locked() {
@@ -91,6 +91,7 @@ bool valid(int key, int v) {
     case EMU_TUNE_CHUNK_K: return v >= 64 && v <= 960 && v % 64 == 0;
     case EMU_TUNE_CRT_ROWS: return v == 1 || v == 2 || v == 4;
     case EMU_TUNE_SPLIT_ELEMS: return v == 2 || v == 4;
+    case EMU_TUNE_NBLOCK: return v == 0 || (v >= 128 && v % 128 == 0);
     default: return false;
   }
 }
@@ -102,6 +103,7 @@ void set(Tune& t, int key, int v) {
     case EMU_TUNE_CHUNK_K: t.chunk_k = v; break;
     case EMU_TUNE_CRT_ROWS: t.crt_rows = v; break;
     case EMU_TUNE_SPLIT_ELEMS: t.split_elems = v; break;
+    case EMU_TUNE_NBLOCK: t.nblock = v; break;
     default: break;
   }
 }
@@ -150,11 +152,14 @@ size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 }  // namespace
 
-Tune tune_for(bool single, int N, int64_t m, int64_t n, int64_t k) {
+Tune tune_for(int dtype, int N, int64_t m, int64_t n, int64_t k) {
   std::lock_guard<std::mutex> lk(g_mu);
   load_locked();
-  auto it = g_table.find(key_of(single, N, m, n, k));
-  return it != g_table.end() ? it->second : g_default;
+  auto it = g_table.find(key_of(dtype, N, m, n, k));
+  if (it == g_table.end()) return g_default;
+  Tune t = it->second;
+  t.nblock = g_default.nblock;          // column blocking is a process setting, not tuned
+  return t;
 }
 
 void set_default_tuning(int key, int value) {
@@ -181,6 +186,7 @@ int emu_get_tuning(int key) {
     case EMU_TUNE_CHUNK_K: return t.chunk_k;
     case EMU_TUNE_CRT_ROWS: return t.crt_rows;
     case EMU_TUNE_SPLIT_ELEMS: return t.split_elems;
+    case EMU_TUNE_NBLOCK: return t.nblock;
     default: return -1;
   }
 }
@@ -191,17 +197,21 @@ emu_status_t emu_autotune_clear(void) {
   return EMU_OK;
 }
 
-emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, int num_moduli, int* best) {
+emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int num_moduli, int* best) {
   using namespace emu;
+  if (dtype < EMU_DTYPE_Z || dtype > EMU_DTYPE_S) return EMU_ERR_INVALID_ARG;
   if (m <= 0 || n <= 0 || k <= 0 || k > EMU_MAX_K) return EMU_ERR_INVALID_ARG;
   if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
   unsigned int* status = device_status_ptr();
   if (!status) return EMU_ERR_UNSUPPORTED;
-  const bool single = is_single != 0;
+  const bool single = (dtype == EMU_DTYPE_C || dtype == EMU_DTYPE_S);
+  const bool real = dtype >= EMU_DTYPE_D;
+  const int ppm = real ? 1 : 3;
   const Plan* pl = get_plan(num_moduli);
-  const int J = 3 * num_moduli;
+  const int J = ppm * num_moduli;
   const int64_t kpad = round_up(k, 64), ldr = round_up(m, 16);
-  const size_t esz = single ? 8 : 16;
+  const int parts = real ? 1 : 2;                     // real numbers per entry
+  const size_t esz = static_cast<size_t>(parts) * (single ? 4 : 8);
   // one buffer: A, B, x, y, exponent scratch, fp16 planes, residues, C
   size_t o = 0;
   const size_t oA = o; o += al(esz * static_cast<size_t>(m) * k);
@@ -222,21 +232,20 @@ emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, i
   cudaEvent_t a = nullptr, b = nullptr;
   bool ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
-  const int64_t cntA = 2 * m * k, cntB = 2 * k * n;   // complex128: 2 doubles per entry
+  const int64_t cntA = parts * m * k, cntB = parts * k * n;   // real numbers in A and B
   if (ok && !single) {
     fill_kernel<<<static_cast<unsigned int>((cntA + 255) / 256), 256, 0, st>>>(reinterpret_cast<double*>(M + oA), cntA);
     fill_kernel<<<static_cast<unsigned int>((cntB + 255) / 256), 256, 0, st>>>(reinterpret_cast<double*>(M + oB), cntB);
   } else if (ok) {
-    const int64_t fa = 2 * m * k, fb = 2 * k * n;   // complex64: 2 floats per entry
-    fill_kernel_f<<<static_cast<unsigned int>((fa + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(M + oA), fa);
-    fill_kernel_f<<<static_cast<unsigned int>((fb + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(M + oB), fb);
+    fill_kernel_f<<<static_cast<unsigned int>((cntA + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(M + oA), cntA);
+    fill_kernel_f<<<static_cast<unsigned int>((cntB + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(M + oB), cntB);
   }
   int16_t* x = reinterpret_cast<int16_t*>(M + ox);
   int16_t* y = reinterpret_cast<int16_t*>(M + oy);
-  Tune t = tune_for(single, num_moduli, m, n, k);
+  Tune t = tune_for(dtype, num_moduli, m, n, k);
   if (ok) {
-    ok = launch_exponents(single, M + oA, m, k, 1, m, *pl, x, M + os, st) == cudaSuccess &&
-         launch_exponents(single, M + oB, n, k, k, 1, *pl, y, M + os, st) == cudaSuccess;
+    ok = launch_exponents(single, M + oA, m, k, 1, m, *pl, x, M + os, st, real) == cudaSuccess &&
+         launch_exponents(single, M + oB, n, k, k, 1, *pl, y, M + os, st, real) == cudaSuccess;
   }
   const int reps = (static_cast<double>(m) * n * k > 1e12) ? 2 : 3;
   if (ok) {
@@ -244,8 +253,8 @@ emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, i
     float bt = 1e30f;
     for (int e : {4, 2}) {
       const float ms = time_min(st, a, b, reps, [&] {
-        launch_split(single, false, M + oA, m, k, 1, m, *pl, x, true, kpad, M + opa, st, e);
-        launch_split(single, false, M + oB, n, k, k, 1, *pl, y, true, kpad, M + opb, st, e);
+        launch_split(single, false, M + oA, m, k, 1, m, *pl, x, true, kpad, M + opa, st, e, real);
+        launch_split(single, false, M + oB, n, k, k, 1, *pl, y, true, kpad, M + opb, st, e, real);
       });
       if (ms < bt) {
         bt = ms;
@@ -265,7 +274,7 @@ emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, i
           if (!ok) break;
           const float ms = time_min(st, a, b, reps, [&] {
             launch_gemm_f16(m, n, kpad, *pl, M + opa, M + opb, reinterpret_cast<int8_t*>(M + ores), ldr, c, status,
-                            st, tn, g);
+                            st, tn, g, ppm);
           });
           if (ms < bt) {
             bt = ms;
@@ -279,7 +288,7 @@ emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, i
     for (int r : {4, 2, 1}) {
       const float ms = time_min(st, a, b, reps, [&] {
         launch_crt(single, m, n, *pl, reinterpret_cast<int8_t*>(M + ores), ldr, x, y, 1.0, 0.0, 0.0, 0.0, M + oC, m,
-                   st, r);
+                   st, r, real);
       });
       if (ms < bt) {
         bt = ms;
@@ -299,7 +308,8 @@ emu_status_t emu_autotune_gemm(int is_single, int64_t m, int64_t n, int64_t k, i
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_locked();
-    g_table[key_of(single, num_moduli, m, n, k)] = t;
+    t.nblock = 0;
+    g_table[key_of(dtype, num_moduli, m, n, k)] = t;
     save_locked();
   }
   if (best) {

@@ -47,6 +47,12 @@ _SIGS = [
     ("emu_cgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
                            _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
                            _c_i64, _c_int, _c_ptr]),
+    ("emu_dgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_double),
+                           _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_double), _c_ptr,
+                           _c_i64, _c_int, _c_ptr]),
+    ("emu_sgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
+                           _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
+                           _c_i64, _c_int, _c_ptr]),
     ("emu_grouped_create", _c_int, [_c_int, _c_int, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                     _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_int,
                                     ctypes.POINTER(_c_ptr)]),
@@ -164,6 +170,18 @@ def emu_cgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_
     b = (ctypes.c_float * 2)(float(beta.real), float(beta.imag))
     return lib().emu_cgemm(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc,
                            num_moduli, _stream(stream))
+
+
+def emu_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a, b = ctypes.c_double(float(alpha)), ctypes.c_double(float(beta))
+    return lib().emu_dgemm(_op(transa), _op(transb), m, n, k, ctypes.byref(a), A, lda, B, ldb, ctypes.byref(b),
+                           C, ldc, num_moduli, _stream(stream))
+
+
+def emu_sgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a, b = ctypes.c_float(float(alpha)), ctypes.c_float(float(beta))
+    return lib().emu_sgemm(_op(transa), _op(transb), m, n, k, ctypes.byref(a), A, lda, B, ldb, ctypes.byref(b),
+                           C, ldc, num_moduli, _stream(stream))
 
 
 class GroupedArgs:
@@ -299,8 +317,11 @@ def emu_mlp_choose(theta, features, threshold, n_out, stream=None):
     return lib().emu_mlp_choose(theta, features, float(threshold), n_out, _stream(stream))
 
 
-def emu_workspace_bytes(is_single, m, n, k, num_moduli):
-    return lib().emu_workspace_bytes(int(is_single), m, n, k, num_moduli)
+EMU_DTYPE_Z, EMU_DTYPE_C, EMU_DTYPE_D, EMU_DTYPE_S = 0, 1, 2, 3
+
+
+def emu_workspace_bytes(dtype, m, n, k, num_moduli):
+    return lib().emu_workspace_bytes(int(dtype), m, n, k, num_moduli)
 
 
 def emu_set_workspace(ptr, nbytes):
@@ -313,6 +334,7 @@ def emu_set_engine(engine, chunk_k=0):
 
 EMU_CRT_EXACT, EMU_CRT_PAPER_FP64 = 0, 1
 EMU_TUNE_TILE_N, EMU_TUNE_GROUP, EMU_TUNE_CHUNK_K, EMU_TUNE_CRT_ROWS, EMU_TUNE_SPLIT_ELEMS = 1, 2, 3, 4, 5
+EMU_TUNE_NBLOCK = 6
 
 
 def emu_set_tuning(key, value):
@@ -323,10 +345,11 @@ def emu_get_tuning(key):
     return lib().emu_get_tuning(int(key))
 
 
-def emu_autotune_gemm(is_single, m, n, k, num_moduli):
-    """Returns (status, [tile_n, group, chunk_k, crt_rows, split_elems])."""
+def emu_autotune_gemm(dtype, m, n, k, num_moduli):
+    """Returns (status, [tile_n, group, chunk_k, crt_rows, split_elems]); dtype
+    is an EMU_DTYPE_* code (0/1 = complex128/complex64)."""
     best = (_c_int * 5)()
-    st = lib().emu_autotune_gemm(int(is_single), m, n, k, num_moduli, best)
+    st = lib().emu_autotune_gemm(int(dtype), m, n, k, num_moduli, best)
     return st, list(best)
 
 
@@ -419,12 +442,15 @@ def emu_version():
 def gemm(A_store, B_store, C_store, m, n, k, num_moduli, transa="N", transb="N",
          alpha=1.0, beta=0.0, lda=None, ldb=None, ldc=None, stream=None):
     """Emulated GEMM on column-major matrices held as C-contiguous (cols x ld)
-    torch tensors (complex128 -> ZGEMM, complex64 -> CGEMM).  Raises on error."""
-    single = A_store.dtype == torch.complex64
+    torch tensors (complex128 -> ZGEMM, complex64 -> CGEMM, float64 -> DGEMM,
+    float32 -> SGEMM).  Raises on error."""
+    f = {torch.complex128: emu_zgemm, torch.complex64: emu_cgemm,
+         torch.float64: emu_dgemm, torch.float32: emu_sgemm}[A_store.dtype]
     lda = lda if lda is not None else A_store.shape[-1]
     ldb = ldb if ldb is not None else B_store.shape[-1]
     ldc = ldc if ldc is not None else C_store.shape[-1]
-    f = emu_cgemm if single else emu_zgemm
-    st = f(transa, transb, m, n, k, complex(alpha), A_store.data_ptr(), lda, B_store.data_ptr(), ldb,
-           complex(beta), C_store.data_ptr(), ldc, num_moduli, stream)
-    return check(st, "emu_cgemm" if single else "emu_zgemm")
+    real = not A_store.dtype.is_complex
+    st = f(transa, transb, m, n, k, float(alpha) if real else complex(alpha), A_store.data_ptr(), lda,
+           B_store.data_ptr(), ldb, float(beta) if real else complex(beta), C_store.data_ptr(), ldc, num_moduli,
+           stream)
+    return check(st, f.__name__)

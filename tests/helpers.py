@@ -23,13 +23,14 @@ def host(T, rows):
 
 
 def same_bits(a, b):
-    """Bitwise equality of complex arrays, NaN == NaN (any payload)."""
+    """Bitwise equality of complex or real arrays, NaN == NaN (any payload)."""
     a = np.asarray(a)
     b = np.asarray(b)
     if a.shape != b.shape or a.dtype != b.dtype:
         return False
-    fa = a.view(np.float64 if a.dtype == np.complex128 else np.float32)
-    fb = b.view(np.float64 if b.dtype == np.complex128 else np.float32)
+    wide = a.dtype in (np.complex128, np.float64)
+    fa = a.view(np.float64 if wide else np.float32)
+    fb = b.view(np.float64 if wide else np.float32)
     both_nan = np.isnan(fa) & np.isnan(fb)
     ia = fa.view(np.int64 if fa.dtype == np.float64 else np.int32)
     ib = fb.view(np.int64 if fb.dtype == np.float64 else np.int32)
@@ -52,6 +53,22 @@ def run_gemm(A, B, N, opA="N", opB="N", alpha=1.0, beta=0.0, C=None, single=Fals
     k = A.shape[1] if opA == "N" else A.shape[0]
     n = B.shape[1] if opB == "N" else B.shape[0]
     dt = np.complex64 if single else np.complex128
+    dA = dev(A.astype(dt), lda)
+    dB = dev(B.astype(dt), ldb)
+    Cin = np.zeros((m, n), dtype=dt) if C is None else C.astype(dt)
+    dC = dev(Cin, ldc)
+    emu.gemm(dA, dB, dC, m, n, k, N, opA, opB, alpha, beta, lda=dA.shape[1], ldb=dB.shape[1],
+             ldc=dC.shape[1])
+    torch.cuda.synchronize()
+    return host(dC, m)
+
+
+def run_real(A, B, N, opA="N", opB="N", alpha=1.0, beta=0.0, C=None, single=False, lda=None, ldb=None, ldc=None):
+    """Emulated real op(A) op(B) (DGEMM / SGEMM) through the C ABI; returns numpy."""
+    m = A.shape[0] if opA == "N" else A.shape[1]
+    k = A.shape[1] if opA == "N" else A.shape[0]
+    n = B.shape[1] if opB == "N" else B.shape[0]
+    dt = np.float32 if single else np.float64
     dA = dev(A.astype(dt), lda)
     dB = dev(B.astype(dt), ldb)
     Cin = np.zeros((m, n), dtype=dt) if C is None else C.astype(dt)
