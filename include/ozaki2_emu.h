@@ -91,8 +91,8 @@ emu_status_t emu_cgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
                        const void* B, int64_t ldb, const float* beta,
                        void* C, int64_t ldc, int num_moduli, void* stream);
 
-/* Real analogues (the paper's supplemental real-valued comparison, Section
- * IV): Algorithm 1 on real matrices, one residue product per modulus
+/* Real analogues: Algorithm 1 as Section II states it for real matrices (the
+ * scheme of the real-valued comparison of Section IV-C), one residue product per modulus
  * (E'_l = mod(A'_l B'_l, p_l)), fast-mode scaling on the k entries of each
  * row of op(A) / column of op(B), the same exact CRT.  C = alpha op(A) op(B)
  * + beta C with host scalars alpha and beta; with (alpha, beta) != (1, 0) the

@@ -2,10 +2,10 @@
 
 Oracle (test infrastructure only).
 
-The paper's supplemental comparison (Section IV, "Supplemental Comparison of
-Real-Valued Emulation") runs Algorithm 1 on real matrices: the same steps as
-the complex scheme without the Karatsuba combination, one residue product per
-modulus.  Steps, in the paper's order and notation:
+Algorithm 1 as Section II states it for real matrices (the scheme the paper
+extends to complex products, and the one its real-valued comparison of
+Section IV-C runs): one residue product per modulus, no Karatsuba
+combination.  Steps, in the paper's order and notation:
 
   III   scaling exponents x_i (rows of A) and y_j (columns of B), fast mode:
         the row vector is the k real entries of A(i,:)            [scaling.py]
@@ -15,9 +15,10 @@ modulus.  Steps, in the paper's order and notation:
   V-v   S = sum_l (P/p_l) q_l E'_l;  V-vi  c' = mod(S, P)
   VI    C = diag(mu)^-1 C' diag(nu)^-1, then alpha*C + beta*C_in
 
-The bound of Section III-B carries over unchanged: |c'_ij| <= ||a'_i|| ||b'_j||
-by Cauchy-Schwarz on k-vectors, and the exponent rule keeps that product
-within (P-1)/8, so condition (cond) holds.
+Fast mode (Section II): |c'_ij| <= ||a'_i|| ||b'_j|| by Cauchy-Schwarz on
+k-vectors, and the exponent rule of Section III-B (the same formula the
+complex rows use) keeps that product within (P-1)/8, so condition (cond)
+holds.
 
 Readings (the paper gives no real-domain alpha/beta): with (alpha, beta) !=
 (1, 0) the output is t = RN(alpha * o) and, when beta != 0, u = fma(beta, c, t)

@@ -1,4 +1,5 @@
-"""Build the CUDA library in-tree: paper_2512_08321_gb300/libozaki2emu.so.
+"""Build the CUDA library in-tree: paper_2512_08321_gb300/libozaki2emu.so, and
+the cuBLAS interposer libozaki2emu_preload.so.
 
 Every translation unit under csrc/ is compiled for sm_103a only (one
 -gencode), in parallel, then linked against the shared CUDA runtime so the
@@ -14,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libozaki2emu.so")
+PRELOAD = os.path.join(HERE, "libozaki2emu_preload.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -57,7 +59,29 @@ def build(verbose=False, extra=()):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_preload(nvcc)
     return LIB
+
+
+def build_preload(nvcc=None):
+    """The LD_PRELOAD interposer (host code only): libozaki2emu_preload.so beside
+    the library, linked to it with an $ORIGIN run path; cuBLAS is not linked
+    (its routines are looked up at run time in the libraries loaded after it)."""
+    nvcc = nvcc or _nvcc()
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        raise RuntimeError("g++ not found")
+    tmp = PRELOAD + ".tmp"
+    cmd = [cxx, "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, os.path.join(HERE, "preload", "ozaki2_preload.cpp"),
+           "-I", os.path.join(os.path.dirname(HERE), "include"), "-I", os.path.join(cuda, "include"),
+           "-L", HERE, "-lozaki2emu", "-L", os.path.join(cuda, "lib64"), "-lcudart", "-ldl",
+           "-Wl,-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"preload build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PRELOAD)
+    return PRELOAD
 
 
 if __name__ == "__main__":

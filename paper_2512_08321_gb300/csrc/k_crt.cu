@@ -64,7 +64,8 @@ __device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
   uint64_t q;
   if (sh <= 0) {
     // |c'| < 2^53: the value fits in limbs 0..1
-    const uint64_t v = static_cast<uint64_t>(c[0]) | (L > 1 ? static_cast<uint64_t>(c[1]) << 32 : 0ull);
+    uint64_t v = static_cast<uint64_t>(c[0]);
+    if constexpr (L > 1) v |= static_cast<uint64_t>(c[1]) << 32;
     q = v << (-sh);
   } else {
     // q = bits [sh, sh + 53] of c, plus round and sticky bits
@@ -521,6 +522,7 @@ cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob,
   if (nprob <= 0 || blocks <= 0) return cudaSuccess;
   if (blocks > 2147483647LL) return cudaErrorInvalidValue;
   switch (pl.L) {
+    case 1: return launch_grouped_l<1>(single, probs_dev, nprob, blocks, pl, st);
     case 2: return launch_grouped_l<2>(single, probs_dev, nprob, blocks, pl, st);
     case 3: return launch_grouped_l<3>(single, probs_dev, nprob, blocks, pl, st);
     case 4: return launch_grouped_l<4>(single, probs_dev, nprob, blocks, pl, st);
@@ -555,6 +557,7 @@ cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const 
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ldr % 16 || n > 2147483647LL) return cudaErrorInvalidValue;
   switch (pl.L) {
+    case 1: return launch_l<1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
     case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
     case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
     case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);

@@ -98,3 +98,23 @@ def test_workspace_query(L):
     b16 = emu.emu_workspace_bytes(0, 1000, 900, 700, 16)
     assert 0 < b14 < b16
     assert emu.emu_workspace_bytes(0, -1, 900, 700, 14) == 0
+
+
+INTERPOSED = ["cublasSgemm_v2", "cublasDgemm_v2", "cublasCgemm_v2", "cublasZgemm_v2", "cublasSgemm_v2_64",
+              "cublasDgemm_v2_64", "cublasCgemm_v2_64", "cublasZgemm_v2_64", "cublasGemmEx", "cublasSgemm",
+              "cublasDgemm", "cublasCgemm", "cublasZgemm", "cublasSetKernelStream"]
+
+
+def test_preload_interposer_exports(L):
+    import ctypes
+    from paper_2512_08321_gb300 import build as B
+    if not os.path.exists(B.PRELOAD):
+        B.build_preload()
+    txt = open(os.path.join(ROOT, "include", "ozaki2_preload.h")).read()
+    shim = ctypes.CDLL(B.PRELOAD)
+    for name in INTERPOSED:
+        assert name in txt, name
+        assert hasattr(shim, name), name
+    calls = shim.ozaki2_preload_calls
+    calls.restype = ctypes.c_uint64
+    assert [calls(r, e) for r in range(-1, 7) for e in (0, 1)] == [0] * 16

@@ -158,3 +158,15 @@ def test_real_workspace_bytes_and_invalid_nblock():
     assert emu.emu_workspace_bytes(7, 1000, 900, 700, 14) == 0
     assert emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 100) == emu.EMU_ERR_INVALID_ARG
     assert emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 256) == emu.EMU_OK
+
+
+@pytest.mark.parametrize("N", [2, 3])
+@pytest.mark.parametrize("single", [False, True])
+def test_single_limb_crt_complex(N, single):
+    # N = 2, 3: P < 2^31, the CRT runs on one 32-bit limb
+    A, B = _complex(90, 70, 80, 53, single)
+    from oracle.emulate import emulate
+    ref = emulate(A.astype(np.complex128), B.astype(np.complex128), N,
+                  out_fmt=fp.BINARY32 if single else fp.BINARY64).out
+    got = run_gemm(A, B, N, single=single)
+    assert same_bits(got, ref), mismatch_report(got, ref)
