@@ -64,6 +64,9 @@ def from_dev(p, shape, dtype):
 
 
 def same(a, b):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    if a.shape != b.shape or a.dtype != b.dtype:
+        return False
     wide = a.dtype in (np.float64, np.complex128)
     ia = a.view(np.int64 if wide else np.int32)
     ib = b.view(np.int64 if wide else np.int32)
