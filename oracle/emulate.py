@@ -107,16 +107,24 @@ class Emulation:
     """
 
     def __init__(self, A, B, N, alpha=(1.0, 0.0), beta=(0.0, 0.0), C_in=None,
-                 out_fmt=fp.BINARY64, keep_residue_planes=True, plan=None):
+                 out_fmt=fp.BINARY64, keep_residue_planes=True, plan=None, scaling="fast"):
         A = np.asarray(A)
         B = np.asarray(B)
         self.m, self.k = A.shape
         self.n = B.shape[1]
         self.plan = plan if plan is not None else Plan(N)
         P = self.plan.P
-        # Step III (fast mode)
-        self.x, self.e_a, self.S_a, self.E_a, self.flag_a = vector_exponents(row_vectors(A), P)
-        self.y, self.e_b, self.S_b, self.E_b, self.flag_b = vector_exponents(col_vectors(B), P)
+        # Step III: fast mode, or accurate mode (accurate.py)
+        if scaling == "accurate":
+            from .accurate import accurate_exponents
+            self.accu = accurate_exponents(A, B, P)
+            self.x, self.y = self.accu["x"], self.accu["y"]
+            self.flag_a, self.flag_b = self.accu["flag_a"], self.accu["flag_b"]
+        elif scaling == "fast":
+            self.x, self.e_a, self.S_a, self.E_a, self.flag_a = vector_exponents(row_vectors(A), P)
+            self.y, self.e_b, self.S_b, self.E_b, self.flag_b = vector_exponents(col_vectors(B), P)
+        else:
+            raise ValueError(scaling)
         # Step IV
         self.Ar = truncate(A.real, self.x)
         self.Ai = truncate(A.imag, self.x)

@@ -49,16 +49,24 @@ class RealEmulation:
     out_fmt: fp.BINARY64 (DGEMM) or fp.BINARY32 (SGEMM).
     """
 
-    def __init__(self, A, B, N, alpha=1.0, beta=0.0, C_in=None, out_fmt=fp.BINARY64, plan=None):
+    def __init__(self, A, B, N, alpha=1.0, beta=0.0, C_in=None, out_fmt=fp.BINARY64, plan=None, scaling="fast"):
         A = np.asarray(A, dtype=np.float64)
         B = np.asarray(B, dtype=np.float64)
         self.m, self.k = A.shape
         self.n = B.shape[1]
         self.plan = plan if plan is not None else Plan(N)
         P = self.plan.P
-        # Step III (fast mode) on the real rows of A and columns of B
-        self.x, self.e_a, self.S_a, self.E_a, self.flag_a = vector_exponents(A, P)
-        self.y, self.e_b, self.S_b, self.E_b, self.flag_b = vector_exponents(B.T, P)
+        # Step III on the real rows of A and columns of B: fast or accurate mode
+        if scaling == "accurate":
+            from .accurate import accurate_exponents
+            self.accu = accurate_exponents(A, B, P, real=True)
+            self.x, self.y = self.accu["x"], self.accu["y"]
+            self.flag_a, self.flag_b = self.accu["flag_a"], self.accu["flag_b"]
+        elif scaling == "fast":
+            self.x, self.e_a, self.S_a, self.E_a, self.flag_a = vector_exponents(A, P)
+            self.y, self.e_b, self.S_b, self.E_b, self.flag_b = vector_exponents(B.T, P)
+        else:
+            raise ValueError(scaling)
         # Step IV
         self.Ai = truncate(A, self.x)
         self.Bi = truncate(B.T, self.y).T
