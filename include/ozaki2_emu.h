@@ -282,6 +282,24 @@ emu_status_t emu_autotune_clear(void);
 #define EMU_CRT_PAPER_FP64 1
 emu_status_t emu_set_crt_mode(int mode);
 
+/* Scaling vectors (Algorithm 1 Step III) of emu_zgemm/cgemm/dgemm/sgemm (the
+ * grouped path always uses fast mode):
+ *   EMU_SCALING_FAST (default): fast mode, Section III-B eqs. mu-fast/nu-fast,
+ *     the Cauchy-Schwarz bound decided exactly on quantised row sums;
+ *   EMU_SCALING_ACCURATE: accurate mode, Section III-B eqs. mu-accu/nu-accu:
+ *     rows of op(A) and columns of op(B) pre-scaled by 2^(5 - e) (e = ilogb of
+ *     the largest |entry|), their magnitudes rounded up to integers <= 64, the
+ *     bound product C-bar (complex: C-bar_I = A-bar_I B-bar_R + A-bar_R B-bar_I,
+ *     C-bar_R = C-bar_I + (A-bar_R - A-bar_I)(B-bar_R - B-bar_I)) formed exactly
+ *     on the tensor cores, and x_i = 5 - e_i + max{E : 4^E max(M_i, 1) <= (P-1)/2}
+ *     with M_i = max_j max(C-bar_R, C-bar_I)_ij (y_j likewise over i).  The exact
+ *     CRT then corrects its quotient so that |c'| up to (P-1)/2 is recovered.
+ * A process setting, not per thread. */
+#define EMU_SCALING_FAST 0
+#define EMU_SCALING_ACCURATE 1
+emu_status_t emu_set_scaling(int mode);
+int emu_get_scaling(void);
+
 /* ----------------------------------------------------- stage entry points --
  * The four phases of one emulated GEMM on caller buffers, for stage-wise
  * checking and for composing other pipelines.  is_single selects complex64
@@ -361,6 +379,10 @@ emu_status_t emu_plan_info(int num_moduli, int32_t* moduli, int32_t* q,
  * (sum of ceil(|t| 2^15)^2), i.e. the largest E with 4^E max(2^32,S) <=
  * (P-1) 2^27.  Host only. */
 int emu_plan_exponent(int num_moduli, uint64_t S);
+
+/* Accurate-mode exponent of the library for a bound-product maximum M (< 2^35):
+ * the largest E with 4^E max(M, 1) <= (P-1)/2.  Host only. */
+int emu_plan_exponent_accu(int num_moduli, uint64_t M);
 
 /* 1-based index of the offending argument of the last EMU_ERR_INVALID_ARG
  * returned on this thread (0 if none). */

@@ -12,6 +12,8 @@ namespace emu {
 // Device status word: first device-side error recorded (0 = none).
 __device__ unsigned int g_device_status;
 
+int g_scaling = EMU_SCALING_FAST;
+
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -72,7 +74,7 @@ emu_status_t device_init(int dev, DeviceState*& ds) {
 // (nb == n: one pass).  ppm = residue planes per modulus (3 complex, 1 real).
 struct Layout {
   int64_t kpad, ldr;
-  size_t off_x, off_y, off_scr, off_pa, off_pb, off_res, total;
+  size_t off_x, off_y, off_scr, off_acc, off_pa, off_pb, off_res, total;
 };
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
@@ -87,6 +89,7 @@ Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm = 3, in
   L.off_x = o;   o += al(static_cast<size_t>(m) * 2);
   L.off_y = o;   o += al(static_cast<size_t>(n) * 2);
   L.off_scr = o; o += al(exponents_scratch_bytes(m > nb ? m : nb));
+  L.off_acc = o; o += al(static_cast<size_t>(12) * (m + n));   // accurate mode: e, flag, bound maxima
   L.off_pa = o;  o += al(static_cast<size_t>(ppm * N) * m * L.kpad * esz);
   L.off_pb = o;  o += al(static_cast<size_t>(ppm * N) * nb * L.kpad * esz);
   L.off_res = o; o += al(static_cast<size_t>(ppm * N) * nb * L.ldr);
@@ -240,33 +243,69 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   // element sizes of B and C, to step to a column block
   const size_t in_esz = (dt.real ? 1 : 2) * (dt.single ? 4 : 8);
   const bool conj_a = !dt.real && ta == EMU_OP_C, conj_b = !dt.real && tb == EMU_OP_C;
+  const bool accurate = (g_scaling == EMU_SCALING_ACCURATE);
+  // accurate-mode exponents reach 7 bits further: the split covers them with more chunks
+  Plan pls = *pl;
+  if (accurate) pls.nchunk = pl->nchunk_accu;
+  auto block_ptr = [&](int64_t j0) {
+    return k > 0 ? static_cast<const void*>(static_cast<const char*>(B) + static_cast<size_t>(j0) * rsb * in_esz)
+                 : B;
+  };
   cudaError_t e;
   phase(0, st);
   if (k == 0) {
     // empty inner dimension: the product is zero
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = cudaMemsetAsync(y, 0, static_cast<size_t>(n) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
+  } else if (accurate) {
+    // Section III-B accurate mode: pre-scaling, 7-bit ceiling planes, bound products, exponents
+    int* emA = reinterpret_cast<int*>(ws + L.off_acc);
+    unsigned int* fA = reinterpret_cast<unsigned int*>(emA + m);
+    unsigned int* MA = fA + m;
+    int* emB = reinterpret_cast<int*>(MA + m);
+    unsigned int* fB = reinterpret_cast<unsigned int*>(emB + n);
+    unsigned int* NB = fB + n;
+    if (cudaMemsetAsync(MA, 0, static_cast<size_t>(m) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(NB, 0, static_cast<size_t>(n) * 4, st) != cudaSuccess ||
+        launch_exp_max(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, st) != cudaSuccess ||
+        launch_bound_split(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, L.kpad, pa, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    for (int64_t j0 = 0; j0 < n; j0 += nb) {
+      const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
+      const void* Bj = block_ptr(j0);
+      if (launch_exp_max(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, st) != cudaSuccess ||
+          launch_bound_split(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, L.kpad, pb, st) !=
+              cudaSuccess)
+        return EMU_ERR_CUDA;
+      e = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ds->status, st);
+      if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
+      if (e != cudaSuccess) return EMU_ERR_CUDA;
+    }
+    if (launch_accu_finalize(m, emA, fA, MA, *pl, x, st) != cudaSuccess ||
+        launch_accu_finalize(n, emB, fB, NB, *pl, y, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
   } else {
     if ((e = launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, st, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
   }
   for (int64_t j0 = 0; j0 < n; j0 += nb) {
     const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
-    const void* Bj = k > 0 ? static_cast<const char*>(B) + static_cast<size_t>(j0) * rsb * in_esz : B;
+    const void* Bj = block_ptr(j0);
     void* Cj = static_cast<char*>(C) + static_cast<size_t>(j0) * ldc * in_esz;
     int16_t* yj = y + j0;
     if (k == 0) {
       if ((e = cudaMemsetAsync(res, 0, static_cast<size_t>(ppm * N) * nj * L.ldr, st)) != cudaSuccess)
         return EMU_ERR_CUDA;
     } else {
-      if ((e = launch_exponents(dt.single, Bj, nj, k, rsb, hsb, *pl, yj, scr, st, dt.real)) != cudaSuccess)
+      if (!accurate &&
+          (e = launch_exponents(dt.single, Bj, nj, k, rsb, hsb, *pl, yj, scr, st, dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
       phase(1, st);
       if (j0 == 0 &&
-          (e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, *pl, x, fp16, L.kpad, pa, st, tn.split_elems,
+          (e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, st, tn.split_elems,
                             dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
-      if ((e = launch_split(dt.single, conj_b, Bj, nj, k, rsb, hsb, *pl, yj, fp16, L.kpad, pb, st, tn.split_elems,
+      if ((e = launch_split(dt.single, conj_b, Bj, nj, k, rsb, hsb, pls, yj, fp16, L.kpad, pb, st, tn.split_elems,
                             dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
       phase(2, st);
@@ -277,7 +316,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     s = cuda_status(g_crt_mode == 1
                         ? launch_crt_fp(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st, dt.real)
                         : launch_crt(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st,
-                                     tn.crt_rows, dt.real));
+                                     tn.crt_rows, dt.real, accurate));
     if (s != EMU_OK) return s;
   }
   phase(4, st);
@@ -481,6 +520,14 @@ emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli, 
                               : emu::launch_crt(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
                                                 ldc, st));
 }
+
+emu_status_t emu_set_scaling(int mode) {
+  if (mode != EMU_SCALING_FAST && mode != EMU_SCALING_ACCURATE) return emu::bad(1);
+  emu::g_scaling = mode;
+  return EMU_OK;
+}
+
+int emu_get_scaling(void) { return emu::g_scaling; }
 
 emu_status_t emu_set_crt_mode(int mode) {
   if (mode != EMU_CRT_EXACT && mode != EMU_CRT_PAPER_FP64) return emu::bad(1);

@@ -16,6 +16,7 @@ constexpr int kPow2Table = 128;     // 2^s mod p for s in [0, 128)
 constexpr int kChunkBits = 13;      // residue split: a' in signed 13-bit chunks
 constexpr int kMaxChunks = 8;       // 8 x 13 = 104 bits > every |a'| (< 2^97)
 constexpr int kSumFracBits = 15;    // row sums use ceil(|t| 2^15), Section III-B reading
+constexpr int kAccuPreBits = 5;     // accurate mode: pre-scaling 2^(5 - e), magnitudes below 2^6
 constexpr int16_t kExpNonfinite = EMU_EXP_NONFINITE;
 // moduli-selection network
 constexpr int kMlpIn = 39, kMlpHidden = 64, kMlpOut = 21, kMlpNmin = 4;
@@ -37,8 +38,11 @@ struct Plan {
   uint32_t w[kMaxModuli][kMaxLimbs];      // w_l = (P/p_l) q_l, little endian
   uint32_t negP[kMaxLimbs];               // 2^(32L) - P
   uint32_t K[kMaxLimbs];                  // R0*P - 128*sum_l w_l  (mod 2^(32L))
+  uint32_t Pw[kMaxLimbs];                 // P
+  uint32_t H[kMaxLimbs];                  // (P - 1) / 2
   uint8_t pow2[kMaxModuli][kPow2Table];   // 2^s mod p_l
   int nchunk;                             // 13-bit chunks covering every |a'| (< 2^(Emax+1))
+  int nchunk_accu;                        // the same for accurate-mode exponents
   float w13[kMaxModuli][kMaxChunks];      // 2^(13 t) mod p_l, symmetric, as float
   float inv_p[kMaxModuli];                // 1 / p_l rounded to float
   // the paper's floating-point CRT (Section II, eq. CRTaccumulation)
@@ -51,6 +55,7 @@ struct Plan {
 // Host: build (and cache) the plan of N moduli; nullptr when N is out of range.
 const Plan* get_plan(int N);
 int plan_exponent(const Plan& pl, uint64_t S);
+int plan_exponent_accu(const Plan& pl, uint64_t M);
 
 // Device status word helpers (api.cu).
 unsigned int* device_status_ptr();
@@ -60,6 +65,24 @@ cudaError_t launch_exponents(bool single, const void* X, int64_t rows, int64_t k
                              int64_t rs, int64_t hs, const Plan& pl, int16_t* xout,
                              void* scratch, cudaStream_t st, bool real = false);
 size_t exponents_scratch_bytes(int64_t rows);
+
+// Accurate-mode scaling (Section III-B, eqs. mu-accu / nu-accu):
+//   launch_exp_max        row maxima of ilogb (offset 2048; 0 = zero row) and Inf/NaN flags
+//   launch_bound_split    7-bit ceiling planes ceil(|v| 2^(5-e)) as fp16, [planes][rows][kpad]:
+//                         complex 3 planes (Re, Im, Re - Im), real 1; flagged rows are zero
+//   launch_gemm_bound     exact bound products on tcgen05; atomicMax of the row maxima into
+//                         Mrow[m] and of the column maxima into Ncol[n] (both zeroed by the caller)
+//   launch_accu_finalize  x_r = 5 - e_r + max{E : 4^E max(M_r,1) <= (P-1)/2}
+cudaError_t launch_exp_max(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
+                           int* emax, unsigned int* flag, cudaStream_t st);
+cudaError_t launch_bound_split(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs,
+                               int64_t hs, const int* emax, const unsigned int* flag, int64_t kpad, void* planes,
+                               cudaStream_t st);
+cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, const void* planesA,
+                              const void* planesB, unsigned int* Mrow, unsigned int* Ncol, unsigned int* status,
+                              cudaStream_t st);
+cudaError_t launch_accu_finalize(int64_t rows, const int* emax, const unsigned int* flag, const unsigned int* Mb,
+                                 const Plan& pl, int16_t* xout, cudaStream_t st);
 
 // Launch-configuration knobs of one GEMM (process defaults, autotuned per shape bucket).
 struct Tune {
@@ -94,12 +117,14 @@ cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        const int8_t* res, int64_t ldr, const int16_t* x, const int16_t* y,
                        double ar, double ai, double br, double bi,
-                       void* C, int64_t ldc, cudaStream_t st, int rows_per_thread = 4, bool real = false);
+                       void* C, int64_t ldc, cudaStream_t st, int rows_per_thread = 4, bool real = false,
+                       bool robust = false);
 
 cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                           const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
                           int64_t ldc, cudaStream_t st, bool real = false);
 extern int g_crt_mode;   // 0: exact integer CRT, 1: the paper's floating-point CRT
+extern int g_scaling;    // EMU_SCALING_FAST or EMU_SCALING_ACCURATE
 
 cudaError_t launch_bounded_wait_selftest(int64_t limit_cycles, unsigned int* status,
                                          cudaStream_t st);

@@ -96,8 +96,51 @@ __device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
-// Finish one part: add the quotient term, carry once, round.
+// Accurate-mode range fix: |c'| <= (P-1)/2 there, so the float quotient can be
+// one off near the ends of the range and c holds c' - P or c' + P.  With H =
+// (P-1)/2: c > H (H - c < 0) means c -= P; c < -H (c + H < 0) means c += P.
+// The limbs hold these values without wrapping (2^(32L-1) > 2P).
 template <int L>
+__device__ __forceinline__ void fix_range(uint32_t (&c)[L], const Plan& pl) {
+  uint32_t d[L];
+  int64_t b = 0;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {        // d = H - c
+    const int64_t v = static_cast<int64_t>(pl.H[t]) - static_cast<int64_t>(c[t]) + b;
+    d[t] = static_cast<uint32_t>(v);
+    b = v >> 32;
+  }
+  if (d[L - 1] >> 31) {                // c > H: c -= P
+    b = 0;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const int64_t v = static_cast<int64_t>(c[t]) - static_cast<int64_t>(pl.Pw[t]) + b;
+      c[t] = static_cast<uint32_t>(v);
+      b = v >> 32;
+    }
+    return;
+  }
+  uint64_t cy = 0;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {        // d = c + H
+    const uint64_t v = static_cast<uint64_t>(c[t]) + pl.H[t] + cy;
+    d[t] = static_cast<uint32_t>(v);
+    cy = v >> 32;
+  }
+  if (d[L - 1] >> 31) {                // c < -H: c += P
+    cy = 0;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+      const uint64_t v = static_cast<uint64_t>(c[t]) + pl.Pw[t] + cy;
+      c[t] = static_cast<uint32_t>(v);
+      cy = v >> 32;
+    }
+  }
+}
+
+// Finish one part: add the quotient term, carry once, (accurate mode) fix the
+// range, round.
+template <int L, bool ROBUST>
 __device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, const Plan& pl, int e2) {
   const uint32_t rq = static_cast<uint32_t>(static_cast<int>(rintf(est)) + pl.R0);
   uint32_t c[L];
@@ -108,6 +151,7 @@ __device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, co
     c[t] = static_cast<uint32_t>(v);
     carry = v >> 32;
   }
+  if constexpr (ROBUST) fix_range<L>(c, pl);
   return round_limbs<L>(c, e2);
 }
 
@@ -127,7 +171,7 @@ struct Word<4> {
   __device__ static uint32_t load(const int8_t* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
 };
 
-template <int L, bool SINGLE, int kRowsPerThread>
+template <int L, bool SINGLE, int kRowsPerThread, bool ROBUST = false>
 __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
                                           int64_t ldr, const int16_t* __restrict__ x, const int16_t* __restrict__ y,
                                           double ar, double ai, double br, double bi, void* __restrict__ Cv,
@@ -190,8 +234,8 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
       orr = oi = __longlong_as_double(0x7FF8000000000000ll);
     } else {
       const int e2 = -(xi + yj);
-      orr = finish<L>(accR[q], estR[q], pl, e2);
-      oi = finish<L>(accI[q], estI[q], pl, e2);
+      orr = finish<L, ROBUST>(accR[q], estR[q], pl, e2);
+      oi = finish<L, ROBUST>(accI[q], estI[q], pl, e2);
     }
     const int64_t ci = j * ldc + i;
     if (!plain) {
@@ -224,7 +268,7 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
 
 // Real input (DGEMM/SGEMM emulation): E'_l is the residue of job l itself; one
 // accumulator per row.  alpha/beta: t = RN(alpha o), then fma(beta, c, t).
-template <int L, bool SINGLE, int kRowsPerThread>
+template <int L, bool SINGLE, int kRowsPerThread, bool ROBUST>
 __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
                                                int64_t ldr, const int16_t* __restrict__ x,
                                                const int16_t* __restrict__ y, double ar, double br,
@@ -264,7 +308,7 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
     if (i >= m) break;
     const int xi = x[i];
     double o = (xi == kExpNonfinite || yj == kExpNonfinite) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                            : finish<L>(acc[q], est[q], pl, -(xi + yj));
+                                                            : finish<L, ROBUST>(acc[q], est[q], pl, -(xi + yj));
     const int64_t ci = j * ldc + i;
     if (!plain) {
       double t = __dmul_rn(ar, o);
@@ -277,16 +321,16 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
   }
 }
 
-template <int L, bool SINGLE, int R>
+template <int L, bool SINGLE, int R, bool ROBUST>
 __global__ void __launch_bounds__(kThreads) crt_real_kernel(int64_t m, int64_t n, const __grid_constant__ Plan pl,
                                                             const int8_t* __restrict__ res, int64_t ldr,
                                                             const int16_t* __restrict__ x,
                                                             const int16_t* __restrict__ y, double ar, double br,
                                                             void* __restrict__ Cv, int64_t ldc) {
-  crt_block_real<L, SINGLE, R>(m, n, pl, res, ldr, x, y, ar, br, Cv, ldc, blockIdx.x, blockIdx.y);
+  crt_block_real<L, SINGLE, R, ROBUST>(m, n, pl, res, ldr, x, y, ar, br, Cv, ldc, blockIdx.x, blockIdx.y);
 }
 
-template <int L, bool SINGLE, int R>
+template <int L, bool SINGLE, int R, bool ROBUST>
 __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
                                                        const __grid_constant__ Plan pl,
                                                        const int8_t* __restrict__ res, int64_t ldr,
@@ -294,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
                                                        const int16_t* __restrict__ y, double ar,
                                                        double ai, double br, double bi,
                                                        void* __restrict__ Cv, int64_t ldc) {
-  crt_block<L, SINGLE, R>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, Cv, ldc, blockIdx.x, blockIdx.y);
+  crt_block<L, SINGLE, R, ROBUST>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, Cv, ldc, blockIdx.x, blockIdx.y);
 }
 
 // one launch over every problem of a grouped call: blocks are (column, row block) of each problem
@@ -313,20 +357,29 @@ __global__ void __launch_bounds__(kThreads) crt_grouped(const CrtProb* __restric
                           local / c.iblocks, local % c.iblocks);
 }
 
+template <int L, int R, bool ROBUST>
+void launch_lrr(bool single, bool real, dim3 grid, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
+                int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
+                int64_t ldc, cudaStream_t st) {
+  if (real) {
+    if (single) crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+    else crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+  } else if (single) {
+    crt_kernel<L, true, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  } else {
+    crt_kernel<L, false, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  }
+}
+
 template <int L, int R>
 cudaError_t launch_lr(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                       const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
-                      int64_t ldc, cudaStream_t st, bool real) {
+                      int64_t ldc, cudaStream_t st, bool real, bool robust) {
   const int64_t per_block = static_cast<int64_t>(kThreads) * R;
   if ((m + per_block - 1) / per_block > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>(n), static_cast<unsigned int>((m + per_block - 1) / per_block));
-  if (real) {
-    if (single) crt_real_kernel<L, true, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
-    else crt_real_kernel<L, false, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
-  } else if (single)
-    crt_kernel<L, true, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
-  else
-    crt_kernel<L, false, R><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+  if (robust) launch_lrr<L, R, true>(single, real, grid, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
+  else launch_lrr<L, R, false>(single, real, grid, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -334,11 +387,12 @@ cudaError_t launch_lr(bool single, int64_t m, int64_t n, const Plan& pl, const i
 template <int L>
 cudaError_t launch_l(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                      int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
-                     double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real) {
+                     double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real,
+                     bool robust) {
   switch (rows) {
-    case 1: return launch_lr<L, 1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real);
-    case 2: return launch_lr<L, 2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real);
-    default: return launch_lr<L, 4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real);
+    case 1: return launch_lr<L, 1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real, robust);
+    case 2: return launch_lr<L, 2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real, robust);
+    default: return launch_lr<L, 4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, real, robust);
   }
 }
 
@@ -553,16 +607,17 @@ cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, con
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                        int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai,
-                       double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real) {
+                       double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real,
+                       bool robust) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ldr % 16 || n > 2147483647LL) return cudaErrorInvalidValue;
   switch (pl.L) {
-    case 1: return launch_l<1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
-    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
-    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
-    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
-    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
-    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real);
+    case 1: return launch_l<1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
+    case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
+    case 3: return launch_l<3>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
+    case 4: return launch_l<4>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
+    case 5: return launch_l<5>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
+    case 6: return launch_l<6>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -100,8 +100,8 @@ __device__ __forceinline__ unsigned long long ceil_q(typename Bits<S>::U u, int 
   return q + ((m & ((1ull << s) - 1)) != 0ull ? 1ull : 0ull);
 }
 
-__device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long long S) {
-  const unsigned long long M = S > (1ull << 32) ? S : (1ull << 32);
+// Largest E with 4^E * M <= X = (P-1) 2^27 (M >= 1).
+__device__ __forceinline__ int exponent_le(const Plan& pl, unsigned long long M) {
   const int bm = 64 - __clzll(M);
   const int bx = pl.sX + (64 - __clzll(pl.Xtop));
   auto fits = [&](int E) -> bool {
@@ -117,6 +117,11 @@ __device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long l
   while (!fits(E)) --E;
   while (fits(E + 1)) ++E;
   return E;
+}
+
+// Fast mode: 4^E max(2^32, S) <= (P-1) 2^27.
+__device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long long S) {
+  return exponent_le(pl, S > (1ull << 32) ? S : (1ull << 32));
 }
 
 // ---- pass 1: max exponent and non-finite flag (one block: row block rb, h chunk hc)
@@ -312,6 +317,42 @@ cudaError_t launch_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t
   return cudaGetLastError();
 }
 
+// ---- accurate mode (Section III-B, eqs. mu-accu / nu-accu): x_r = 5 - e_r + E_r with
+// E_r = max{E : 4^E max(M_r, 1) <= (P-1)/2}, M_r the row (column) maximum of the
+// bound products, i.e. 4^E max(M_r, 1) 2^28 <= (P-1) 2^27.
+__global__ void accu_finalize_kernel(int64_t rows, const int* __restrict__ emax, const unsigned int* __restrict__ flag,
+                                     const unsigned int* __restrict__ Mb, const __grid_constant__ Plan pl,
+                                     int16_t* __restrict__ xout) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  if (flag[r]) {
+    xout[r] = kExpNonfinite;
+    return;
+  }
+  const int e = emax[r] ? emax[r] - 2048 : 0;
+  const unsigned long long M = Mb[r] > 1u ? Mb[r] : 1u;
+  xout[r] = static_cast<int16_t>(kAccuPreBits - e + exponent_le(pl, M << 28));
+}
+
+template <bool S, bool R>
+cudaError_t launch_max_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs, int* emax,
+                         unsigned int* flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(emax, 0, static_cast<size_t>(rows) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, static_cast<size_t>(rows) * 4, st);
+  if (e != cudaSuccess) return e;
+  const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
+  if (ychunks == 0) return cudaSuccess;
+  if (rs == 1) {
+    dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
+    exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
+  } else {
+    dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
+    exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // ---- features of the moduli-selection network
 // 16-bin histogram of exponent spans d = e_r - ilogb|v| (zero entries: bin 15)
 template <bool S, bool ROWS_CONTIG>
@@ -490,6 +531,25 @@ cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, int ns
         segs_dev, nseg, row_begin_dev, total_rows, pl);
     count_launches(1);
   }
+  return cudaGetLastError();
+}
+
+// Row maxima of ilogb (offset 2048, 0 = zero row) and non-finite flags only (accurate mode).
+cudaError_t launch_exp_max(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
+                           int* emax, unsigned int* flag, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  if (real)
+    return single ? launch_max_t<true, true>(X, rows, k, rs, hs, emax, flag, st)
+                  : launch_max_t<false, true>(X, rows, k, rs, hs, emax, flag, st);
+  return single ? launch_max_t<true, false>(X, rows, k, rs, hs, emax, flag, st)
+                : launch_max_t<false, false>(X, rows, k, rs, hs, emax, flag, st);
+}
+
+cudaError_t launch_accu_finalize(int64_t rows, const int* emax, const unsigned int* flag, const unsigned int* Mb,
+                                 const Plan& pl, int16_t* xout, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  accu_finalize_kernel<<<static_cast<unsigned int>((rows + 255) / 256), 256, 0, st>>>(rows, emax, flag, Mb, pl, xout);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -248,6 +248,98 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   }
 }
 
+// ---- accurate mode: the 7-bit ceiling planes of Section III-B.  For a row r
+// with ilogb of its largest |entry| e_r, each entry becomes ceil(|v| 2^(5 - e_r))
+// (an integer in [0, 64]; a nonzero entry too small to register has ceiling 1).
+// Complex rows give plane 0 = ceil |Re|, plane 1 = ceil |Im|, plane 2 = their
+// difference; real rows give plane 0.  Flagged rows and non-finite entries are 0.
+template <bool SINGLE>
+__device__ __forceinline__ float ceil_scaled(uint64_t bits, int e) {
+  uint64_t m;
+  int elsb;
+  if (SINGLE) {
+    const uint32_t b = static_cast<uint32_t>(bits) & 0x7FFFFFFFu;
+    const int ex = static_cast<int>(b >> 23);
+    m = ex ? ((b & 0x7FFFFFu) | 0x800000u) : b;
+    elsb = ex ? ex - 150 : -149;
+  } else {
+    const uint64_t b = bits & 0x7FFFFFFFFFFFFFFFull;
+    const int ex = static_cast<int>(b >> 52);
+    m = ex ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : b;
+    elsb = ex ? ex - 1075 : -1074;
+  }
+  if (m == 0) return 0.0f;
+  const int s = elsb + kAccuPreBits - e;       // |v| 2^(5-e) = m 2^s < 2^6
+  uint64_t q;
+  if (s >= 0) q = m << s;                      // only for tiny m: the value stays below 64
+  else if (-s >= 64) q = 1;
+  else q = (m >> (-s)) + (((m & ((1ull << (-s)) - 1ull)) != 0ull) ? 1ull : 0ull);
+  return static_cast<float>(q);
+}
+
+template <bool SINGLE, bool ROWS_CONTIG, bool R>
+__global__ void __launch_bounds__(kThreads) bound_split_kernel(const void* __restrict__ Xv, int64_t rows, int64_t k,
+                                                               int64_t rs, int64_t hs, const int* __restrict__ emax,
+                                                               const unsigned int* __restrict__ flag, int64_t kpad,
+                                                               __half* __restrict__ planes) {
+  __shared__ SplitSmem sm;
+  const int tid = threadIdx.x;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kTileR;
+  const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kTileH;
+#pragma unroll
+  for (int it = 0; it < (kTileR * kTileH) / kThreads; ++it) {
+    int rr, hh;
+    if (ROWS_CONTIG) {
+      rr = tid & 31;
+      hh = (tid >> 5) + 8 * it;
+    } else {
+      hh = tid & 31;
+      rr = (tid >> 5) + 8 * it;
+    }
+    const int64_t r = r0 + rr, h = h0 + hh;
+    uint64_t bre = 0, bim = 0;
+    if (r < rows && h < k) {
+      const int64_t off = r * rs + h * hs;
+      if constexpr (R) {
+        bre = SINGLE ? static_cast<uint64_t>(__float_as_uint(static_cast<const float*>(Xv)[off]))
+                     : static_cast<uint64_t>(__double_as_longlong(static_cast<const double*>(Xv)[off]));
+      } else if (SINGLE) {
+        const float2 v = static_cast<const float2*>(Xv)[off];
+        bre = __float_as_uint(v.x);
+        bim = __float_as_uint(v.y);
+      } else {
+        const double2 v = static_cast<const double2*>(Xv)[off];
+        bre = static_cast<uint64_t>(__double_as_longlong(v.x));
+        bim = static_cast<uint64_t>(__double_as_longlong(v.y));
+      }
+    }
+    sm.tre[rr][hh] = bre;
+    sm.tim[rr][hh] = bim;
+  }
+  __syncthreads();
+  // each thread: 4 consecutive h of one row, 8 threads per row, 32 rows per pass
+  const int rr = tid / 8;
+  const int hb = (tid % 8) * 4;
+  const int64_t r = r0 + rr;
+  if (r >= rows) return;
+  const bool zero = flag[r] != 0;
+  const int e = emax[r] ? emax[r] - 2048 : 0;
+  float vr[4], vi[4], vd[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    vr[j] = zero ? 0.0f : ceil_scaled<SINGLE>(sm.tre[rr][hb + j], e);
+    vi[j] = (zero || R) ? 0.0f : ceil_scaled<SINGLE>(sm.tim[rr][hb + j], e);
+    vd[j] = vr[j] - vi[j];
+  }
+  const int64_t plane = rows * kpad;
+  __half* dst = planes + r * kpad + h0 + hb;
+  StoreE<__half, 4>::put(dst, vr);
+  if constexpr (!R) {
+    StoreE<__half, 4>::put(dst + plane, vi);
+    StoreE<__half, 4>::put(dst + 2 * plane, vd);
+  }
+}
+
 template <bool SINGLE, bool ROWS_CONTIG, typename T, int E, bool R>
 __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict__ Xv, int64_t rows,
                                                          int64_t k, int64_t rs, int64_t hs,
@@ -328,6 +420,28 @@ cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_de
   }
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <bool S, bool R>
+cudaError_t bound_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs, const int* emax,
+                    const unsigned int* flag, int64_t kpad, void* planes, cudaStream_t st) {
+  dim3 grid(static_cast<unsigned int>((rows + kTileR - 1) / kTileR), static_cast<unsigned int>(kpad / kTileH));
+  __half* P = static_cast<__half*>(planes);
+  if (rs == 1) bound_split_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, kpad, P);
+  else bound_split_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, kpad, P);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bound_split(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs,
+                               int64_t hs, const int* emax, const unsigned int* flag, int64_t kpad, void* planes,
+                               cudaStream_t st) {
+  if (rows <= 0 || kpad <= 0) return cudaSuccess;
+  if (kpad % 64 || (rows + kTileR - 1) / kTileR > 2147483647LL || kpad / kTileH > 65535) return cudaErrorInvalidValue;
+  if (real) return single ? bound_t<true, true>(X, rows, k, rs, hs, emax, flag, kpad, planes, st)
+                          : bound_t<false, true>(X, rows, k, rs, hs, emax, flag, kpad, planes, st);
+  return single ? bound_t<true, false>(X, rows, k, rs, hs, emax, flag, kpad, planes, st)
+                : bound_t<false, false>(X, rows, k, rs, hs, emax, flag, kpad, planes, st);
 }
 
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,

@@ -160,7 +160,8 @@ void build(int N, Plan& pl) {
   Big P(1);
   for (int l = 0; l < N; ++l) mul_small(P, static_cast<uint32_t>(pl.p[l]));
   const int bitsP = bitlen(P);
-  pl.L = (bitsP + 1 + 31) / 32;
+  // limbs hold c' + {-P, 0, P} with |c'| <= P/2 (accurate mode) in two's complement: 2^(32L-1) > 2P
+  pl.L = (bitsP + 2 + 31) / 32;
   // Step II and the CRT weights
   Big sumw;
   for (int l = 0; l < N; ++l) {
@@ -239,9 +240,14 @@ void build(int N, Plan& pl) {
   Big w128 = sumw;
   mul_small(w128, 128u);
   sub(K, w128);
+  Big H = P;                                   // (P - 1) / 2
+  sub(H, Big(1));
+  divmod_small(H, 2u);
   for (int t = 0; t < kMaxLimbs; ++t) {
     pl.negP[t] = t < pl.L ? negP.v[t] : 0u;
     pl.K[t] = t < pl.L ? K.v[t] : 0u;
+    pl.Pw[t] = t < pl.L ? P.v[t] : 0u;
+    pl.H[t] = t < pl.L ? H.v[t] : 0u;
   }
   // X = (P - 1) 2^27 for the fast-mode exponent rule
   Big X = P;
@@ -254,6 +260,10 @@ void build(int N, Plan& pl) {
   const int Emax = plan_exponent(pl, 0);
   pl.nchunk = (Emax + 1 + kChunkBits - 1) / kChunkBits;
   if (pl.nchunk < 1) pl.nchunk = 1;
+  // accurate mode: |a'| < 64 * 2^E with E at most its value for a bound of 1
+  const int Eaccu = plan_exponent_accu(pl, 1);
+  pl.nchunk_accu = (Eaccu + 6 + kChunkBits - 1) / kChunkBits;
+  if (pl.nchunk_accu < 1) pl.nchunk_accu = 1;
 }
 
 std::mutex g_mu;
@@ -272,10 +282,9 @@ const Plan* get_plan(int N) {
   return &g_plans[N];
 }
 
-// Largest E with 4^E * max(2^32, S) <= X, X = (P-1) 2^27 = Xtop 2^sX + rest.
+// Largest E with 4^E * M <= X, X = (P-1) 2^27 = Xtop 2^sX + rest, for M >= 1.
 // Shared by host queries; the device copy lives in k_scale.cu.
-int plan_exponent(const Plan& pl, uint64_t S) {
-  const uint64_t M = S > (1ull << 32) ? S : (1ull << 32);
+int exponent_le(const Plan& pl, uint64_t M) {
   const int bm = 64 - __builtin_clzll(M);
   const int bx = pl.sX + (64 - __builtin_clzll(pl.Xtop));
   auto fits = [&](int E) -> bool {
@@ -292,6 +301,12 @@ int plan_exponent(const Plan& pl, uint64_t S) {
   while (fits(E + 1)) ++E;
   return E;
 }
+
+// Fast mode: largest E with 4^E * max(2^32, S) <= (P-1) 2^27.
+int plan_exponent(const Plan& pl, uint64_t S) { return exponent_le(pl, S > (1ull << 32) ? S : (1ull << 32)); }
+
+// Accurate mode: largest E with 4^E * max(M, 1) <= (P-1)/2, i.e. 4^E max(M,1) 2^28 <= X.
+int plan_exponent_accu(const Plan& pl, uint64_t M) { return exponent_le(pl, (M > 1 ? M : 1ull) << 28); }
 
 }  // namespace emu
 
@@ -331,6 +346,12 @@ int emu_plan_exponent(int num_moduli, uint64_t S) {
   const emu::Plan* pl = emu::get_plan(num_moduli);
   if (!pl) return -100000;
   return emu::plan_exponent(*pl, S);
+}
+
+int emu_plan_exponent_accu(int num_moduli, uint64_t M) {
+  const emu::Plan* pl = emu::get_plan(num_moduli);
+  if (!pl || M >= (1ull << 35)) return -100000;
+  return emu::plan_exponent_accu(*pl, M);
 }
 
 }  // extern "C"

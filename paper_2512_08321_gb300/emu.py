@@ -88,6 +88,9 @@ _SIGS = [
     ("emu_get_tuning", _c_int, [_c_int]),
     ("emu_autotune_gemm", _c_int, [_c_int, _c_i64, _c_i64, _c_i64, _c_int, ctypes.POINTER(_c_int)]),
     ("emu_autotune_clear", _c_int, []),
+    ("emu_set_scaling", _c_int, [_c_int]),
+    ("emu_get_scaling", _c_int, []),
+    ("emu_plan_exponent_accu", _c_int, [_c_int, ctypes.c_uint64]),
     ("emu_stage_exponents", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
                                      _c_ptr, _c_i64, _c_int, _c_ptr, _c_ptr, _c_ptr]),
     ("emu_stage_exponents_static", _c_int, [_c_int, _c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_ptr, _c_i64,
@@ -355,6 +358,21 @@ def emu_autotune_gemm(dtype, m, n, k, num_moduli):
 
 def emu_autotune_clear():
     return lib().emu_autotune_clear()
+
+
+EMU_SCALING_FAST, EMU_SCALING_ACCURATE = 0, 1
+
+
+def emu_set_scaling(mode):
+    return lib().emu_set_scaling(int(mode))
+
+
+def emu_get_scaling():
+    return lib().emu_get_scaling()
+
+
+def emu_plan_exponent_accu(num_moduli, M):
+    return lib().emu_plan_exponent_accu(int(num_moduli), int(M))
 
 
 def emu_set_crt_mode(mode):

@@ -50,7 +50,7 @@ def test_plan_matches_oracle(L, N):
     ref = Plan(N)
     assert st == emu.EMU_OK
     assert mod == ref.p and q == ref.q and P == ref.P
-    assert 2 ** (32 * limbs - 1) > ref.P // 8            # c' fits the two's-complement limbs
+    assert 2 ** (32 * limbs - 1) > 2 * ref.P             # c' + {-P, 0, P} fits the two's-complement limbs
 
 
 @pytest.mark.parametrize("N", [2, 5, 8, 14, 20, 24])
@@ -118,3 +118,14 @@ def test_preload_interposer_exports(L):
     calls = shim.ozaki2_preload_calls
     calls.restype = ctypes.c_uint64
     assert [calls(r, e) for r in range(-1, 7) for e in (0, 1)] == [0] * 16
+
+
+@pytest.mark.parametrize("N", [2, 5, 12, 15, 24])
+def test_plan_exponent_accu_matches_oracle(L, N):
+    from oracle.accurate import exponent_accu
+    P = Plan(N).P
+    rng = np.random.default_rng(100 + N)
+    Ms = [0, 1, 2, 3, 63, 64, 4095, 4096, 2 ** 30, 2 ** 31 - 1] + [int(v) for v in rng.integers(0, 2 ** 31, 200)]
+    for M in Ms:
+        assert emu.emu_plan_exponent_accu(N, M) == exponent_accu(M, P), M
+    assert emu.emu_plan_exponent_accu(N, 2 ** 35) == -100000

@@ -1,0 +1,164 @@
+"""GPU parity of accurate-mode scaling (Section III-B, eqs. mu-accu / nu-accu):
+exponents and results bit for bit against the CPU oracle for all four element
+types, the exact bound products across several k chunks, column blocking,
+edge cases, and the CRT's range correction near |c'| = P/2."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fp
+from oracle.crt_fp import outputs, outputs_real
+from oracle.emulate import Emulation, apply_op
+from oracle.emulate_real import RealEmulation, apply_op_real
+from paper_2512_08321_gb300 import emu
+from paper_2512_08321_gb300.workloads import paper_matrix, paper_matrix_real
+
+from .helpers import mismatch_report, run_gemm, run_real, same_bits
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _accurate():
+    emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE), "scaling")
+    yield
+    emu.emu_set_scaling(emu.EMU_SCALING_FAST)
+    emu.emu_set_crt_mode(emu.EMU_CRT_EXACT)
+    emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 0)
+
+
+def _cplx(m, n, k, opA, opB, phi, seed, single):
+    A = paper_matrix(m, k, phi, seed) if opA == "N" else paper_matrix(k, m, phi, seed)
+    B = paper_matrix(k, n, phi, seed + 1) if opB == "N" else paper_matrix(n, k, phi, seed + 1)
+    if single:
+        A, B = A.astype(np.complex64), B.astype(np.complex64)
+    return A, B
+
+
+def _real(m, n, k, opA, opB, phi, seed, single):
+    A = paper_matrix_real(m, k, phi, seed) if opA == "N" else paper_matrix_real(k, m, phi, seed)
+    B = paper_matrix_real(k, n, phi, seed + 1) if opB == "N" else paper_matrix_real(n, k, phi, seed + 1)
+    if single:
+        A, B = A.astype(np.float32), B.astype(np.float32)
+    return A, B
+
+
+def test_scaling_switch():
+    assert emu.emu_get_scaling() == emu.EMU_SCALING_ACCURATE
+    assert emu.emu_set_scaling(7) == emu.EMU_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("single", [False, True])
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("C", "T")])
+def test_complex_accurate_bitexact(single, opA, opB):
+    N = 7 if single else 13
+    A, B = _cplx(300, 260, 333, opA, opB, 2.0, 80, single)
+    em = Emulation(apply_op(A.astype(np.complex128), opA), apply_op(B.astype(np.complex128), opB), N,
+                   scaling="accurate", out_fmt=fp.BINARY32 if single else fp.BINARY64, keep_residue_planes=False)
+    got = run_gemm(A, B, N, opA, opB, single=single)
+    assert same_bits(got, em.out), mismatch_report(got, em.out)
+
+
+@pytest.mark.parametrize("single", [False, True])
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("T", "N")])
+def test_real_accurate_bitexact(single, opA, opB):
+    N = 7 if single else 14
+    A, B = _real(300, 260, 333, opA, opB, 2.0, 82, single)
+    em = RealEmulation(apply_op_real(A.astype(np.float64), opA), apply_op_real(B.astype(np.float64), opB), N,
+                       scaling="accurate", out_fmt=fp.BINARY32 if single else fp.BINARY64)
+    got = run_real(A, B, N, opA, opB, single=single)
+    assert same_bits(got, em.out), mismatch_report(got, em.out)
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_bound_products_over_many_chunks(real):
+    # k = 5000: the bound accumulation restarts every 2048 (complex C-bar_I runs over 2k)
+    if real:
+        A, B = _real(70, 150, 5000, "N", "N", 1.0, 84, False)
+        ref = RealEmulation(A, B, 12, scaling="accurate").out
+        got = run_real(A, B, 12)
+    else:
+        A, B = _cplx(70, 150, 5000, "N", "N", 1.0, 86, False)
+        ref = Emulation(A, B, 12, scaling="accurate", keep_residue_planes=False).out
+        got = run_gemm(A, B, 12)
+    assert same_bits(got, ref), mismatch_report(got, ref)
+
+
+@pytest.mark.parametrize("N", [2, 24])
+def test_moduli_extremes(N):
+    A, B = _cplx(90, 70, 120, "N", "N", 3.0, 88, False)
+    ref = Emulation(A, B, N, scaling="accurate", keep_residue_planes=False).out
+    assert same_bits(run_gemm(A, B, N), ref)
+
+
+def test_edge_cases():
+    A, B = _cplx(40, 33, 64, "N", "N", 1.0, 90, False)
+    A[3] = 0.0
+    A[5, 7] = complex(np.inf, 0.0)
+    B[9, 4] = complex(0.0, np.nan)
+    A[8] *= 1e-310
+    B[:, 11] *= 1e300
+    ref = Emulation(A, B, 14, scaling="accurate", keep_residue_planes=False).out
+    got = run_gemm(A, B, 14)
+    assert same_bits(got, ref), mismatch_report(got, ref)
+    Ar, Br = A.real.copy(), B.real.copy()
+    refr = RealEmulation(Ar, Br, 14, scaling="accurate").out
+    assert same_bits(run_real(Ar, Br, 14), refr)
+
+
+@pytest.mark.parametrize("N,k", [(4, 16867), (5, 16274), (6, 15321)])
+@pytest.mark.parametrize("kind", ["real", "complex"])
+def test_range_correction_near_half_P(N, k, kind):
+    # constant integer inputs with k chosen so that c' = M 4^E sits within 1e-4 of P/2:
+    # the float quotient can round either way and the CRT must still return c'
+    m, n = 16, 24
+    if kind == "real":
+        A, B = np.full((m, k), 3.0), np.full((k, n), 5.0)
+        got = run_real(A, B, N)
+        want = np.full((m, n), 15.0 * k)
+    else:
+        A, B = np.full((m, k), 3.0 + 0.0j), np.full((k, n), 5.0 + 0.0j)
+        got = run_gemm(A, B, N)
+        want = np.full((m, n), complex(15.0 * k, 0.0))
+    assert same_bits(got, want), mismatch_report(got, want)
+
+
+@pytest.mark.parametrize("kind", ["z", "d"])
+def test_accurate_with_column_blocking(kind):
+    m, n, k = 150, 3 * 128 + 45, 200
+    if kind == "z":
+        A, B = _cplx(m, n, k, "N", "N", 2.0, 92, False)
+        one = run_gemm(A, B, 12)
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 128), "nblock")
+        blk = run_gemm(A, B, 12)
+    else:
+        A, B = _real(m, n, k, "N", "N", 2.0, 93, False)
+        one = run_real(A, B, 12)
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 128), "nblock")
+        blk = run_real(A, B, 12)
+    assert same_bits(blk, one), mismatch_report(blk, one)
+
+
+def test_accurate_with_paper_fp_crt():
+    A, B = _cplx(60, 50, 90, "N", "N", 1.0, 94, False)
+    em = Emulation(A, B, 16, scaling="accurate")
+    ref = outputs(em)
+    emu.check(emu.emu_set_crt_mode(emu.EMU_CRT_PAPER_FP64), "crt")
+    got = run_gemm(A, B, 16)
+    assert same_bits(got, ref), mismatch_report(got, ref)
+    Ar, Br = A.real.copy(), B.real.copy()
+    emr = RealEmulation(Ar, Br, 16, scaling="accurate")
+    assert same_bits(run_real(Ar, Br, 16), outputs_real(emr))
+
+
+def test_accuracy_gain_over_fast_at_same_N():
+    A, B = _cplx(200, 180, 2000, "N", "N", 2.0, 96, False)
+    exact = Emulation(A, B, 24, keep_residue_planes=False).out            # reference, far below the errors
+    bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    errs = {}
+    for mode in (emu.EMU_SCALING_FAST, emu.EMU_SCALING_ACCURATE):
+        emu.check(emu.emu_set_scaling(mode), "scaling")
+        got = run_gemm(A, B, 10)
+        d = np.maximum(np.abs(got.real - exact.real), np.abs(got.imag - exact.imag))
+        errs[mode] = float(np.max(d / bound))
+    assert errs[emu.EMU_SCALING_ACCURATE] < errs[emu.EMU_SCALING_FAST] / 2, errs
