@@ -5,6 +5,9 @@
 //   E'_R,l = mod(D_l - E_l, p_l),  E'_I,l = mod(F_l - D_l - E_l, p_l)       (eq. karatsuba)
 //   c' = mod(sum_l (P/p_l) q_l E'_l, P)                                     (Steps V-v, V-vi)
 //   C_ij = alpha RN(c' 2^-(x_i + y_j)) + beta C_ij                          (Step VI)
+// The CRT sum only needs each E'_l modulo p_l, so the exact path feeds the
+// unreduced D_l - E_l and F_l - D_l - E_l (offset to be non-negative) and
+// never forms the symmetric remainders; the result is the same c'.
 //
 // The paper evaluates the CRT sum in two double-precision parts and the final
 // reduction in double-double (Section II, eq. CRTaccumulation; Section IV-A).
@@ -189,13 +192,15 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
   for (int q = 0; q < kRowsPerThread; ++q) {
     estR[q] = estI[q] = 0.0f;
 #pragma unroll
-    for (int t = 0; t < L; ++t) accR[q][t] = accI[q][t] = pl.K[t];
+    for (int t = 0; t < L; ++t) {
+      accR[q][t] = pl.KR[t];
+      accI[q][t] = pl.KI[t];
+    }
   }
   auto word = [&](int q) { return Word<kRowsPerThread>::load(base + q * job_stride); };
   // the residue words of modulus l+1 are loaded while modulus l is processed
   uint32_t nd = word(0), ne = word(1), nf = word(2);
   for (int l = 0; l < N; ++l) {
-    const int p = pl.p[l];
     const float qp = pl.qp[l];
     const uint32_t wd = nd, we = ne, wf = nf;
     if (l + 1 < N) {
@@ -208,17 +213,17 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
       const int d = static_cast<int8_t>(wd >> (8 * q));
       const int e = static_cast<int8_t>(we >> (8 * q));
       const int f = static_cast<int8_t>(wf >> (8 * q));
-      const int er = sym_small(d - e, p);          // E'_R,l
-      const int ei = sym_small(f - d - e, p);      // E'_I,l
-      const uint32_t ur = static_cast<uint32_t>(er + 128), ui = static_cast<uint32_t>(ei + 128);
+      const int vr = d - e;                        // == E'_R,l (mod p_l), in [-255, 255]
+      const int vi = f - vr - 2 * e;               // F - D - E == E'_I,l (mod p_l), in [-382, 383]
+      const uint32_t ur = static_cast<uint32_t>(vr + 255), ui = static_cast<uint32_t>(vi + 382);
 #pragma unroll
       for (int t = 0; t < L; ++t) {
         const uint64_t w = pl.w[l][t];
         accR[q][t] += ur * w;
         accI[q][t] += ui * w;
       }
-      estR[q] = fmaf(static_cast<float>(er), qp, estR[q]);
-      estI[q] = fmaf(static_cast<float>(ei), qp, estI[q]);
+      estR[q] = fmaf(static_cast<float>(vr), qp, estR[q]);
+      estI[q] = fmaf(static_cast<float>(vi), qp, estI[q]);
     }
   }
   const int yj = y[j];

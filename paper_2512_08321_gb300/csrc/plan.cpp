@@ -5,9 +5,12 @@
 //          ... when coprime to all kept so far).
 // Step II  q_l = (P/p_l)^-1 mod p_l, CRT weights w_l = (P/p_l) q_l, so that
 //          sum_l w_l E'_l == A'B' (mod P) (Section II).
-// The CRT is evaluated exactly in L 32-bit limbs modulo 2^(32L) > 8|c'|:
-//   c' = sum_l w_l u_l + r' (2^(32L) - P) + K,  u_l = E'_l + 128,
-//   r' = r + R0 with r = round(S/P) and K = R0 P - 128 sum_l w_l.
+// The CRT is evaluated exactly in L 32-bit limbs modulo 2^(32L) (2^(32L-1) > 2P):
+//   c' = sum_l w_l u_l + r' (2^(32L) - P) + K,  u_l = v_l + o,
+//   r' = r + R0 with r = round(S/P) and K = R0 P - o sum_l w_l,
+// where v_l is any integer congruent to c' modulo p_l: E'_l for real input
+// (o = 128, K), and the unreduced Karatsuba combinations D_l - E_l (o = 255,
+// KR) and F_l - D_l - E_l (o = 382, KI) for complex input.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -234,18 +237,24 @@ void build(int N, Plan& pl) {
   Big zero;
   Big negP = zero;
   sub(negP, P);
-  pl.R0 = 128 * N;
-  Big K = P;
-  mul_small(K, static_cast<uint32_t>(pl.R0));
-  Big w128 = sumw;
-  mul_small(w128, 128u);
-  sub(K, w128);
+  pl.R0 = 384 * N;                             // r >= -383 N for every offset below
+  auto offset_const = [&](uint32_t o) {        // R0 P - o sum w
+    Big Kc = P;
+    mul_small(Kc, static_cast<uint32_t>(pl.R0));
+    Big wo = sumw;
+    mul_small(wo, o);
+    sub(Kc, wo);
+    return Kc;
+  };
+  const Big K = offset_const(128u), KR = offset_const(255u), KI = offset_const(382u);
   Big H = P;                                   // (P - 1) / 2
   sub(H, Big(1));
   divmod_small(H, 2u);
   for (int t = 0; t < kMaxLimbs; ++t) {
     pl.negP[t] = t < pl.L ? negP.v[t] : 0u;
     pl.K[t] = t < pl.L ? K.v[t] : 0u;
+    pl.KR[t] = t < pl.L ? KR.v[t] : 0u;
+    pl.KI[t] = t < pl.L ? KI.v[t] : 0u;
     pl.Pw[t] = t < pl.L ? P.v[t] : 0u;
     pl.H[t] = t < pl.L ? H.v[t] : 0u;
   }

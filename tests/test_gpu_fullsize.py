@@ -76,7 +76,7 @@ def test_fullsize_sampled(workload, moduli, tol):
     assert report["by_moduli"][default_N]["max_normalised_error"] <= max(report["native"]["max_normalised_error"], tol)
 
 
-@pytest.mark.parametrize("workload,moduli,tol", [("dgemm16384", (12, 14, 16, 18), 1e-15),
+@pytest.mark.parametrize("workload,moduli,tol", [("dgemm16384", (12, 14, 15, 16, 18), 1e-15),
                                                   ("sgemm16384", (6, 7, 8, 10), 1e-6)])
 def test_fullsize_sampled_real(workload, moduli, tol):
     from oracle.emulate_real import emulate_real_entries
