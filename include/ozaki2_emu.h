@@ -107,6 +107,29 @@ emu_status_t emu_sgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
                        const float* B, int64_t ldb, const float* beta,
                        float* C, int64_t ldc, int num_moduli, void* stream);
 
+/* Host-buffer forms of the four GEMMs: A, B and C are in host memory (same
+ * arguments, layouts and results as the device forms; alpha/beta as there).
+ * The inputs are copied to a library-owned device staging buffer by a copy
+ * kernel that reads host memory over the CPU-GPU link, and the CRT writes C
+ * straight into host memory.  Host memory is read and written from kernels
+ * when it is pinned or registered; pageable memory goes through
+ * cudaMemcpyAsync and a device copy of C.
+ * Asynchronous on `stream` like the device forms: the host buffers must stay
+ * valid and untouched until the stream reaches the end of the call.  Calls
+ * share the staging buffer and must be ordered on one stream. */
+emu_status_t emu_zgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                            const double* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            const double* beta, void* C, int64_t ldc, int num_moduli, void* stream);
+emu_status_t emu_cgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                            const float* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            const float* beta, void* C, int64_t ldc, int num_moduli, void* stream);
+emu_status_t emu_dgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                            const double* alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                            const double* beta, double* C, int64_t ldc, int num_moduli, void* stream);
+emu_status_t emu_sgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
+                            const float* alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                            const float* beta, float* C, int64_t ldc, int num_moduli, void* stream);
+
 /* Element-type codes of emu_workspace_bytes and emu_autotune_gemm. */
 #define EMU_DTYPE_Z 0   /* complex128 */
 #define EMU_DTYPE_C 1   /* complex64 */

@@ -31,6 +31,8 @@ struct DeviceState {
   bool mlp_loaded = false;
   float* feat = nullptr;       // 39 features + chosen N (pinned host mirror below)
   int* chosen_host = nullptr;
+  void* stage = nullptr;       // staging of the host-buffer entry points
+  size_t stage_bytes = 0;
 };
 
 std::mutex g_mu;
@@ -324,6 +326,41 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
 }
 
 }  // namespace
+
+emu_status_t run_gemm(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar,
+                      double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi, void* C,
+                      int64_t ldc, int N, void* stream) {
+  return gemm(Dt{single, real}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream);
+}
+
+emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
+                             int64_t ldc, int N) {
+  return check_common(ta, tb, m, n, k, lda, ldb, ldc, N, true);
+}
+
+emu_status_t set_bad_param(int idx) { return bad(idx); }
+
+// Per-device staging buffer of the host-buffer entry points (grown on demand).
+emu_status_t get_staging(size_t need, char** out) {
+  DeviceState* ds = nullptr;
+  emu_status_t s = device_init(current_device(), ds);
+  if (s != EMU_OK) return s;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (ds->stage_bytes < need) {
+    if (ds->stage) {
+      cudaFree(ds->stage);
+      ds->stage = nullptr;
+      ds->stage_bytes = 0;
+    }
+    if (cudaMalloc(&ds->stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return EMU_ERR_ALLOC;
+    }
+    ds->stage_bytes = need;
+  }
+  *out = static_cast<char*>(ds->stage);
+  return EMU_OK;
+}
 
 void count_launches(int n) { g_launches.fetch_add(static_cast<uint64_t>(n), std::memory_order_relaxed); }
 

@@ -53,6 +53,18 @@ _SIGS = [
     ("emu_sgemm", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
                            _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
                            _c_i64, _c_int, _c_ptr]),
+    ("emu_zgemm_host", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_double),
+                                _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_double), _c_ptr,
+                                _c_i64, _c_int, _c_ptr]),
+    ("emu_cgemm_host", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
+                                _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
+                                _c_i64, _c_int, _c_ptr]),
+    ("emu_dgemm_host", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_double),
+                                _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_double), _c_ptr,
+                                _c_i64, _c_int, _c_ptr]),
+    ("emu_sgemm_host", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, ctypes.POINTER(ctypes.c_float),
+                                _c_ptr, _c_i64, _c_ptr, _c_i64, ctypes.POINTER(ctypes.c_float), _c_ptr,
+                                _c_i64, _c_int, _c_ptr]),
     ("emu_grouped_create", _c_int, [_c_int, _c_int, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr,
                                     _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_ptr, _c_int, _c_int,
                                     ctypes.POINTER(_c_ptr)]),
@@ -185,6 +197,32 @@ def emu_sgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_
     a, b = ctypes.c_float(float(alpha)), ctypes.c_float(float(beta))
     return lib().emu_sgemm(_op(transa), _op(transb), m, n, k, ctypes.byref(a), A, lda, B, ldb, ctypes.byref(b),
                            C, ldc, num_moduli, _stream(stream))
+
+
+def emu_zgemm_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a = (ctypes.c_double * 2)(float(alpha.real), float(alpha.imag))
+    b = (ctypes.c_double * 2)(float(beta.real), float(beta.imag))
+    return lib().emu_zgemm_host(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc,
+                                num_moduli, _stream(stream))
+
+
+def emu_cgemm_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a = (ctypes.c_float * 2)(float(alpha.real), float(alpha.imag))
+    b = (ctypes.c_float * 2)(float(beta.real), float(beta.imag))
+    return lib().emu_cgemm_host(_op(transa), _op(transb), m, n, k, a, A, lda, B, ldb, b, C, ldc,
+                                num_moduli, _stream(stream))
+
+
+def emu_dgemm_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a, b = ctypes.c_double(float(alpha)), ctypes.c_double(float(beta))
+    return lib().emu_dgemm_host(_op(transa), _op(transb), m, n, k, ctypes.byref(a), A, lda, B, ldb,
+                                ctypes.byref(b), C, ldc, num_moduli, _stream(stream))
+
+
+def emu_sgemm_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli, stream=None):
+    a, b = ctypes.c_float(float(alpha)), ctypes.c_float(float(beta))
+    return lib().emu_sgemm_host(_op(transa), _op(transb), m, n, k, ctypes.byref(a), A, lda, B, ldb,
+                                ctypes.byref(b), C, ldc, num_moduli, _stream(stream))
 
 
 class GroupedArgs:

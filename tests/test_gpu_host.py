@@ -1,0 +1,88 @@
+"""Host-buffer GEMMs (emu_?gemm_host): A, B, C in host memory (pinned and
+pageable), results bit-identical to the device-buffer calls, which the
+parity tests tie to the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2512_08321_gb300 import emu
+from paper_2512_08321_gb300.workloads import paper_matrix, paper_matrix_real
+
+from .helpers import dev, host, mismatch_report, same_bits
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {"z": (np.complex128, emu.emu_zgemm, emu.emu_zgemm_host),
+         "c": (np.complex64, emu.emu_cgemm, emu.emu_cgemm_host),
+         "d": (np.float64, emu.emu_dgemm, emu.emu_dgemm_host),
+         "s": (np.float32, emu.emu_sgemm, emu.emu_sgemm_host)}
+
+
+def _mats(kind, m, n, k, opA, opB, seed):
+    dt = KINDS[kind][0]
+    gen = paper_matrix if kind in "zc" else paper_matrix_real
+    A = gen(m, k, 1.0, seed) if opA == "N" else gen(k, m, 1.0, seed)
+    B = gen(k, n, 1.0, seed + 1) if opB == "N" else gen(n, k, 1.0, seed + 1)
+    C = gen(m, n, 1.0, seed + 2)
+    return A.astype(dt), B.astype(dt), C.astype(dt)
+
+
+def _scal(kind, v):
+    return complex(v) if kind in "zc" else float(v)
+
+
+def _device_ref(kind, A, B, C, m, n, k, opA, opB, alpha, beta, N):
+    f = KINDS[kind][1]
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    emu.check(f(opA, opB, m, n, k, _scal(kind, alpha), dA.data_ptr(), dA.shape[1], dB.data_ptr(), dB.shape[1],
+                _scal(kind, beta), dC.data_ptr(), dC.shape[1], N), "device call")
+    torch.cuda.synchronize()
+    return host(dC, m)
+
+
+@pytest.mark.parametrize("kind", ["z", "c", "d", "s"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffers_match_device_call(kind, pinned):
+    m, n, k, N = 130, 97, 150, 9
+    opA, opB = "T", "N"
+    A, B, C = _mats(kind, m, n, k, opA, opB, 300)
+    alpha, beta = 0.75, -1.5
+    ref = _device_ref(kind, A, B, C, m, n, k, opA, opB, alpha, beta, N)
+    f = KINDS[kind][2]
+    if pinned:
+        tA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+        tB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+        tC = torch.from_numpy(np.ascontiguousarray(C.T)).pin_memory()
+        pa, pb, pc = tA.data_ptr(), tB.data_ptr(), tC.data_ptr()
+    else:
+        hA, hB, hC = np.asfortranarray(A), np.asfortranarray(B), np.asfortranarray(C.copy())
+        pa, pb, pc = hA.ctypes.data, hB.ctypes.data, hC.ctypes.data
+    st = f(opA, opB, m, n, k, _scal(kind, alpha), pa, A.shape[0], pb, B.shape[0], _scal(kind, beta), pc, m, N)
+    emu.check(st, "host call")
+    torch.cuda.synchronize()
+    got = tC.numpy().T if pinned else hC
+    assert same_bits(np.ascontiguousarray(got), np.ascontiguousarray(ref)), mismatch_report(got, ref)
+
+
+def test_host_buffers_with_leading_dimensions_and_k0():
+    m, n, k, N = 70, 50, 40, 12
+    A, B, C = _mats("z", m, n, k, "N", "N", 310)
+    ref = _device_ref("z", A, B, C, m, n, k, "N", "N", 1.0, 0.0, N)
+    lda, ldb, ldc = m + 5, k + 3, m + 9
+    hA = np.zeros((lda, k), np.complex128, order="F"); hA[:m] = A
+    hB = np.zeros((ldb, n), np.complex128, order="F"); hB[:k] = B
+    hC = np.full((ldc, n), 7.0 + 7.0j, np.complex128, order="F")
+    emu.check(emu.emu_zgemm_host("N", "N", m, n, k, 1.0, hA.ctypes.data, lda, hB.ctypes.data, ldb, 0.0,
+                                 hC.ctypes.data, ldc, N), "host call")
+    torch.cuda.synchronize()
+    assert same_bits(np.ascontiguousarray(hC[:m]), np.ascontiguousarray(ref))
+    assert np.all(hC[m:] == 7.0 + 7.0j)                     # rows beyond m untouched
+    # k = 0 with beta: C = beta C, A and B never read
+    emu.check(emu.emu_zgemm_host("N", "N", m, n, 0, 1.0, None, m, None, 1, 2.0, hC.ctypes.data, ldc, N), "k=0")
+    torch.cuda.synchronize()
+    assert np.array_equal(hC[:m], 2.0 * ref)
+
+
+def test_host_argument_errors():
+    assert emu.emu_zgemm_host("N", "N", 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 12) == emu.EMU_ERR_INVALID_ARG
+    assert emu.emu_zgemm_host("N", "N", 4, 4, 4, 1.0, 1, 2, 1, 4, 0.0, 1, 4, 12) == emu.EMU_ERR_INVALID_ARG
