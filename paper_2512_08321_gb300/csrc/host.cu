@@ -99,15 +99,22 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
     return v ? copy_bytes(dst, v, bytes, st) : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
   };
   if (bring(dA, A, bA) != cudaSuccess || bring(dB, B, bB) != cudaSuccess) return EMU_ERR_CUDA;
+  // pageable C: a device copy with the same leading dimension; only the m x n
+  // entries travel, so the rows between columns stay as the caller left them
+  const size_t pitch = static_cast<size_t>(ldc) * esz, width = static_cast<size_t>(m) * esz;
   void* target = Cv;
   if (!Cv) {
     target = dC;
-    if (use_beta && cudaMemcpyAsync(dC, C, bC, cudaMemcpyHostToDevice, st) != cudaSuccess) return EMU_ERR_CUDA;
+    if (use_beta && cudaMemcpy2DAsync(dC, pitch, C, pitch, width, static_cast<size_t>(n), cudaMemcpyHostToDevice,
+                                      st) != cudaSuccess)
+      return EMU_ERR_CUDA;
   }
   s = run_gemm(single, real, ta, tb, m, n, k, ar, ai, bA ? dA : nullptr, lda, bB ? dB : nullptr, ldb, br, bi, target,
                ldc, N, stream);
   if (s != EMU_OK) return s;
-  if (!Cv && cudaMemcpyAsync(C, dC, bC, cudaMemcpyDeviceToHost, st) != cudaSuccess) return EMU_ERR_CUDA;
+  if (!Cv && cudaMemcpy2DAsync(C, pitch, dC, pitch, width, static_cast<size_t>(n), cudaMemcpyDeviceToHost, st) !=
+                 cudaSuccess)
+    return EMU_ERR_CUDA;
   return EMU_OK;
 }
 
