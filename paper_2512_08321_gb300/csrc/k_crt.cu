@@ -158,6 +158,13 @@ __device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, co
   return round_limbs<L>(c, e2);
 }
 
+// a * b + c with a 32 x 32 -> 64-bit product
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t r;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
+  return r;
+}
+
 // residue words of R consecutive rows: 8, 16 or 32 bits
 template <int R>
 struct Word;
@@ -197,30 +204,36 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
       accI[q][t] = pl.KI[t];
     }
   }
-  auto word = [&](int q) { return Word<kRowsPerThread>::load(base + q * job_stride); };
-  // the residue words of modulus l+1 are loaded while modulus l is processed
-  uint32_t nd = word(0), ne = word(1), nf = word(2);
+  // the residue words of modulus l+1 are loaded while modulus l is processed;
+  // pointers advance by one modulus (three jobs) per step
+  const int8_t* pw = base;
+  uint32_t nd = Word<kRowsPerThread>::load(pw), ne = Word<kRowsPerThread>::load(pw + job_stride),
+           nf = Word<kRowsPerThread>::load(pw + 2 * job_stride);
   for (int l = 0; l < N; ++l) {
     const float qp = pl.qp[l];
-    const uint32_t wd = nd, we = ne, wf = nf;
+    uint32_t w[L];
+#pragma unroll
+    for (int t = 0; t < L; ++t) w[t] = pl.w[l][t];
+    // bytes as D + 128, E + 128, F + 128 (unsigned)
+    const uint32_t wd = nd ^ 0x80808080u, we = ne ^ 0x80808080u, wf = nf ^ 0x80808080u;
     if (l + 1 < N) {
-      nd = word(3 * l + 3);
-      ne = word(3 * l + 4);
-      nf = word(3 * l + 5);
+      pw += 3 * job_stride;
+      nd = Word<kRowsPerThread>::load(pw);
+      ne = Word<kRowsPerThread>::load(pw + job_stride);
+      nf = Word<kRowsPerThread>::load(pw + 2 * job_stride);
     }
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
-      const int d = static_cast<int8_t>(wd >> (8 * q));
-      const int e = static_cast<int8_t>(we >> (8 * q));
-      const int f = static_cast<int8_t>(wf >> (8 * q));
-      const int vr = d - e;                        // == E'_R,l (mod p_l), in [-255, 255]
-      const int vi = f - vr - 2 * e;               // F - D - E == E'_I,l (mod p_l), in [-382, 383]
+      const int d = static_cast<int>((wd >> (8 * q)) & 0xFFu);
+      const int e = static_cast<int>((we >> (8 * q)) & 0xFFu);
+      const int f = static_cast<int>((wf >> (8 * q)) & 0xFFu);
+      const int vr = d - e;                        // D - E == E'_R,l (mod p_l), in [-255, 255]
+      const int vi = f - d - e + 128;              // F - D - E == E'_I,l (mod p_l), in [-382, 383]
       const uint32_t ur = static_cast<uint32_t>(vr + 255), ui = static_cast<uint32_t>(vi + 382);
 #pragma unroll
       for (int t = 0; t < L; ++t) {
-        const uint64_t w = pl.w[l][t];
-        accR[q][t] += ur * w;
-        accI[q][t] += ui * w;
+        accR[q][t] = mad_wide(ur, w[t], accR[q][t]);
+        accI[q][t] = mad_wide(ui, w[t], accI[q][t]);
       }
       estR[q] = fmaf(static_cast<float>(vr), qp, estR[q]);
       estI[q] = fmaf(static_cast<float>(vi), qp, estI[q]);
@@ -291,18 +304,24 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
 #pragma unroll
     for (int t = 0; t < L; ++t) acc[q][t] = pl.K[t];
   }
-  uint32_t nw = Word<kRowsPerThread>::load(base);
+  const int8_t* pw = base;
+  uint32_t nw = Word<kRowsPerThread>::load(pw);
   for (int l = 0; l < N; ++l) {
     const float qp = pl.qp[l];
-    const uint32_t wv = nw;
-    if (l + 1 < N) nw = Word<kRowsPerThread>::load(base + (l + 1) * job_stride);
+    uint32_t w[L];
+#pragma unroll
+    for (int t = 0; t < L; ++t) w[t] = pl.w[l][t];
+    const uint32_t wv = nw ^ 0x80808080u;          // bytes as E' + 128
+    if (l + 1 < N) {
+      pw += job_stride;
+      nw = Word<kRowsPerThread>::load(pw);
+    }
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
-      const int e = static_cast<int8_t>(wv >> (8 * q));
-      const uint32_t u = static_cast<uint32_t>(e + 128);
+      const uint32_t u = (wv >> (8 * q)) & 0xFFu;
 #pragma unroll
-      for (int t = 0; t < L; ++t) acc[q][t] += u * static_cast<uint64_t>(pl.w[l][t]);
-      est[q] = fmaf(static_cast<float>(e), qp, est[q]);
+      for (int t = 0; t < L; ++t) acc[q][t] = mad_wide(u, w[t], acc[q][t]);
+      est[q] = fmaf(static_cast<float>(static_cast<int>(u) - 128), qp, est[q]);
     }
   }
   const int yj = y[j];

@@ -25,6 +25,8 @@
 // each thread then owns 4 consecutive h of one row, 8 threads per row.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "emu_internal.h"
 
 namespace emu {
@@ -40,8 +42,8 @@ struct SplitSmem {
 };
 
 // Signed 13-bit chunks of a' = trunc(v 2^x) (exact floats, least significant first).
-template <bool SINGLE>
-__device__ __forceinline__ void chunks(uint64_t bits, int x, int nchunk, float (&c)[kMaxChunks]) {
+template <bool SINGLE, int TC>
+__device__ __forceinline__ void chunks(uint64_t bits, int x, int nchunk, float (&c)[TC]) {
   bool neg;
   int ex;
   uint64_t m;
@@ -73,7 +75,7 @@ __device__ __forceinline__ void chunks(uint64_t bits, int x, int nchunk, float (
   }
   const float sg = neg ? -1.0f : 1.0f;
 #pragma unroll
-  for (int t = 0; t < kMaxChunks; ++t) {
+  for (int t = 0; t < TC; ++t) {
     const int b = kChunkBits * t;
     uint32_t v;
     if (b + kChunkBits <= 64) v = static_cast<uint32_t>(lo >> b);
@@ -86,11 +88,12 @@ __device__ __forceinline__ void chunks(uint64_t bits, int x, int nchunk, float (
   }
 }
 
-// Symmetric residue (ties up) of the exact float integer z, |z| < 2^23.
-__device__ __forceinline__ float sym_mod_f(float z, float p, float inv_p) {
+// Symmetric residue (ties up) of the exact float integer z, |z| < 2^23;
+// ph = p/2 (exact).
+__device__ __forceinline__ float sym_mod_f(float z, float p, float ph, float inv_p) {
   float r = fmaf(-rintf(z * inv_p), p, z);      // exact; |r| <= p/2 + 2
-  if (2.0f * r >= p) r -= p;
-  if (2.0f * r < -p) r += p;
+  if (r >= ph) r -= p;
+  if (r < -ph) r += p;
   return r;
 }
 
@@ -132,7 +135,8 @@ struct StoreE<__half, 2> {
   }
 };
 
-template <bool SINGLE, bool ROWS_CONTIG, typename T, int kPerThread, bool R = false>
+// NCH: the chunk count when known at compile time (0: pl.nchunk at run time).
+template <bool SINGLE, bool ROWS_CONTIG, typename T, int kPerThread, bool R = false, int NCH = 0>
 __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restrict__ Xv, int64_t rows, int64_t k,
                                             int64_t rs, int64_t hs, bool conj, const int16_t* __restrict__ xexp,
                                             const Plan& pl, int64_t kpad, T* __restrict__ planes, int64_t rtile,
@@ -186,9 +190,10 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   if (r >= rows) continue;
   const int x = xexp[r];
   const bool flagged = (x == kExpNonfinite);
-  const int nch = pl.nchunk;
+  const int nch = NCH ? NCH : pl.nchunk;
+  constexpr int TC = NCH ? NCH : kMaxChunks;
 
-  float cre[kPerThread][kMaxChunks], cim[kPerThread][kMaxChunks];
+  float cre[kPerThread][TC], cim[kPerThread][TC];
 #pragma unroll
   for (int j = 0; j < kPerThread; ++j) {
     uint64_t br = sm.tre[rr][hb + j], bi = sm.tim[rr][hb + j];
@@ -197,17 +202,19 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
                      (SINGLE ? (((br >> 23) & 0xFF) == 0xFF || ((bi >> 23) & 0xFF) == 0xFF)
                              : (((br >> 52) & 0x7FF) == 0x7FF || ((bi >> 52) & 0x7FF) == 0x7FF));
     if (bad) br = bi = 0;
-    chunks<SINGLE>(br, flagged ? 0 : x, nch, cre[j]);
-    if constexpr (!R) chunks<SINGLE>(bi, flagged ? 0 : x, nch, cim[j]);
+    chunks<SINGLE, TC>(br, flagged ? 0 : x, nch, cre[j]);
+    if constexpr (!R) chunks<SINGLE, TC>(bi, flagged ? 0 : x, nch, cim[j]);
   }
   const int64_t plane_stride = rows * kpad;
   T* base = planes + r * kpad + h0 + hb;
+  T* dst = base;
   for (int l = 0; l < pl.N; ++l) {
     const float p = static_cast<float>(pl.p[l]);
+    const float ph = 0.5f * p;
     const float ip = pl.inv_p[l];
-    float w[kMaxChunks];
+    float w[TC];
 #pragma unroll
-    for (int t = 0; t < kMaxChunks; ++t) w[t] = pl.w13[l][t];
+    for (int t = 0; t < TC; ++t) w[t] = pl.w13[l][t];
     if constexpr (R) {
       // real input: one plane per modulus
       float vr[kPerThread];
@@ -215,35 +222,36 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
       for (int j = 0; j < kPerThread; ++j) {
         float zr = 0.0f;
 #pragma unroll
-        for (int t = 0; t < kMaxChunks; ++t)
-          if (t < nch) zr = fmaf(cre[j][t], w[t], zr);
-        vr[j] = sym_mod_f(zr, p, ip);
+        for (int t = 0; t < TC; ++t)
+          if (NCH || t < nch) zr = fmaf(cre[j][t], w[t], zr);
+        vr[j] = sym_mod_f(zr, p, ph, ip);
       }
-      StoreE<T, kPerThread>::put(base + static_cast<int64_t>(l) * plane_stride, vr);
-      continue;
-    }
-    float vr[kPerThread], vi[kPerThread], vs[kPerThread];
+      StoreE<T, kPerThread>::put(dst, vr);
+      dst += plane_stride;
+    } else {
+      float vr[kPerThread], vi[kPerThread], vs[kPerThread];
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-      float zr = 0.0f, zi = 0.0f;
+      for (int j = 0; j < kPerThread; ++j) {
+        float zr = 0.0f, zi = 0.0f;
 #pragma unroll
-      for (int t = 0; t < kMaxChunks; ++t) {
-        if (t < nch) {
-          zr = fmaf(cre[j][t], w[t], zr);
-          zi = fmaf(cim[j][t], w[t], zi);
+        for (int t = 0; t < TC; ++t) {
+          if (NCH || t < nch) {
+            zr = fmaf(cre[j][t], w[t], zr);
+            zi = fmaf(cim[j][t], w[t], zi);
+          }
         }
+        vr[j] = sym_mod_f(zr, p, ph, ip);
+        vi[j] = sym_mod_f(zi, p, ph, ip);
+        float sr = vr[j] + vi[j];
+        if (sr >= ph) sr -= p;
+        if (sr < -ph) sr += p;
+        vs[j] = sr;
       }
-      vr[j] = sym_mod_f(zr, p, ip);
-      vi[j] = sym_mod_f(zi, p, ip);
-      float sr = vr[j] + vi[j];
-      if (2.0f * sr >= p) sr -= p;
-      if (2.0f * sr < -p) sr += p;
-      vs[j] = sr;
+      StoreE<T, kPerThread>::put(dst, vr);
+      StoreE<T, kPerThread>::put(dst + plane_stride, vi);
+      StoreE<T, kPerThread>::put(dst + 2 * plane_stride, vs);
+      dst += 3 * plane_stride;
     }
-    T* dst = base + static_cast<int64_t>(3 * l) * plane_stride;
-    StoreE<T, kPerThread>::put(dst, vr);
-    StoreE<T, kPerThread>::put(dst + plane_stride, vi);
-    StoreE<T, kPerThread>::put(dst + 2 * plane_stride, vs);
   }
   }
 }
@@ -340,15 +348,15 @@ __global__ void __launch_bounds__(kThreads) bound_split_kernel(const void* __res
   }
 }
 
-template <bool SINGLE, bool ROWS_CONTIG, typename T, int E, bool R>
+template <bool SINGLE, bool ROWS_CONTIG, typename T, int E, bool R, int NCH = 0>
 __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict__ Xv, int64_t rows,
                                                          int64_t k, int64_t rs, int64_t hs,
                                                          bool conj, const int16_t* __restrict__ xexp,
                                                          const __grid_constant__ Plan pl,
                                                          int64_t kpad, T* __restrict__ planes) {
   __shared__ SplitSmem sm;
-  split_block<SINGLE, ROWS_CONTIG, T, E, R>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x,
-                                            blockIdx.y);
+  split_block<SINGLE, ROWS_CONTIG, T, E, R, NCH>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x,
+                                                 blockIdx.y);
 }
 
 // one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
@@ -380,7 +388,29 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
   dim3 grid(static_cast<unsigned int>((rows + kTileR - 1) / kTileR),
             static_cast<unsigned int>(kpad / kTileH));
   T* P = static_cast<T*>(planes);
-  if (elems == 2) {
+  // the common configuration (fp16 planes, 4 entries per thread) has the chunk count compiled in
+  auto fixed = [&](auto nch_tag) {
+    constexpr int NC = decltype(nch_tag)::value;
+    if (rs == 1) split_kernel<SINGLE, true, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    else split_kernel<SINGLE, false, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+  };
+  bool done = false;
+  if constexpr (std::is_same<T, __half>::value) {
+    if (elems != 2) {
+      done = true;
+      switch (pl.nchunk) {
+        case 3: fixed(std::integral_constant<int, 3>{}); break;
+        case 4: fixed(std::integral_constant<int, 4>{}); break;
+        case 5: fixed(std::integral_constant<int, 5>{}); break;
+        case 6: fixed(std::integral_constant<int, 6>{}); break;
+        case 7: fixed(std::integral_constant<int, 7>{}); break;
+        case 8: fixed(std::integral_constant<int, 8>{}); break;
+        default: done = false;
+      }
+    }
+  }
+  if (done) {
+  } else if (elems == 2) {
     if (rs == 1) split_kernel<SINGLE, true, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
     else split_kernel<SINGLE, false, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
   } else {
