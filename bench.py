@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--scaling", choices=["fast", "accurate"], default="fast",
+                    help="scaling vectors of Section III-B (fast or accurate mode)")
     return ap.parse_args()
 
 
@@ -238,6 +240,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     emu.lib()
+    emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE if args.scaling == "accurate" else emu.EMU_SCALING_FAST),
+              "emu_set_scaling")
     m, n, k, N = wl["m"], wl["n"], wl["k"], wl["N"]
     single = wl["single"]
     real = bool(wl.get("real"))
@@ -324,7 +328,7 @@ def main():
            "vs_baseline": None, "dtype": "fp16", "data": "synthetic",
            "config": {"workload": args.workload, "m": m, "n": n, "k": k,
                       "io": str(cdt).replace("torch.", ""), "num_moduli": N, "phi": wl["phi"],
-                      "engine": "tcgen05 kind::f16 (exact residues), integer CRT",
+                      "engine": "tcgen05 kind::f16 (exact residues), integer CRT", "scaling": args.scaling,
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "seed": wl["seed"],
                       "tuning": dict(zip(["tile_n", "group", "chunk_k", "crt_rows", "split_elems"], tuned))
