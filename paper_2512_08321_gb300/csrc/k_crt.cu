@@ -56,11 +56,15 @@ __device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
     }
   }
   int top = -1;
+  uint32_t topw = 0;
 #pragma unroll
   for (int t = 0; t < L; ++t)
-    if (c[t]) top = t;
+    if (c[t]) {
+      top = t;
+      topw = c[t];
+    }
   if (top < 0) return 0.0;
-  const int b = 32 * top + (31 - __clz(c[top]));          // leading bit index
+  const int b = 32 * top + (31 - __clz(topw));            // leading bit index
   const int lead = b + e2;
   const int lsb = max(lead - 52, -1074);
   const int sh = lsb - e2;                                  // bit index of the result LSB
@@ -81,7 +85,11 @@ __device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
       q |= pos >= 0 ? (limb << pos) : (limb >> (-pos));
     }
     const int rb = sh - 1;                                  // round bit index
-    const bool half = (c[rb >> 5] >> (rb & 31)) & 1u;
+    uint32_t rw = 0;                                        // limb holding it (no dynamic indexing)
+#pragma unroll
+    for (int t = 0; t < L; ++t)
+      if (t == (rb >> 5)) rw = c[t];
+    const bool half = (rw >> (rb & 31)) & 1u;
     bool sticky = false;
 #pragma unroll
     for (int t = 0; t < L; ++t) {
@@ -165,21 +173,35 @@ __device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c)
   return r;
 }
 
-// residue words of R consecutive rows: 8, 16 or 32 bits
+// Residues of the block's rows for every job, staged in shared memory with
+// asynchronous 16-byte copies issued all at once (the rows of one job are
+// contiguous and the block start is 16-byte aligned), so the loads of all
+// moduli are in flight together instead of one modulus at a time.
+// smem[job * (kThreads * R) + r]; returns after the copies have landed.
 template <int R>
-struct Word;
-template <>
-struct Word<1> {
-  __device__ static uint32_t load(const int8_t* p) { return static_cast<uint8_t>(__ldg(p)); }
-};
-template <>
-struct Word<2> {
-  __device__ static uint32_t load(const int8_t* p) { return __ldg(reinterpret_cast<const unsigned short*>(p)); }
-};
-template <>
-struct Word<4> {
-  __device__ static uint32_t load(const int8_t* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
-};
+__device__ __forceinline__ void stage_residues(int8_t* smem, const int8_t* __restrict__ blk, int64_t job_stride,
+                                               int jobs, int64_t rows_left) {
+  constexpr int kRows = kThreads * R;
+  const int rows = static_cast<int>(rows_left < kRows ? rows_left : kRows);   // a multiple of 16
+  const int per_job = rows / 16;
+  const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  for (int c = threadIdx.x; c < jobs * per_job; c += kThreads) {
+    const int job = c / per_job, q = c - job * per_job;
+    const int8_t* g = blk + job * job_stride + 16 * q;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0 + job * kRows + 16 * q), "l"(g));
+  }
+  asm volatile("cp.async.commit_group;\n");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t smem_word(const int8_t* smem, int job, int r) {
+  const int8_t* p = smem + job * (kThreads * R) + r;
+  if constexpr (R == 4) return *reinterpret_cast<const uint32_t*>(p);
+  else if constexpr (R == 2) return *reinterpret_cast<const unsigned short*>(p);
+  else return static_cast<uint8_t>(*p);
+}
 
 template <int L, bool SINGLE, int kRowsPerThread, bool ROBUST = false>
 __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
@@ -187,10 +209,13 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
                                           double ar, double ai, double br, double bi, void* __restrict__ Cv,
                                           int64_t ldc, int64_t j, int64_t iblock) {
   const int64_t i0 = (iblock * kThreads + threadIdx.x) * kRowsPerThread;
-  if (i0 >= m) return;
   const int N = pl.N;
   const int64_t job_stride = n * ldr;
-  const int8_t* base = res + j * ldr + i0;
+  const int64_t row0 = iblock * kThreads * kRowsPerThread;
+  extern __shared__ int8_t crt_smem[];
+  stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, 3 * N, ldr - row0);
+  if (i0 >= m) return;
+  const int rr = threadIdx.x * kRowsPerThread;
 
   // exact limb accumulators for the real and imaginary parts of 4 rows
   uint64_t accR[kRowsPerThread][L], accI[kRowsPerThread][L];
@@ -204,24 +229,15 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
       accI[q][t] = pl.KI[t];
     }
   }
-  // the residue words of modulus l+1 are loaded while modulus l is processed;
-  // pointers advance by one modulus (three jobs) per step
-  const int8_t* pw = base;
-  uint32_t nd = Word<kRowsPerThread>::load(pw), ne = Word<kRowsPerThread>::load(pw + job_stride),
-           nf = Word<kRowsPerThread>::load(pw + 2 * job_stride);
   for (int l = 0; l < N; ++l) {
     const float qp = pl.qp[l];
     uint32_t w[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) w[t] = pl.w[l][t];
     // bytes as D + 128, E + 128, F + 128 (unsigned)
-    const uint32_t wd = nd ^ 0x80808080u, we = ne ^ 0x80808080u, wf = nf ^ 0x80808080u;
-    if (l + 1 < N) {
-      pw += 3 * job_stride;
-      nd = Word<kRowsPerThread>::load(pw);
-      ne = Word<kRowsPerThread>::load(pw + job_stride);
-      nf = Word<kRowsPerThread>::load(pw + 2 * job_stride);
-    }
+    const uint32_t wd = smem_word<kRowsPerThread>(crt_smem, 3 * l, rr) ^ 0x80808080u;
+    const uint32_t we = smem_word<kRowsPerThread>(crt_smem, 3 * l + 1, rr) ^ 0x80808080u;
+    const uint32_t wf = smem_word<kRowsPerThread>(crt_smem, 3 * l + 2, rr) ^ 0x80808080u;
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int d = static_cast<int>((wd >> (8 * q)) & 0xFFu);
@@ -292,10 +308,13 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
                                                const int16_t* __restrict__ y, double ar, double br,
                                                void* __restrict__ Cv, int64_t ldc, int64_t j, int64_t iblock) {
   const int64_t i0 = (iblock * kThreads + threadIdx.x) * kRowsPerThread;
-  if (i0 >= m) return;
   const int N = pl.N;
   const int64_t job_stride = n * ldr;
-  const int8_t* base = res + j * ldr + i0;
+  const int64_t row0 = iblock * kThreads * kRowsPerThread;
+  extern __shared__ int8_t crt_smem[];
+  stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, N, ldr - row0);
+  if (i0 >= m) return;
+  const int rr = threadIdx.x * kRowsPerThread;
   uint64_t acc[kRowsPerThread][L];
   float est[kRowsPerThread];
 #pragma unroll
@@ -304,18 +323,12 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
 #pragma unroll
     for (int t = 0; t < L; ++t) acc[q][t] = pl.K[t];
   }
-  const int8_t* pw = base;
-  uint32_t nw = Word<kRowsPerThread>::load(pw);
   for (int l = 0; l < N; ++l) {
     const float qp = pl.qp[l];
     uint32_t w[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) w[t] = pl.w[l][t];
-    const uint32_t wv = nw ^ 0x80808080u;          // bytes as E' + 128
-    if (l + 1 < N) {
-      pw += job_stride;
-      nw = Word<kRowsPerThread>::load(pw);
-    }
+    const uint32_t wv = smem_word<kRowsPerThread>(crt_smem, l, rr) ^ 0x80808080u;   // bytes as E' + 128
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const uint32_t u = (wv >> (8 * q)) & 0xFFu;
@@ -385,13 +398,14 @@ template <int L, int R, bool ROBUST>
 void launch_lrr(bool single, bool real, dim3 grid, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                 int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
                 int64_t ldc, cudaStream_t st) {
+  const size_t sm = static_cast<size_t>(real ? 1 : 3) * pl.N * kThreads * R;   // staged residues
   if (real) {
-    if (single) crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
-    else crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+    if (single) crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+    else crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
   } else if (single) {
-    crt_kernel<L, true, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+    crt_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   } else {
-    crt_kernel<L, false, R, ROBUST><<<grid, kThreads, 0, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+    crt_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   }
 }
 
@@ -581,8 +595,9 @@ template <int L>
 cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long long blocks, const Plan& pl,
                              cudaStream_t st) {
   const unsigned int gb = static_cast<unsigned int>(blocks);
-  if (single) crt_grouped<L, true><<<gb, kThreads, 0, st>>>(probs, nprob, pl);
-  else crt_grouped<L, false><<<gb, kThreads, 0, st>>>(probs, nprob, pl);
+  const size_t sm = static_cast<size_t>(3) * pl.N * kThreads * 4;                 // staged residues
+  if (single) crt_grouped<L, true><<<gb, kThreads, sm, st>>>(probs, nprob, pl);
+  else crt_grouped<L, false><<<gb, kThreads, sm, st>>>(probs, nprob, pl);
   count_launches(1);
   return cudaGetLastError();
 }

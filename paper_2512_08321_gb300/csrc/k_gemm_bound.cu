@@ -1,0 +1,265 @@
+// K1 (accurate mode, Section III-B eqs. mu-accu / nu-accu): the exact bound
+// products of the 7-bit ceiling planes on the 5th-generation tensor cores,
+// reduced on the fly to the row and column maxima the exponent rule needs.
+#include "tc_common.cuh"
+
+namespace emu {
+namespace {
+
+// Exact non-negative bound products of
+// the 7-bit ceiling planes (entries <= 64, products <= 2^12).  Planes of both
+// operands: 0 = X_R (real input: X), 1 = X_I, 2 = X_R - X_I.
+//   complex: slot 0 = C-bar_I = A-bar_I B-bar_R + A-bar_R B-bar_I (2 nkb k-blocks),
+//            slot 1 = (A-bar_R - A-bar_I)(B-bar_R - B-bar_I) (nkb k-blocks),
+//            C-bar_R = C-bar_I + slot 1 (the identity of Section III-B);
+//   real:    slot 0 = C-bar = A-bar B-bar.
+// FP32 accumulation is exact while partial sums stay below 2^24, so each
+// accumulation restarts every kBoundChunk k-blocks (2048 k: sums <= 2^23) and
+// the epilogue adds the chunk into int32 registers.  At the end of a tile each
+// epilogue thread holds one output column (TMEM lane) and 32 output rows; the
+// row maxima over columns (a 5-step butterfly across the warp) and the column
+// maxima over rows of max(C-bar_R, C-bar_I) go to global memory by atomicMax.
+// Output rows/columns beyond m/n read TMA's zero fill, so they add nothing.
+constexpr int kBoundBN = 64;
+constexpr int kBoundChunk = 32;
+constexpr int kBoundStages = 8;        // 24 KB stages: deeper than the main kernel's 48 KB ones
+constexpr int kBoundSmem = kBoundStages * Cfg<kBoundBN>::kStageBytes + 1024 + 256;
+
+struct BoundSched {
+  int TJ, TI, tiles, group, nkb, real;
+};
+
+// which operand planes and k-block of the planes feed k-block kb of a slot
+__device__ __forceinline__ void bound_src(int slot, int kb, int nkb, bool real, int& pa, int& pb, int& kc) {
+  if (real) { pa = 0; pb = 0; kc = kb; return; }
+  if (slot == 1) { pa = 2; pb = 2; kc = kb; return; }
+  if (kb < nkb) { pa = 0; pb = 1; kc = kb; }        // B-bar_R (MMA A) x A-bar_I (MMA B)
+  else { pa = 1; pb = 0; kc = kb - nkb; }           // B-bar_I x A-bar_R
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bound_kernel(const __grid_constant__ CUtensorMap mapA,   // B-bar planes: MMA operand A
+                      const __grid_constant__ CUtensorMap mapB,   // A-bar planes: MMA operand B
+                      const BoundSched s, unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
+                      int64_t m, int64_t n, unsigned int* status) {
+  constexpr int BN = kBoundBN;
+  using C = Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kBoundStages * C::kStageBytes);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (kBoundStages + i); };
+  auto tfull = [&](int i) { return bar0 + 8u * (2 * kBoundStages + i); };
+  auto tempty = [&](int i) { return bar0 + 8u * (2 * kBoundStages + 2 + i); };
+  const uint32_t done = bar0 + 8u * (2 * kBoundStages + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kBoundStages + 5);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Ctl ctl{status, abort_s};
+  const bool real = s.real != 0;
+  const int len0 = real ? s.nkb : 2 * s.nkb, len1 = real ? 0 : s.nkb;
+  const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk, nch1 = (len1 + kBoundChunk - 1) / kBoundChunk;
+  const long long nunits = s.tiles;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBoundStages; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull(i), 1);
+      mbar_init(tempty(i), 32 * kEpiWarps);
+    }
+    mbar_init(done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      long long it = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+        int tj, ti;
+        tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
+        for (int c = 0; ok && c < nch0; ++c) {
+          for (int slot = 0; ok && slot < 2; ++slot) {
+            const int len = slot ? len1 : len0;
+            if (c * kBoundChunk >= len) continue;
+            const int kb1 = min(len, (c + 1) * kBoundChunk);
+            for (int kb = c * kBoundChunk; kb < kb1; ++kb, ++it) {
+              const int st = static_cast<int>(it % kBoundStages);
+              const uint32_t ph = static_cast<uint32_t>((it / kBoundStages) & 1);
+              if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
+              int pa, pb, kc;
+              bound_src(slot, kb, s.nkb, real, pa, pb, kc);
+              const uint32_t sa = base + st * C::kStageBytes;
+              mbar_expect_tx(full(st), C::kStageBytes);
+              tma_load_3d(sa, &mapA, full(st), kc * BK, tj * BM, pa);
+              tma_load_3d(sa + kStageA, &mapB, full(st), kc * BK, ti * BN, pb);
+            }
+          }
+        }
+      }
+      for (int st = 0; st < kBoundStages; ++st) {
+        if (it <= st) continue;
+        const long long last = st + ((it - 1 - st) / kBoundStages) * kBoundStages;
+        const uint32_t ph = static_cast<uint32_t>((last / kBoundStages) & 1);
+        const long long t0 = clock64();
+        while (!mbar_try(full(st), ph) && clock64() - t0 < kWaitLimit) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      long long it = 0;
+      int used[2] = {0, 0};
+      bool ok = true;
+      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+        for (int c = 0; ok && c < nch0; ++c) {
+          for (int slot = 0; ok && slot < 2; ++slot) {
+            const int len = slot ? len1 : len0;
+            if (c * kBoundChunk >= len) continue;
+            if (!mbar_wait(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u, ctl)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
+            const int kb0 = c * kBoundChunk, kb1 = min(len, (c + 1) * kBoundChunk);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+              const int st = static_cast<int>(it % kBoundStages);
+              const uint32_t ph = static_cast<uint32_t>((it / kBoundStages) & 1);
+              if (!mbar_wait(full(st), ph, ctl)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t sa = base + st * C::kStageBytes;
+              const uint64_t da = smem_desc(sa), db = smem_desc(sa + kStageA);
+#pragma unroll
+              for (int kk = 0; kk < BK / UK; ++kk) {
+                const uint64_t off = static_cast<uint64_t>((kk * UK * 2) >> 4);
+                mma_f16(td, da + off, db + off, C::kIdesc, !(kb == kb0 && kk == 0));   // fresh sum per chunk
+              }
+              mma_commit(empty(st));
+            }
+            if (!ok) break;
+            mma_commit(tfull(slot));
+            ++used[slot];
+          }
+        }
+      }
+      mma_commit(done);
+      const long long t0 = clock64();
+      while (!mbar_try(done, 0u) && clock64() - t0 < kWaitLimit) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    int used[2] = {0, 0};
+    bool ok = true;
+    for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      int tj, ti;
+      tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
+      int acc0[32], acc1[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) acc0[q] = acc1[q] = 0;
+      for (int c = 0; ok && c < nch0; ++c) {
+        for (int slot = 0; ok && slot < 2; ++slot) {
+          const int len = slot ? len1 : len0;
+          if (c * kBoundChunk >= len) continue;
+          if (!mbar_wait(tfull(slot), static_cast<uint32_t>(used[slot] & 1), ctl)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) +
+                              static_cast<uint32_t>(slot * BN + half * 32);
+          uint32_t v[32];
+          tmem_ld32(ta, v);
+          tmem_wait_ld();
+          tc_fence_before();
+          mbar_arrive(tempty(slot));
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int x = static_cast<int>(__uint_as_float(v[q]));   // exact integer
+            if (slot) acc1[q] += x; else acc0[q] += x;
+          }
+          ++used[slot];
+        }
+      }
+      if (!ok) break;
+      // max(C-bar_R, C-bar_I) per (row q, this column)
+      unsigned int colmax = 0u;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int cr = real ? acc0[q] : acc0[q] + acc1[q];
+        acc0[q] = max(cr, acc0[q]);
+        colmax = max(colmax, static_cast<unsigned int>(acc0[q]));
+      }
+      const int64_t col = static_cast<int64_t>(tj) * BM + quad * 32 + lane;
+      if (col < n) atomicMax(Ncol + col, colmax);
+      // butterfly: after the step with distance d each lane keeps the maxima of half
+      // of its rows; in the end lane L holds the maximum over the warp of row L
+#pragma unroll
+      for (int d = 16; d >= 1; d >>= 1) {
+        const bool up = (lane & d) != 0;
+#pragma unroll
+        for (int t = 0; t < d; ++t) {
+          const int send = up ? acc0[t] : acc0[t + d];
+          const int keep = up ? acc0[t + d] : acc0[t];
+          acc0[t] = max(keep, __shfl_xor_sync(0xffffffffu, send, d));
+        }
+      }
+      const int64_t row = static_cast<int64_t>(ti) * BN + half * 32 + lane;
+      if (row < m) atomicMax(Mrow + row, static_cast<unsigned int>(acc0[0]));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::kTmemCols));
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, const void* planesA,
+                              const void* planesB, unsigned int* Mrow, unsigned int* Ncol, unsigned int* status,
+                              cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (kpad % BK || ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u))
+    return cudaErrorInvalidValue;
+  if (!get_encoder()) return cudaErrorNotSupported;
+  static cudaError_t attr =
+      cudaFuncSetAttribute(gemm_bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoundSmem);
+  if (attr != cudaSuccess) return attr;
+  const int planes = real ? 1 : 3;
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, planesB, n, kpad, planes, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, planesA, m, kpad, planes, kBoundBN)) return cudaErrorInvalidValue;
+  BoundSched s;
+  s.TJ = static_cast<int>((n + BM - 1) / BM);
+  s.TI = static_cast<int>((m + kBoundBN - 1) / kBoundBN);
+  s.tiles = s.TJ * s.TI;
+  s.group = 16;
+  s.nkb = static_cast<int>(kpad / BK);
+  s.real = real ? 1 : 0;
+  const int grid = s.tiles < g_sms ? s.tiles : g_sms;
+  gemm_bound_kernel<<<grid, kThreads, kBoundSmem, st>>>(mapA, mapB, s, Mrow, Ncol, m, n, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace emu
