@@ -401,6 +401,11 @@ def main():
                                 "speedup_of_emulation": nms / ms,
                                 "math_mode": "default (CUBLAS_EMULATION_STRATEGY %s)"
                                              % os.environ.get("CUBLAS_EMULATION_STRATEGY", "unset")}
+    if rank == 0 and not args.no_native and not real:
+        g3 = gemm3m(torch, A, B, C, m, n, k, single, st)
+        if g3:
+            g3["speedup_of_emulation"] = g3["ms"] / ms
+        out["native_cublas_3m"] = g3
     if rank == 0 and not args.no_plain and not real:
         out["plain_emulation"] = plain_emulation(emu, torch, A, B, wl, C)
 
@@ -412,6 +417,48 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def gemm3m(torch, A, B, C, m, n, k, single, stream):
+    """cuBLAS's Gauss 3-multiplication complex GEMM (cublasZgemm3m / cublasCgemm3m, the paper's
+    Zgemm3m comparator), called through ctypes on the same device buffers; None if unavailable."""
+    import ctypes
+    try:
+        cb = None
+        for nm in ("libcublas.so.13", "libcublas.so"):
+            try:
+                cb = ctypes.CDLL(nm)
+                break
+            except OSError:
+                continue
+        if cb is None:
+            return None
+        h = ctypes.c_void_p()
+        if cb.cublasCreate_v2(ctypes.byref(h)) != 0:
+            return None
+        cb.cublasSetStream_v2(h, ctypes.c_void_p(stream.cuda_stream))
+        T = ctypes.c_float if single else ctypes.c_double
+        one, zero = (T * 2)(1.0, 0.0), (T * 2)(0.0, 0.0)
+        fn = cb.cublasCgemm3m if single else cb.cublasZgemm3m
+        call = lambda: fn(h, 0, 0, m, n, k, one, ctypes.c_void_p(A.data_ptr()), m, ctypes.c_void_p(B.data_ptr()), k,
+                          zero, ctypes.c_void_p(C.data_ptr()), m)
+        if call() != 0:
+            cb.cublasDestroy_v2(h)
+            return None
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        st = call()
+        b.record()
+        torch.cuda.synchronize()
+        cb.cublasDestroy_v2(h)
+        if st != 0:
+            return None
+        ms = a.elapsed_time(b)
+        return {"routine": "cublasCgemm3m" if single else "cublasZgemm3m", "ms": ms,
+                "tflops": 8.0 * m * n * k / (ms * 1e-3) * 1e-12}
+    except Exception:
+        return None
 
 
 def max_over_ranks(ms, dist):

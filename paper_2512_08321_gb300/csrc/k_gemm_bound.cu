@@ -14,16 +14,20 @@ namespace {
 //            C-bar_R = C-bar_I + slot 1 (the identity of Section III-B);
 //   real:    slot 0 = C-bar = A-bar B-bar.
 // FP32 accumulation is exact while partial sums stay below 2^24, so each
-// accumulation restarts every kBoundChunk k-blocks (2048 k: sums <= 2^23) and
-// the epilogue adds the chunk into int32 registers.  At the end of a tile each
-// epilogue thread holds one output column (TMEM lane) and 32 output rows; the
-// row maxima over columns (a 5-step butterfly across the warp) and the column
-// maxima over rows of max(C-bar_R, C-bar_I) go to global memory by atomicMax.
-// Output rows/columns beyond m/n read TMA's zero fill, so they add nothing.
-constexpr int kBoundBN = 64;
+// accumulation restarts every kBoundChunk k-blocks (2048 k: sums <= 2^23).
+// TMEM holds, per slot, the FP32 accumulator (128 columns) and an int32
+// running sum (128 columns): after each chunk the epilogue adds the chunk
+// into the running sum, so the MMA can start the next chunk in the FP32 half.
+// At the end of a tile each epilogue thread reads one output column (TMEM
+// lane) and 64 output rows; the row maxima over columns (5-step butterflies
+// across the warp) and the column maxima over rows of max(C-bar_R, C-bar_I) go
+// to global memory by atomicMax.  Rows/columns beyond m/n read TMA's zero
+// fill, so they add nothing.
+constexpr int kBoundBN = 128;
 constexpr int kBoundChunk = 32;
-constexpr int kBoundStages = 8;        // 24 KB stages: deeper than the main kernel's 48 KB ones
+constexpr int kBoundStages = 6;        // 32 KB stages
 constexpr int kBoundSmem = kBoundStages * Cfg<kBoundBN>::kStageBytes + 1024 + 256;
+constexpr int kBoundTmemCols = 512;    // 2 slots x (128 FP32 + 128 int32) columns
 
 struct BoundSched {
   int TJ, TI, tiles, group, nkb, real;
@@ -62,7 +66,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   Ctl ctl{status, abort_s};
   const bool real = s.real != 0;
   const int len0 = real ? s.nkb : 2 * s.nkb, len1 = real ? 0 : s.nkb;
-  const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk, nch1 = (len1 + kBoundChunk - 1) / kBoundChunk;
+  const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk;   // len1 <= len0: slot 1 has no more chunks
   const long long nunits = s.tiles;
 
   if (threadIdx.x == 0) {
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(C::kTmemCols));
+                 "r"(kBoundTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   tc_fence_before();
@@ -168,61 +172,75 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int half = ew >> 2;
+    const int half = ew >> 2;                        // columns [64 half, 64 half + 64) of a slot
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quad * 32) << 16);
+    auto fp_col = [&](int slot, int piece) { return lane_base + static_cast<uint32_t>(slot * BN + half * 64 + 32 * piece); };
+    auto in_col = [&](int slot, int piece) {
+      return lane_base + static_cast<uint32_t>(2 * BN + slot * BN + half * 64 + 32 * piece);
+    };
     int used[2] = {0, 0};
     bool ok = true;
     for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
       int tj, ti;
       tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
-      int acc0[32], acc1[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) acc0[q] = acc1[q] = 0;
       for (int c = 0; ok && c < nch0; ++c) {
         for (int slot = 0; ok && slot < 2; ++slot) {
           const int len = slot ? len1 : len0;
           if (c * kBoundChunk >= len) continue;
           if (!mbar_wait(tfull(slot), static_cast<uint32_t>(used[slot] & 1), ctl)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) +
-                              static_cast<uint32_t>(slot * BN + half * 32);
-          uint32_t v[32];
-          tmem_ld32(ta, v);
-          tmem_wait_ld();
+#pragma unroll 1
+          for (int piece = 0; piece < 2; ++piece) {
+            uint32_t v[32], a[32];
+            tmem_ld32(fp_col(slot, piece), v);
+            if (c > 0) tmem_ld32(in_col(slot, piece), a);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int x = static_cast<int>(__uint_as_float(v[q]));   // exact integer
+              a[q] = static_cast<uint32_t>((c > 0 ? static_cast<int>(a[q]) : 0) + x);
+            }
+            tmem_st32(in_col(slot, piece), a);
+          }
+          tmem_wait_st();
           tc_fence_before();
           mbar_arrive(tempty(slot));
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int x = static_cast<int>(__uint_as_float(v[q]));   // exact integer
-            if (slot) acc1[q] += x; else acc0[q] += x;
-          }
           ++used[slot];
         }
       }
       if (!ok) break;
-      // max(C-bar_R, C-bar_I) per (row q, this column)
-      unsigned int colmax = 0u;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int cr = real ? acc0[q] : acc0[q] + acc1[q];
-        acc0[q] = max(cr, acc0[q]);
-        colmax = max(colmax, static_cast<unsigned int>(acc0[q]));
-      }
+      // max(C-bar_R, C-bar_I) per (row, this column); rows of this thread: 64 half + 32 piece + q
       const int64_t col = static_cast<int64_t>(tj) * BM + quad * 32 + lane;
-      if (col < n) atomicMax(Ncol + col, colmax);
-      // butterfly: after the step with distance d each lane keeps the maxima of half
-      // of its rows; in the end lane L holds the maximum over the warp of row L
+      unsigned int colmax = 0u;
+#pragma unroll 1
+      for (int piece = 0; piece < 2; ++piece) {
+        uint32_t a0[32], a1[32];
+        tmem_ld32(in_col(0, piece), a0);
+        if (!real) tmem_ld32(in_col(1, piece), a1);
+        tmem_wait_ld();
+        int r[32];
 #pragma unroll
-      for (int d = 16; d >= 1; d >>= 1) {
-        const bool up = (lane & d) != 0;
-#pragma unroll
-        for (int t = 0; t < d; ++t) {
-          const int send = up ? acc0[t] : acc0[t + d];
-          const int keep = up ? acc0[t + d] : acc0[t];
-          acc0[t] = max(keep, __shfl_xor_sync(0xffffffffu, send, d));
+        for (int q = 0; q < 32; ++q) {
+          const int ci = static_cast<int>(a0[q]);
+          const int cr = real ? ci : ci + static_cast<int>(a1[q]);
+          r[q] = max(cr, ci);
+          colmax = max(colmax, static_cast<unsigned int>(r[q]));
         }
+        // butterfly: lane L ends with the maximum over the warp of row L of this piece
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+          const bool up = (lane & d) != 0;
+#pragma unroll
+          for (int t = 0; t < d; ++t) {
+            const int send = up ? r[t] : r[t + d];
+            const int keep = up ? r[t + d] : r[t];
+            r[t] = max(keep, __shfl_xor_sync(0xffffffffu, send, d));
+          }
+        }
+        const int64_t row = static_cast<int64_t>(ti) * BN + half * 64 + 32 * piece + lane;
+        if (row < m) atomicMax(Mrow + row, static_cast<unsigned int>(r[0]));
       }
-      const int64_t row = static_cast<int64_t>(ti) * BN + half * 32 + lane;
-      if (row < m) atomicMax(Mrow + row, static_cast<unsigned int>(acc0[0]));
+      if (col < n) atomicMax(Ncol + col, colmax);
     }
   }
 
@@ -230,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::kTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBoundTmemCols));
 }
 
 }  // namespace

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict_
 }
 
 // one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
-template <bool SINGLE, typename T>
+template <bool SINGLE, typename T, int NCH = 0>
 __global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __restrict__ segs, int nseg,
                                                           const __grid_constant__ Plan pl) {
   __shared__ SplitSmem sm;
@@ -375,9 +375,11 @@ __global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __rest
   const int64_t rt = local / g.htiles, ht = local % g.htiles;
   T* planes = static_cast<T*>(g.planes);
   if (g.rows_contig)
-    split_block<SINGLE, true, T, 4>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
+    split_block<SINGLE, true, T, 4, false, NCH>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad,
+                                                planes, rt, ht);
   else
-    split_block<SINGLE, false, T, 4>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad, planes, rt, ht);
+    split_block<SINGLE, false, T, 4, false, NCH>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad,
+                                                 planes, rt, ht);
 }
 
 template <bool SINGLE, typename T, bool R>
@@ -441,12 +443,32 @@ cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_de
   if (nseg <= 0 || blocks <= 0) return cudaSuccess;
   if (blocks > 2147483647LL) return cudaErrorInvalidValue;
   const unsigned int gb = static_cast<unsigned int>(blocks);
-  if (single) {
-    if (fp16) split_grouped<true, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
-    else split_grouped<true, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
-  } else {
-    if (fp16) split_grouped<false, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
-    else split_grouped<false, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+  // fp16 planes: the chunk count compiled in, as in the single-GEMM split
+  auto fixed = [&](auto nch_tag) {
+    constexpr int NC = decltype(nch_tag)::value;
+    if (single) split_grouped<true, __half, NC><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+    else split_grouped<false, __half, NC><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+  };
+  bool done = fp16;
+  if (fp16) {
+    switch (pl.nchunk) {
+      case 3: fixed(std::integral_constant<int, 3>{}); break;
+      case 4: fixed(std::integral_constant<int, 4>{}); break;
+      case 5: fixed(std::integral_constant<int, 5>{}); break;
+      case 6: fixed(std::integral_constant<int, 6>{}); break;
+      case 7: fixed(std::integral_constant<int, 7>{}); break;
+      case 8: fixed(std::integral_constant<int, 8>{}); break;
+      default: done = false;
+    }
+  }
+  if (!done) {
+    if (single) {
+      if (fp16) split_grouped<true, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+      else split_grouped<true, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+    } else {
+      if (fp16) split_grouped<false, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+      else split_grouped<false, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+    }
   }
   count_launches(1);
   return cudaGetLastError();
