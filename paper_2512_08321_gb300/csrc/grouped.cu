@@ -106,11 +106,16 @@ std::string signature(bool single, int N, const std::vector<emu_grouped_s::Prob>
   return buf;
 }
 
+// Descriptors, then the first unit of every problem as a compact array the
+// residue-product kernel scans (long long per problem).
 emu_status_t upload_gemm_descs(emu_grouped_s* g, int tile_n, void* d_dst, long long* total_units) {
-  std::vector<unsigned char> host(group_problem_bytes() * g->probs.size());
+  const size_t np = g->probs.size();
+  std::vector<unsigned char> host(group_problem_bytes() * np + sizeof(long long) * np);
+  long long* ubeg = reinterpret_cast<long long*>(host.data() + group_problem_bytes() * np);
   long long units = 0;
-  for (size_t i = 0; i < g->probs.size(); ++i) {
+  for (size_t i = 0; i < np; ++i) {
     const auto& p = g->probs[i];
+    ubeg[i] = units;
     if (!fill_group_problem(host.data() + i * group_problem_bytes(), p.m, p.n, p.kpad, g->N, p.pa, p.pb, p.res, p.ldr,
                             g->chunk_k, g_f16_group, tile_n, &units))
       return EMU_ERR_CUDA;
@@ -250,7 +255,7 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
   const size_t off_exp = o;     o += al(sizeof(ExpSeg) * 2 * nl + 1);
   const size_t off_rowb = o;    o += al(sizeof(long long) * (2 * nl + 1));
   const size_t off_split = o;   o += al(sizeof(SplitSeg) * 2 * nl + 1);
-  const size_t off_gp = o;      o += al(group_problem_bytes() * nl + 1);
+  const size_t off_gp = o;      o += al((group_problem_bytes() + sizeof(long long)) * nl + 1);
   const size_t off_crt = o;     o += al(sizeof(CrtProb) * nl + 1);
   g->mem_bytes = o;
   if (cudaMalloc(&g->mem, o) != cudaSuccess) {

@@ -68,7 +68,7 @@ struct SingleWork {
   int8_t* res;
   int64_t ldr, n;
   __device__ long long units() const { return s.units; }
-  __device__ Unit get(long long u) const {
+  __device__ Unit get(long long u, int& /*hint*/) const {
     Unit w;
     const int pair = static_cast<int>(u / s.tiles);
     const int t = static_cast<int>(u % s.tiles);
@@ -100,15 +100,17 @@ struct GroupProblem {  // CUtensorMap members give it 64-byte alignment
 
 struct GroupWork {
   const GroupProblem* probs;
+  const long long* ubeg;            // first unit of each problem (compact copy of unit_begin)
   int count;
   long long total;
   __device__ long long units() const { return total; }
-  __device__ Unit get(long long u) const {
-    int lo = 0, hi = count - 1;       // last problem with unit_begin <= u
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (probs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
-    }
+  // `hint`: the problem of the caller's previous unit.  Each role of a CTA
+  // visits units in increasing order, so the problem index only moves forward
+  // (usually by 0 or 1) and a short forward scan replaces a binary search.
+  __device__ Unit get(long long u, int& hint) const {
+    int lo = hint;
+    while (lo + 1 < count && ubeg[lo + 1] <= u) ++lo;
+    hint = lo;
     const GroupProblem& P = probs[lo];
     const long long v = u - P.unit_begin;
     Unit w;
@@ -181,8 +183,9 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       long long it = 0;
       bool ok = true;
       const CUtensorMap* fenced = nullptr;
+      int hint = 0;
       for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Unit U = W.get(u);
+        const Unit U = W.get(u, hint);
         if (fence_maps && U.mapA != fenced) {
           // descriptors written by the host into global memory: acquire them for the TMA unit
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(U.mapA) : "memory");
@@ -222,8 +225,9 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       long long it = 0;
       int used[2] = {0, 0};
       bool ok = true;
+      int hint = 0;
       for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Unit U = W.get(u);
+        const Unit U = W.get(u, hint);
         for (int c = 0; ok && c < U.nch; ++c) {
           for (int which = 0; ok && which < 2; ++which) {
             const int job = which ? U.jb : U.ja;
@@ -269,8 +273,9 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
     const int row_in_tile = quad * 32 + lane;       // output column within the tile
     int used[2] = {0, 0};
     bool ok = true;
+    int hint = 0;
     for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-      const Unit U = W.get(u);
+      const Unit U = W.get(u, hint);
       const int64_t col = static_cast<int64_t>(U.tj) * BM + row_in_tile;
       for (int c = 0; ok && c < U.nch; ++c) {
         const bool last = (c == U.nch - 1);
@@ -370,7 +375,7 @@ template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_f16_grouped_kernel(const GroupProblem* __restrict__ probs, int count, long long total,
                             const __grid_constant__ Plan pl, unsigned int* status) {
-  const GroupWork W{probs, count, total};
+  const GroupWork W{probs, reinterpret_cast<const long long*>(probs + count), count, total};
   gemm_body<BN>(W, pl, status, true);
 }
 
