@@ -205,9 +205,11 @@ int64_t choose_nblock(const DeviceState* ds, int64_t m, int64_t n, int64_t k, in
   return lo > 0 ? 128 * lo : n;            // nothing fits: one block, and the workspace check reports it
 }
 
+// b_ready (host-buffer calls): B is still arriving on another stream; A's
+// phases run first and the stream waits on the event before B is touched.
 emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
                   const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
-                  void* C, int64_t ldc, int N, void* stream) {
+                  void* C, int64_t ldc, int N, void* stream, cudaEvent_t b_ready = nullptr) {
   emu_status_t s = check_common(ta, tb, m, n, k, lda, ldb, ldc, N, true);
   if (s != EMU_OK) return s;
   if (m == 0 || n == 0) return EMU_OK;
@@ -255,10 +257,12 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   };
   cudaError_t e;
   phase(0, st);
+  const bool a_first = (b_ready != nullptr);
   if (k == 0) {
     // empty inner dimension: the product is zero
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = cudaMemsetAsync(y, 0, static_cast<size_t>(n) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
+    if (a_first && cudaStreamWaitEvent(st, b_ready, 0) != cudaSuccess) return EMU_ERR_CUDA;
   } else if (accurate) {
     // Section III-B accurate mode: pre-scaling, 7-bit ceiling planes, bound products, exponents
     int* emA = reinterpret_cast<int*>(ws + L.off_acc);
@@ -272,6 +276,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
         launch_exp_max(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, st) != cudaSuccess ||
         launch_bound_split(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, L.kpad, pa, st) != cudaSuccess)
       return EMU_ERR_CUDA;
+    if (a_first && cudaStreamWaitEvent(st, b_ready, 0) != cudaSuccess) return EMU_ERR_CUDA;
     for (int64_t j0 = 0; j0 < n; j0 += nb) {
       const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
       const void* Bj = block_ptr(j0);
@@ -289,6 +294,13 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   } else {
     if ((e = launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, st, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
+    if (a_first) {
+      // A's planes while B is in flight
+      if ((e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, st, tn.split_elems,
+                            dt.real)) != cudaSuccess ||
+          cudaStreamWaitEvent(st, b_ready, 0) != cudaSuccess)
+        return EMU_ERR_CUDA;
+    }
   }
   for (int64_t j0 = 0; j0 < n; j0 += nb) {
     const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
@@ -303,7 +315,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
           (e = launch_exponents(dt.single, Bj, nj, k, rsb, hsb, *pl, yj, scr, st, dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
       phase(1, st);
-      if (j0 == 0 &&
+      if (j0 == 0 && !(a_first && !accurate) &&
           (e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, st, tn.split_elems,
                             dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
@@ -329,8 +341,8 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
 
 emu_status_t run_gemm(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar,
                       double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi, void* C,
-                      int64_t ldc, int N, void* stream) {
-  return gemm(Dt{single, real}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream);
+                      int64_t ldc, int N, void* stream, cudaEvent_t b_ready) {
+  return gemm(Dt{single, real}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream, b_ready);
 }
 
 emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,

@@ -200,7 +200,7 @@ extern int g_f16_group;
 // GEMM entry shared by the device- and host-buffer calls (api.cu).
 emu_status_t run_gemm(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar,
                       double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi, void* C,
-                      int64_t ldc, int N, void* stream);
+                      int64_t ldc, int N, void* stream, cudaEvent_t b_ready = nullptr);
 emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
                              int64_t ldc, int N);
 emu_status_t set_bad_param(int idx);

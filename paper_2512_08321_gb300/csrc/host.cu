@@ -6,6 +6,8 @@
 // memory, with no separate device-to-host pass.  A host pointer is used from
 // kernels when it is pinned or registered (its device address); pageable
 // memory goes through cudaMemcpyAsync and a device copy of C.
+#include <mutex>
+
 #include "emu_internal.h"
 
 namespace emu {
@@ -71,6 +73,31 @@ size_t stored_bytes(int64_t rows, int64_t cols, int64_t ld, size_t esz) {
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
+// Per-device side stream and events: B is brought in on the side stream while
+// A is copied and processed on the caller's stream.
+struct Side {
+  cudaStream_t s = nullptr;
+  cudaEvent_t start = nullptr, b_done = nullptr;
+};
+std::mutex g_side_mu;
+Side g_side[64];
+
+cudaError_t side_for_device(Side** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  Side& sd = g_side[dev];
+  if (!sd.s) {
+    if ((e = cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&sd.start, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&sd.b_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  *out = &sd;
+  return cudaSuccess;
+}
+
 emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k,
                        double ar, double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br,
                        double bi, void* C, int64_t ldc, int N, void* stream) {
@@ -93,12 +120,19 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
   char* dA = stg;
   char* dB = stg + al(bA);
   char* dC = dB + al(bB);
-  auto bring = [&](char* dst, const void* src, size_t bytes) -> cudaError_t {
+  Side* sd = nullptr;
+  if (side_for_device(&sd) != cudaSuccess) return EMU_ERR_CUDA;
+  auto bring = [&](char* dst, const void* src, size_t bytes, cudaStream_t s2) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;
     const void* v = device_view(src);
-    return v ? copy_bytes(dst, v, bytes, st) : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    return v ? copy_bytes(dst, v, bytes, s2) : cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s2);
   };
-  if (bring(dA, A, bA) != cudaSuccess || bring(dB, B, bB) != cudaSuccess) return EMU_ERR_CUDA;
+  // A first on the caller's stream; then B on the side stream (the link carries
+  // one copy at a time) while A's exponents and planes are formed
+  if (bring(dA, A, bA, st) != cudaSuccess || cudaEventRecord(sd->start, st) != cudaSuccess ||
+      cudaStreamWaitEvent(sd->s, sd->start, 0) != cudaSuccess || bring(dB, B, bB, sd->s) != cudaSuccess ||
+      cudaEventRecord(sd->b_done, sd->s) != cudaSuccess)
+    return EMU_ERR_CUDA;
   // pageable C: a device copy with the same leading dimension; only the m x n
   // entries travel, so the rows between columns stay as the caller left them
   const size_t pitch = static_cast<size_t>(ldc) * esz, width = static_cast<size_t>(m) * esz;
@@ -110,7 +144,7 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
       return EMU_ERR_CUDA;
   }
   s = run_gemm(single, real, ta, tb, m, n, k, ar, ai, bA ? dA : nullptr, lda, bB ? dB : nullptr, ldb, br, bi, target,
-               ldc, N, stream);
+               ldc, N, stream, sd->b_done);
   if (s != EMU_OK) return s;
   if (!Cv && cudaMemcpy2DAsync(C, pitch, dC, pitch, width, static_cast<size_t>(n), cudaMemcpyDeviceToHost, st) !=
                  cudaSuccess)

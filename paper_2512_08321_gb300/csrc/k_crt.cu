@@ -26,6 +26,8 @@
 //
 // Thread mapping: 4 consecutive rows i of one column j; the residue bytes of
 // those rows are one 32-bit word per job.
+#include <algorithm>
+
 #include "emu_internal.h"
 
 namespace emu {
@@ -212,14 +214,15 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
   const int N = pl.N;
   const int64_t job_stride = n * ldr;
   const int64_t row0 = iblock * kThreads * kRowsPerThread;
-  extern __shared__ int8_t crt_smem[];
+  extern __shared__ __align__(16) int8_t crt_smem[];
   stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, 3 * N, ldr - row0);
-  if (i0 >= m) return;
+  const bool active = i0 < m;
   const int rr = threadIdx.x * kRowsPerThread;
 
   // exact limb accumulators for the real and imaginary parts of 4 rows
   uint64_t accR[kRowsPerThread][L], accI[kRowsPerThread][L];
   float estR[kRowsPerThread], estI[kRowsPerThread];
+  if (active) {
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
     estR[q] = estI[q] = 0.0f;
@@ -255,22 +258,40 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
       estI[q] = fmaf(static_cast<float>(vi), qp, estI[q]);
     }
   }
+  }
+  // the residues are consumed: the buffer now holds the unscaled outputs, which
+  // are then written row-coalesced (thread t: rows t, t + 128, ...), so every
+  // store instruction of a warp covers one contiguous run of C -- also when C
+  // is host memory reached over the CPU-GPU link
+  __syncthreads();
+  double2* so = reinterpret_cast<double2*>(crt_smem);
   const int yj = y[j];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int64_t i = i0 + q;
+      if (i >= m) break;
+      const int xi = x[i];
+      double orr, oi;
+      if (xi == kExpNonfinite || yj == kExpNonfinite) {
+        orr = oi = __longlong_as_double(0x7FF8000000000000ll);
+      } else {
+        const int e2 = -(xi + yj);
+        orr = finish<L, ROBUST>(accR[q], estR[q], pl, e2);
+        oi = finish<L, ROBUST>(accI[q], estI[q], pl, e2);
+      }
+      so[rr + q] = make_double2(orr, oi);
+    }
+  }
+  __syncthreads();
   const bool plain = (ar == 1.0 && ai == 0.0 && br == 0.0 && bi == 0.0);
   const bool use_beta = !(br == 0.0 && bi == 0.0);
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
-    const int64_t i = i0 + q;
+    const int r = q * kThreads + threadIdx.x;
+    const int64_t i = row0 + r;
     if (i >= m) break;
-    const int xi = x[i];
-    double orr, oi;
-    if (xi == kExpNonfinite || yj == kExpNonfinite) {
-      orr = oi = __longlong_as_double(0x7FF8000000000000ll);
-    } else {
-      const int e2 = -(xi + yj);
-      orr = finish<L, ROBUST>(accR[q], estR[q], pl, e2);
-      oi = finish<L, ROBUST>(accI[q], estI[q], pl, e2);
-    }
+    double orr = so[r].x, oi = so[r].y;
     const int64_t ci = j * ldc + i;
     if (!plain) {
       double tr = __fma_rn(ar, orr, -__dmul_rn(ai, oi));
@@ -311,12 +332,13 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
   const int N = pl.N;
   const int64_t job_stride = n * ldr;
   const int64_t row0 = iblock * kThreads * kRowsPerThread;
-  extern __shared__ int8_t crt_smem[];
+  extern __shared__ __align__(16) int8_t crt_smem[];
   stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, N, ldr - row0);
-  if (i0 >= m) return;
+  const bool active = i0 < m;
   const int rr = threadIdx.x * kRowsPerThread;
   uint64_t acc[kRowsPerThread][L];
   float est[kRowsPerThread];
+  if (active) {
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
     est[q] = 0.0f;
@@ -337,15 +359,29 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
       est[q] = fmaf(static_cast<float>(static_cast<int>(u) - 128), qp, est[q]);
     }
   }
+  }
+  // outputs through shared memory, then written row-coalesced (as in crt_block)
+  __syncthreads();
+  double* so = reinterpret_cast<double*>(crt_smem);
   const int yj = y[j];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int64_t i = i0 + q;
+      if (i >= m) break;
+      const int xi = x[i];
+      so[rr + q] = (xi == kExpNonfinite || yj == kExpNonfinite) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                                : finish<L, ROBUST>(acc[q], est[q], pl, -(xi + yj));
+    }
+  }
+  __syncthreads();
   const bool plain = (ar == 1.0 && br == 0.0);
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
-    const int64_t i = i0 + q;
+    const int r = q * kThreads + threadIdx.x;
+    const int64_t i = row0 + r;
     if (i >= m) break;
-    const int xi = x[i];
-    double o = (xi == kExpNonfinite || yj == kExpNonfinite) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                            : finish<L, ROBUST>(acc[q], est[q], pl, -(xi + yj));
+    double o = so[r];
     const int64_t ci = j * ldc + i;
     if (!plain) {
       double t = __dmul_rn(ar, o);
@@ -398,7 +434,9 @@ template <int L, int R, bool ROBUST>
 void launch_lrr(bool single, bool real, dim3 grid, int64_t m, int64_t n, const Plan& pl, const int8_t* res,
                 int64_t ldr, const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
                 int64_t ldc, cudaStream_t st) {
-  const size_t sm = static_cast<size_t>(real ? 1 : 3) * pl.N * kThreads * R;   // staged residues
+  // staged residues, then the unscaled outputs (16 or 8 bytes a row)
+  const size_t sm = std::max(static_cast<size_t>(real ? 1 : 3) * pl.N * kThreads * R,
+                             static_cast<size_t>(real ? 8 : 16) * kThreads * R);
   if (real) {
     if (single) crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
     else crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
@@ -595,7 +633,8 @@ template <int L>
 cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long long blocks, const Plan& pl,
                              cudaStream_t st) {
   const unsigned int gb = static_cast<unsigned int>(blocks);
-  const size_t sm = static_cast<size_t>(3) * pl.N * kThreads * 4;                 // staged residues
+  const size_t sm = std::max(static_cast<size_t>(3) * pl.N * kThreads * 4,      // staged residues, then outputs
+                             static_cast<size_t>(16) * kThreads * 4);
   if (single) crt_grouped<L, true><<<gb, kThreads, sm, st>>>(probs, nprob, pl);
   else crt_grouped<L, false><<<gb, kThreads, sm, st>>>(probs, nprob, pl);
   count_launches(1);
