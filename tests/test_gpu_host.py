@@ -86,3 +86,26 @@ def test_host_buffers_with_leading_dimensions_and_k0():
 def test_host_argument_errors():
     assert emu.emu_zgemm_host("N", "N", 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 12) == emu.EMU_ERR_INVALID_ARG
     assert emu.emu_zgemm_host("N", "N", 4, 4, 4, 1.0, 1, 2, 1, 4, 0.0, 1, 4, 12) == emu.EMU_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kind", ["z", "d"])
+def test_host_buffers_accurate_mode_and_blocking(kind):
+    # accurate-mode scaling and column blocking run A's phases before B arrives
+    m, n, k, N = 150, 3 * 128 + 20, 120, 11
+    A, B, C = _mats(kind, m, n, k, "N", "N", 320)
+    try:
+        emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE), "scaling")
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 128), "nblock")
+        ref = _device_ref(kind, A, B, C, m, n, k, "N", "N", 1.0, 0.0, N)
+        f = KINDS[kind][2]
+        tA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+        tB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+        tC = torch.zeros((n, m), dtype=tA.dtype).pin_memory()
+        emu.check(f("N", "N", m, n, k, _scal(kind, 1.0), tA.data_ptr(), m, tB.data_ptr(), k, _scal(kind, 0.0),
+                    tC.data_ptr(), m, N), "host call")
+        torch.cuda.synchronize()
+    finally:
+        emu.emu_set_scaling(emu.EMU_SCALING_FAST)
+        emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 0)
+    got = tC.numpy().T
+    assert same_bits(np.ascontiguousarray(got), np.ascontiguousarray(ref)), mismatch_report(got, ref)
