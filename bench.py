@@ -334,6 +334,10 @@ def main():
                       "tuning": dict(zip(["tile_n", "group", "chunk_k", "crt_rows", "split_elems"], tuned))
                       if tuned else "defaults"},
            "roofline": roofline, "phases_ms": phases, "memory_phases": mem_phases,
+           # the paper counts the residue products as INT8 operations (6N mnk complex, 2N mnk real):
+           # their rate here, beside GB300's dense INT8 peak from its Table 1 (B300 row)
+           "int8_equivalent": {"tops": gemm_flops / t_gemm * 1e-12, "table1_int8_peak_tops": 150.0,
+                               "ratio_to_int8_peak": gemm_flops / t_gemm * 1e-12 / 150.0},
            "gpu_launches": int(launches), "device_status": emu.STATUS_NAMES.get(status, status),
            "clocks": clk.summary()}
 
