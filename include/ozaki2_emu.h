@@ -109,14 +109,20 @@ emu_status_t emu_sgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
 
 /* Host-buffer forms of the four GEMMs: A, B and C are in host memory (same
  * arguments, layouts and results as the device forms; alpha/beta as there).
- * The inputs are copied to a library-owned device staging buffer by a copy
- * kernel that reads host memory over the CPU-GPU link, and the CRT writes C
- * straight into host memory.  Host memory is read and written from kernels
- * when it is pinned or registered; pageable memory goes through
- * cudaMemcpyAsync and a device copy of C.
+ * The operands go through a library-owned device staging buffer.  A is
+ * copied first; the output columns are then processed in blocks (about eight
+ * blocks of a multiple of 256 columns, at least 1024; one block when n <= 2048;
+ * narrower when column blocking below asks for it), and a library-owned side
+ * stream brings each block's columns of op(B) (and of C when beta != 0) in
+ * while earlier blocks compute, and takes each block's columns of C back
+ * while later blocks compute.  Pinned or registered host memory is moved by
+ * copy kernels through its device address; pageable memory by
+ * cudaMemcpy2DAsync.  Only the m x n entries of C are written (rows beyond m
+ * of a column are left as they are).
  * Asynchronous on `stream` like the device forms: the host buffers must stay
- * valid and untouched until the stream reaches the end of the call.  Calls
- * share the staging buffer and must be ordered on one stream. */
+ * valid and untouched until the stream reaches the end of the call.  Calls on
+ * one device share the staging buffer, so each host-buffer call waits on the
+ * device for the previous one to finish, whatever stream it was issued on. */
 emu_status_t emu_zgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
                             const double* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
                             const double* beta, void* C, int64_t ldc, int num_moduli, void* stream);
@@ -129,6 +135,27 @@ emu_status_t emu_dgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t
 emu_status_t emu_sgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
                             const float* alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
                             const float* beta, float* C, int64_t ldc, int num_moduli, void* stream);
+
+/* Trace of host-buffer calls (for profiling the pipeline above).  While
+ * enabled, each host-buffer call records timing events at its steps, on the
+ * caller's stream (EMU_TRACE_START, EMU_TRACE_A_IN, EMU_TRACE_BLOCK_START,
+ * EMU_TRACE_BLOCK_CRT, EMU_TRACE_END) and on the side stream
+ * (EMU_TRACE_B_IN: a copy block's columns of B and C have arrived,
+ * EMU_TRACE_C_OUT: a block's columns of C are back), up to EMU_TRACE_MAX
+ * events of the latest call; enabling clears the record.
+ * emu_host_trace_read waits for those events, writes up to `cap` pairs
+ * (label, milliseconds after EMU_TRACE_START) in recording order and returns
+ * how many it wrote, or -1 on a CUDA error. */
+#define EMU_TRACE_START 0
+#define EMU_TRACE_A_IN 1
+#define EMU_TRACE_B_IN 2
+#define EMU_TRACE_BLOCK_START 3
+#define EMU_TRACE_BLOCK_CRT 4
+#define EMU_TRACE_C_OUT 5
+#define EMU_TRACE_END 6
+#define EMU_TRACE_MAX 64
+emu_status_t emu_host_trace_enable(int on);
+int emu_host_trace_read(int* labels, float* ms, int cap);
 
 /* Element-type codes of emu_workspace_bytes and emu_autotune_gemm. */
 #define EMU_DTYPE_Z 0   /* complex128 */

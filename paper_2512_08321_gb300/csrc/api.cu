@@ -205,11 +205,11 @@ int64_t choose_nblock(const DeviceState* ds, int64_t m, int64_t n, int64_t k, in
   return lo > 0 ? 128 * lo : n;            // nothing fits: one block, and the workspace check reports it
 }
 
-// b_ready (host-buffer calls): B is still arriving on another stream; A's
-// phases run first and the stream waits on the event before B is touched.
+// hooks (host-buffer calls): B and C move in column blocks on another stream;
+// A's phases run first and each block waits for its own columns.
 emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
                   const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
-                  void* C, int64_t ldc, int N, void* stream, cudaEvent_t b_ready = nullptr) {
+                  void* C, int64_t ldc, int N, void* stream, const BlockHooks* hooks = nullptr) {
   emu_status_t s = check_common(ta, tb, m, n, k, lda, ldb, ldc, N, true);
   if (s != EMU_OK) return s;
   if (m == 0 || n == 0) return EMU_OK;
@@ -230,6 +230,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   {
     std::lock_guard<std::mutex> lk(g_mu);
     nb = choose_nblock(ds, m, n, k, N, fp16, ppm, tn);
+    if (hooks && hooks->nb > 0 && hooks->nb < nb) nb = hooks->nb;
     L = layout(m, n, k, N, fp16, ppm, nb);
     s = get_workspace(ds, L.total, &ws);
   }
@@ -257,12 +258,11 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   };
   cudaError_t e;
   phase(0, st);
-  const bool a_first = (b_ready != nullptr);
+  const bool a_first = (hooks != nullptr);
   if (k == 0) {
     // empty inner dimension: the product is zero
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = cudaMemsetAsync(y, 0, static_cast<size_t>(n) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
-    if (a_first && cudaStreamWaitEvent(st, b_ready, 0) != cudaSuccess) return EMU_ERR_CUDA;
   } else if (accurate) {
     // Section III-B accurate mode: pre-scaling, 7-bit ceiling planes, bound products, exponents
     int* emA = reinterpret_cast<int*>(ws + L.off_acc);
@@ -276,10 +276,10 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
         launch_exp_max(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, st) != cudaSuccess ||
         launch_bound_split(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, L.kpad, pa, st) != cudaSuccess)
       return EMU_ERR_CUDA;
-    if (a_first && cudaStreamWaitEvent(st, b_ready, 0) != cudaSuccess) return EMU_ERR_CUDA;
     for (int64_t j0 = 0; j0 < n; j0 += nb) {
       const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
       const void* Bj = block_ptr(j0);
+      if (hooks && (s = hooks->wait_inputs(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
       if (launch_exp_max(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, st) != cudaSuccess ||
           launch_bound_split(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, L.kpad, pb, st) !=
               cudaSuccess)
@@ -294,19 +294,17 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   } else {
     if ((e = launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, st, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
-    if (a_first) {
-      // A's planes while B is in flight
-      if ((e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, st, tn.split_elems,
-                            dt.real)) != cudaSuccess ||
-          cudaStreamWaitEvent(st, b_ready, 0) != cudaSuccess)
-        return EMU_ERR_CUDA;
-    }
+    // A's planes while B is in flight
+    if (a_first && (e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, st,
+                                     tn.split_elems, dt.real)) != cudaSuccess)
+      return EMU_ERR_CUDA;
   }
   for (int64_t j0 = 0; j0 < n; j0 += nb) {
     const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
     const void* Bj = block_ptr(j0);
     void* Cj = static_cast<char*>(C) + static_cast<size_t>(j0) * ldc * in_esz;
     int16_t* yj = y + j0;
+    if (hooks && (s = hooks->wait_inputs(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
     if (k == 0) {
       if ((e = cudaMemsetAsync(res, 0, static_cast<size_t>(ppm * N) * nj * L.ldr, st)) != cudaSuccess)
         return EMU_ERR_CUDA;
@@ -332,6 +330,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
                         : launch_crt(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st,
                                      tn.crt_rows, dt.real, accurate));
     if (s != EMU_OK) return s;
+    if (hooks && (s = hooks->output_done(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
   }
   phase(4, st);
   return EMU_OK;
@@ -341,8 +340,8 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
 
 emu_status_t run_gemm(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar,
                       double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi, void* C,
-                      int64_t ldc, int N, void* stream, cudaEvent_t b_ready) {
-  return gemm(Dt{single, real}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream, b_ready);
+                      int64_t ldc, int N, void* stream, const BlockHooks* hooks) {
+  return gemm(Dt{single != 0, real != 0}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N, stream, hooks);
 }
 
 emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,

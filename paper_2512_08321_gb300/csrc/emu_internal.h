@@ -197,10 +197,23 @@ cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, 
                             float* feat, void* scratch, cudaStream_t st);
 extern int g_f16_group;
 
+// Column-block hooks of a host-buffer call (host.cu).  The output columns are
+// processed in blocks of at most `nb` (0: the library's choice); before a block's
+// columns of B (and of C, when beta != 0) are touched the caller's stream is
+// made to wait for them (`wait_inputs`), and once the block's CRT is enqueued
+// `output_done` takes its columns of C from there.  With hooks, A's exponents
+// and planes are formed before the first wait.
+struct BlockHooks {
+  int64_t nb;
+  void* ctx;
+  emu_status_t (*wait_inputs)(void* ctx, int64_t j0, int64_t nj, cudaStream_t st);
+  emu_status_t (*output_done)(void* ctx, int64_t j0, int64_t nj, cudaStream_t st);
+};
+
 // GEMM entry shared by the device- and host-buffer calls (api.cu).
 emu_status_t run_gemm(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar,
                       double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi, void* C,
-                      int64_t ldc, int N, void* stream, cudaEvent_t b_ready = nullptr);
+                      int64_t ldc, int N, void* stream, const BlockHooks* hooks = nullptr);
 emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
                              int64_t ldc, int N);
 emu_status_t set_bad_param(int idx);

@@ -122,6 +122,8 @@ _SIGS = [
     ("emu_selftest_bounded_wait", _c_int, [_c_i64, _c_ptr]),
     ("emu_set_phase_events", _c_int, [ctypes.POINTER(_c_ptr), _c_int]),
     ("emu_kernel_launches", ctypes.c_uint64, []),
+    ("emu_host_trace_enable", _c_int, [_c_int]),
+    ("emu_host_trace_read", _c_int, [ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float), _c_int]),
     ("emu_version", ctypes.c_char_p, []),
 ]
 
@@ -488,6 +490,26 @@ def emu_set_phase_events(events):
 
 def emu_kernel_launches():
     return lib().emu_kernel_launches()
+
+
+(EMU_TRACE_START, EMU_TRACE_A_IN, EMU_TRACE_B_IN, EMU_TRACE_BLOCK_START, EMU_TRACE_BLOCK_CRT, EMU_TRACE_C_OUT,
+ EMU_TRACE_END) = range(7)
+EMU_TRACE_MAX = 64
+TRACE_NAMES = ["start", "a_in", "b_in", "block_start", "block_crt", "c_out", "end"]
+
+
+def emu_host_trace_enable(on):
+    return lib().emu_host_trace_enable(int(bool(on)))
+
+
+def emu_host_trace_read():
+    """[(label name, ms after the call's start)] of the latest traced host-buffer call."""
+    labels = (_c_int * EMU_TRACE_MAX)()
+    ms = (ctypes.c_float * EMU_TRACE_MAX)()
+    cnt = lib().emu_host_trace_read(labels, ms, EMU_TRACE_MAX)
+    if cnt < 0:
+        raise EmuError(EMU_ERR_CUDA, "emu_host_trace_read")
+    return [(TRACE_NAMES[labels[i]], float(ms[i])) for i in range(cnt)]
 
 
 def emu_version():

@@ -109,3 +109,85 @@ def test_host_buffers_accurate_mode_and_blocking(kind):
         emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 0)
     got = tC.numpy().T
     assert same_bits(np.ascontiguousarray(got), np.ascontiguousarray(ref)), mismatch_report(got, ref)
+
+
+def _stored(X, ld, pinned, fill=0):
+    """X (rows x cols) stored column-major with leading dimension ld in host
+    memory: a pinned tensor of shape (cols, ld) or a Fortran numpy array."""
+    rows, cols = X.shape
+    buf = np.full((cols, ld), fill, dtype=X.dtype)
+    buf[:, :rows] = X.T
+    if pinned:
+        t = torch.from_numpy(buf).pin_memory()
+        return t, t.data_ptr(), (lambda: t.numpy().T)
+    f = np.asfortranarray(buf.T)
+    return f, f.ctypes.data, (lambda: f)
+
+
+@pytest.mark.parametrize("kind,opB,pinned,nblock", [("c", "C", True, 0), ("z", "N", False, 0),
+                                                     ("d", "T", True, 768), ("s", "N", True, 384)])
+def test_host_column_blocks(kind, opB, pinned, nblock):
+    # n above 2048: B and C travel in column blocks on the side stream while
+    # earlier blocks compute; padded leading dimensions make the copies strided
+    m, n, k, N = 40, 3 * 1024 + 77, 64, 8
+    A, B, C = _mats(kind, m, n, k, "N", opB, 330)
+    alpha, beta = 1.25, -0.5
+    try:
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, nblock), "nblock")
+        ref = _device_ref(kind, A, B, C, m, n, k, "N", opB, alpha, beta, N)
+        lda, ldb, ldc = m + 1, B.shape[0] + 5, m + 3
+        hA, pa, _ = _stored(A, lda, pinned)
+        hB, pb, _ = _stored(B, ldb, pinned)
+        hC, pc, view = _stored(C, ldc, pinned, fill=7)
+        f = KINDS[kind][2]
+        emu.check(f("N", opB, m, n, k, _scal(kind, alpha), pa, lda, pb, ldb, _scal(kind, beta), pc, ldc, N),
+                  "host call")
+        torch.cuda.synchronize()
+    finally:
+        emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 0)
+    got = view()
+    assert same_bits(np.ascontiguousarray(got[:m]), np.ascontiguousarray(ref)), mismatch_report(got[:m], ref)
+    assert np.all(got[m:] == 7)                             # padding rows untouched
+
+
+def test_host_calls_on_two_streams():
+    # two host-buffer calls issued back to back on different streams share the
+    # staging buffers: the second waits for the first
+    m, n, k, N = 64, 2600, 48, 10
+    probs = [_mats("z", m, n, k, "N", "N", 340 + 10 * t) for t in range(2)]
+    refs = [_device_ref("z", A, B, C, m, n, k, "N", "N", 1.0, 0.0, N) for A, B, C in probs]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for (A, B, _), s in zip(probs, streams):
+        hA, pa, _ = _stored(A, m, True)
+        hB, pb, _ = _stored(B, k, True)
+        hC, pc, view = _stored(np.zeros((m, n), np.complex128), m, True)
+        outs.append((hA, hB, hC, view))
+        emu.check(emu.emu_zgemm_host("N", "N", m, n, k, 1.0, pa, m, pb, k, 0.0, pc, m, N, stream=s), "host call")
+    torch.cuda.synchronize()
+    for (_, _, _, view), ref in zip(outs, refs):
+        assert same_bits(np.ascontiguousarray(view()), np.ascontiguousarray(ref))
+
+
+def test_host_trace_records_the_pipeline():
+    m, n, k, N = 48, 3 * 1024 + 77, 32, 6            # four column blocks
+    A, B, _ = _mats("z", m, n, k, "N", "N", 350)
+    hA, pa, _ = _stored(A, m, True)
+    hB, pb, _ = _stored(B, k, True)
+    hC, pc, _ = _stored(np.zeros((m, n), np.complex128), m, True)
+    emu.check(emu.emu_host_trace_enable(1), "trace on")
+    try:
+        emu.check(emu.emu_zgemm_host("N", "N", m, n, k, 1.0, pa, m, pb, k, 0.0, pc, m, N), "host call")
+        torch.cuda.synchronize()
+        tr = emu.emu_host_trace_read()
+    finally:
+        emu.emu_host_trace_enable(0)
+    names = [t[0] for t in tr]
+    assert names == ["start", "a_in"] + ["b_in"] * 4 + ["block_start", "block_crt", "c_out"] * 4 + ["end"]
+    ms = [t[1] for t in tr]
+    assert ms[0] == 0.0 and min(ms) >= 0.0
+    assert ms[-1] >= max(ms[:-1])                            # the call ends after every step
+    for b in range(4):
+        s, c, o = ms[6 + 3 * b: 9 + 3 * b]
+        assert s <= c <= o                                   # block start, its CRT, its copy back
+        assert s >= ms[2 + b]                                # after its columns of B arrived
