@@ -109,20 +109,25 @@ emu_status_t emu_sgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
 
 /* Host-buffer forms of the four GEMMs: A, B and C are in host memory (same
  * arguments, layouts and results as the device forms; alpha/beta as there).
- * The operands go through a library-owned device staging buffer.  A is
- * copied first; the output columns are then processed in blocks (about eight
- * blocks of a multiple of 256 columns, at least 1024; one block when n <= 2048;
- * narrower when column blocking below asks for it), and a library-owned side
- * stream brings each block's columns of op(B) (and of C when beta != 0) in
- * while earlier blocks compute, and takes each block's columns of C back
- * while later blocks compute.  Pinned or registered host memory is moved by
- * copy kernels through its device address; pageable memory by
- * cudaMemcpy2DAsync.  Only the m x n entries of C are written (rows beyond m
- * of a column are left as they are).
- * Asynchronous on `stream` like the device forms: the host buffers must stay
- * valid and untouched until the stream reaches the end of the call.  Calls on
- * one device share the staging buffer, so each host-buffer call waits on the
- * device for the previous one to finish, whatever stream it was issued on. */
+ * The inputs go through a library-owned device staging buffer in blocks: the
+ * output columns in blocks, and the rows of op(A) in blocks (each about an
+ * eighth, a multiple of 256 and at least 1024; one block when the dimension is
+ * at most 2048; narrower column blocks when column blocking below asks for
+ * them).  A library-owned side stream brings op(B)'s (and, for pageable C with
+ * beta != 0, C's) first column block, then op(A) block of rows by block of
+ * rows, then the other column blocks -- contiguous blocks by the DMA engines,
+ * strided ones from pinned memory by a copy kernel -- while the caller's
+ * stream computes the first column block one block of rows at a time (fast
+ * scaling, tcgen05 engine; otherwise after all of A) and the other column
+ * blocks as their columns arrive.  Pinned or registered C is read (beta != 0)
+ * and written in place by the CRT kernel through its device address; pageable
+ * C goes through a device copy and comes back after the last block.  Only the
+ * m x n entries of C are written (rows beyond m of a column are left as they
+ * are).  Asynchronous on `stream` like the device forms: the host buffers must
+ * stay valid and untouched until the stream reaches the end of the call.
+ * Calls on one device share the staging buffer, so each host-buffer call waits
+ * on the device for the previous one to finish, whatever stream it was issued
+ * on. */
 emu_status_t emu_zgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, int64_t k,
                             const double* alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
                             const double* beta, void* C, int64_t ldc, int num_moduli, void* stream);
@@ -138,10 +143,12 @@ emu_status_t emu_sgemm_host(emu_op_t transa, emu_op_t transb, int64_t m, int64_t
 
 /* Trace of host-buffer calls (for profiling the pipeline above).  While
  * enabled, each host-buffer call records timing events at its steps, on the
- * caller's stream (EMU_TRACE_START, EMU_TRACE_A_IN, EMU_TRACE_BLOCK_START,
- * EMU_TRACE_BLOCK_CRT, EMU_TRACE_END) and on the side stream
- * (EMU_TRACE_B_IN: a copy block's columns of B and C have arrived,
- * EMU_TRACE_C_OUT: a block's columns of C are back), up to EMU_TRACE_MAX
+ * caller's stream (EMU_TRACE_START; EMU_TRACE_BLOCK_START: a column block's
+ * inputs are in and its computation starts; EMU_TRACE_BLOCK_CRT: its CRT is
+ * done; EMU_TRACE_END) and on the side stream (EMU_TRACE_A_IN: a block of rows
+ * of op(A) has arrived; EMU_TRACE_B_IN: a column block's columns of B and C
+ * have arrived; EMU_TRACE_C_OUT: pageable C is back), up to
+ * EMU_TRACE_MAX
  * events of the latest call; enabling clears the record.
  * emu_host_trace_read waits for those events, writes up to `cap` pairs
  * (label, milliseconds after EMU_TRACE_START) in recording order and returns

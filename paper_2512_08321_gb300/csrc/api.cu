@@ -155,14 +155,19 @@ emu_status_t check_common(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_
 emu_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? EMU_OK : EMU_ERR_CUDA; }
 
 
+// a_plane_rows / rcap (tcgen05 engine only): pa is a block of rows of planes
+// a_plane_rows rows tall, and residues are stored for rows below rcap.
 emu_status_t run_residue_gemm(emu_engine_t eng, int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                               const void* pa, const void* pb, int8_t* res, int64_t ldr,
-                              DeviceState* ds, cudaStream_t st, const Tune& t, int ppm) {
-  if (eng == EMU_ENGINE_I8)
+                              DeviceState* ds, cudaStream_t st, const Tune& t, int ppm, int64_t a_plane_rows = 0,
+                              int64_t rcap = 0) {
+  if (eng == EMU_ENGINE_I8) {
+    if (a_plane_rows || rcap) return EMU_ERR_UNSUPPORTED;
     return cuda_status(launch_gemm_i8(m, n, kpad, pl, static_cast<const int8_t*>(pa),
                                       static_cast<const int8_t*>(pb), res, ldr, st, ppm));
-  const cudaError_t e =
-      launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, t.chunk_k, ds->status, st, t.tile_n, t.group, ppm);
+  }
+  const cudaError_t e = launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, t.chunk_k, ds->status, st, t.tile_n,
+                                        t.group, ppm, a_plane_rows, rcap);
   if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
   return cuda_status(e);
 }
@@ -205,8 +210,8 @@ int64_t choose_nblock(const DeviceState* ds, int64_t m, int64_t n, int64_t k, in
   return lo > 0 ? 128 * lo : n;            // nothing fits: one block, and the workspace check reports it
 }
 
-// hooks (host-buffer calls): B and C move in column blocks on another stream;
-// A's phases run first and each block waits for its own columns.
+// hooks (host-buffer calls): the operands move in blocks on another stream and
+// each step waits for the blocks it reads (BlockHooks).
 emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
                   const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
                   void* C, int64_t ldc, int N, void* stream, const BlockHooks* hooks = nullptr) {
@@ -256,9 +261,19 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     return k > 0 ? static_cast<const void*>(static_cast<const char*>(B) + static_cast<size_t>(j0) * rsb * in_esz)
                  : B;
   };
+  auto crt = [&](int64_t mi, int64_t nj, const int8_t* r, const int16_t* xi, const int16_t* yj, void* Ci) {
+    return cuda_status(g_crt_mode == 1
+                           ? launch_crt_fp(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, st,
+                                           dt.real)
+                           : launch_crt(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, st,
+                                        tn.crt_rows, dt.real, accurate));
+  };
   cudaError_t e;
   phase(0, st);
-  const bool a_first = (hooks != nullptr);
+  // rows_piped: the first column block row block by row block as A arrives
+  const bool rows_piped = hooks && hooks->mb > 0 && hooks->mb % 16 == 0 && k > 0 && !accurate && fp16;
+  if (hooks && !rows_piped && (s = hooks->wait_rows(hooks->ctx, 0, m, st)) != EMU_OK) return s;
+  const bool a_first = hooks && !rows_piped;
   if (k == 0) {
     // empty inner dimension: the product is zero
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
@@ -291,7 +306,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     if (launch_accu_finalize(m, emA, fA, MA, *pl, x, st) != cudaSuccess ||
         launch_accu_finalize(n, emB, fB, NB, *pl, y, st) != cudaSuccess)
       return EMU_ERR_CUDA;
-  } else {
+  } else if (!rows_piped) {
     if ((e = launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, st, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
     // A's planes while B is in flight
@@ -313,6 +328,31 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
           (e = launch_exponents(dt.single, Bj, nj, k, rsb, hsb, *pl, yj, scr, st, dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
       phase(1, st);
+      if (rows_piped && j0 == 0) {
+        // B's planes, then per block of rows of op(A): exponents, planes, residue products, CRT
+        if (launch_split(dt.single, conj_b, Bj, nj, k, rsb, hsb, pls, yj, fp16, L.kpad, pb, st, tn.split_elems,
+                         dt.real) != cudaSuccess)
+          return EMU_ERR_CUDA;
+        for (int64_t i0 = 0; i0 < m; i0 += hooks->mb) {
+          const int64_t mi = (m - i0) < hooks->mb ? (m - i0) : hooks->mb;
+          const void* Ai = static_cast<const char*>(A) + static_cast<size_t>(i0) * rsa * in_esz;
+          void* pai = static_cast<char*>(pa) + static_cast<size_t>(i0) * L.kpad * 2;
+          if ((s = hooks->wait_rows(hooks->ctx, i0, mi, st)) != EMU_OK) return s;
+          if (launch_exponents(dt.single, Ai, mi, k, rsa, hsa, *pl, x + i0, scr, st, dt.real) != cudaSuccess ||
+              launch_split(dt.single, conj_a, Ai, mi, k, rsa, hsa, pls, x + i0, fp16, L.kpad, pai, st,
+                           tn.split_elems, dt.real, m) != cudaSuccess)
+            return EMU_ERR_CUDA;
+          const int64_t rcap = (L.ldr - i0) < round_up(mi, 16) ? (L.ldr - i0) : round_up(mi, 16);
+          if ((s = hooks->products_start(hooks->ctx, st)) != EMU_OK ||
+              (s = run_residue_gemm(eng, mi, nj, L.kpad, *pl, pai, pb, res + i0, L.ldr, ds, st, tn, ppm, m, rcap)) !=
+                  EMU_OK ||
+              (s = crt(mi, nj, res + i0, x + i0, yj, static_cast<char*>(Cj) + static_cast<size_t>(i0) * in_esz)) !=
+                  EMU_OK)
+            return s;
+        }
+        if ((s = hooks->output_done(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
+        continue;
+      }
       if (j0 == 0 && !(a_first && !accurate) &&
           (e = launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, st, tn.split_elems,
                             dt.real)) != cudaSuccess)
@@ -321,15 +361,12 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
                             dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
       phase(2, st);
+      if (hooks && (s = hooks->products_start(hooks->ctx, st)) != EMU_OK) return s;
       s = run_residue_gemm(eng, m, nj, L.kpad, *pl, pa, pb, res, L.ldr, ds, st, tn, ppm);
       if (s != EMU_OK) return s;
       phase(3, st);
     }
-    s = cuda_status(g_crt_mode == 1
-                        ? launch_crt_fp(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st, dt.real)
-                        : launch_crt(dt.single, m, nj, *pl, res, L.ldr, x, yj, ar, ai, br, bi, Cj, ldc, st,
-                                     tn.crt_rows, dt.real, accurate));
-    if (s != EMU_OK) return s;
+    if ((s = crt(m, nj, res, x, yj, Cj)) != EMU_OK) return s;
     if (hooks && (s = hooks->output_done(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
   }
   phase(4, st);

@@ -105,7 +105,7 @@ void set_default_tuning(int key, int value);
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp,
                          bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems = 4,
-                         bool real = false);
+                         bool real = false, int64_t plane_rows = 0);
 
 cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                            const int8_t* planesA, const int8_t* planesB, int8_t* res,
@@ -114,7 +114,8 @@ cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                             const void* planesA, const void* planesB, int8_t* res,
                             int64_t ldr, int chunk_k, unsigned int* status, cudaStream_t st,
-                            int tile_n = 256, int group = 16, int ppm = 3);
+                            int tile_n = 256, int group = 16, int ppm = 3, int64_t a_plane_rows = 0,
+                            int64_t rcap = 0);
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        const int8_t* res, int64_t ldr, const int16_t* x, const int16_t* y,
@@ -197,17 +198,24 @@ cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, 
                             float* feat, void* scratch, cudaStream_t st);
 extern int g_f16_group;
 
-// Column-block hooks of a host-buffer call (host.cu).  The output columns are
-// processed in blocks of at most `nb` (0: the library's choice); before a block's
-// columns of B (and of C, when beta != 0) are touched the caller's stream is
-// made to wait for them (`wait_inputs`), and once the block's CRT is enqueued
-// `output_done` takes its columns of C from there.  With hooks, A's exponents
-// and planes are formed before the first wait.
+// Block hooks of a host-buffer call (host.cu).  The output columns are
+// processed in blocks of at most `nb` (0: the library's choice); before a
+// block's columns of B (and of C, when beta != 0) are touched the caller's
+// stream is made to wait for them (`wait_inputs`); once the block's CRT is
+// enqueued `output_done` is told its columns of C are final, and
+// `products_start` is called just before each launch of residue products (so
+// that copies can be placed beside those).  A arrives in blocks of `mb` rows
+// (a multiple of 16; 0: all of A before the call): `wait_rows` makes the
+// stream wait for rows i0.. of op(A).  In fast mode on the tcgen05 engine the
+// first column block is computed one block of rows at a time as A arrives;
+// otherwise all of A is waited for first.
 struct BlockHooks {
-  int64_t nb;
+  int64_t nb, mb;
   void* ctx;
   emu_status_t (*wait_inputs)(void* ctx, int64_t j0, int64_t nj, cudaStream_t st);
+  emu_status_t (*wait_rows)(void* ctx, int64_t i0, int64_t mi, cudaStream_t st);
   emu_status_t (*output_done)(void* ctx, int64_t j0, int64_t nj, cudaStream_t st);
+  emu_status_t (*products_start)(void* ctx, cudaStream_t st);
 };
 
 // GEMM entry shared by the device- and host-buffer calls (api.cu).

@@ -1,16 +1,17 @@
 // Host-buffer GEMMs: A, B and C live in host memory.
 //
-// On GB300 the GPU reaches host memory over the chip-to-chip link.  The
-// operands go through a device staging buffer, and the output columns are
-// processed in blocks (the column blocking of Section III-A): a side stream
-// brings block b's columns of B (and of C when beta != 0) in while earlier
-// blocks compute, and takes block b's columns of C back while later blocks
-// compute, so only A's copy, the first block's inputs and the last block's
-// output are not hidden behind the residue products.  Copies that overlap
-// computation use the DMA engines; A's copy and the last block of C, which
-// nothing overlaps, use a copy kernel through the device address of pinned
-// memory, which is faster on the link (211 GB/s in, 194 GB/s out).  Pageable
-// memory always goes through cudaMemcpy2DAsync.
+// On GB300 the GPU reaches host memory over the chip-to-chip link.  The inputs
+// go through a device staging buffer in blocks (the column blocking of Section
+// III-A, and blocks of rows of op(A)), moved on a side stream in the order the
+// computation needs them: the first column block of B, A block of rows by block
+// of rows, then the other column blocks of B.  The first column block of C is
+// computed one block of rows at a time as A arrives, the others as their
+// columns of B arrive, so the residue products start after one block of A and
+// one of B instead of after all of A.  Contiguous inputs move by the DMA
+// engines, strided ones by a copy kernel through the device address of pinned
+// memory; the CRT writes pinned C in place (see the shapes below for why).
+// Pageable memory always goes through cudaMemcpy2DAsync, and pageable C goes
+// back in one piece at the end.
 #include <algorithm>
 #include <mutex>
 
@@ -41,18 +42,25 @@ __global__ void __launch_bounds__(T, 2048 / T)
   }
 }
 
-// Copy kernels run only where nothing else is on the GPU (A's copy, the last
-// block of C): two blocks of 256 threads per SM, about 5 MB of loads in flight.
-// Copies that overlap computation go to the DMA engines instead: beside the
-// split and the residue products, copy kernels' stores to host memory slowed
-// those kernels (a column block took about 2 ms longer).
-enum class Shape { kKernel, kDma };
+// How a copy moves.  kDma: the DMA engines, which leave the SMs alone;
+// measured here, they kept the link's 211 GB/s for contiguous host-to-device
+// copies, but beside the residue products a copy of k segments of 32 KB (a
+// block of rows of a column-major A) ran at 12-100 GB/s and device-to-host
+// copies at 12-190 GB/s.  kNarrow: a copy kernel of one block of 128 threads
+// per SM (1.25 MB of loads in flight, 4096 registers, which three resident
+// split blocks of 256 threads x 80 registers leave free), for strided inputs:
+// it keeps 211 GB/s, at the price of slowing the kernels beside it by about
+// 40 % of its own duration.  C is not copied back beside the computation at
+// all: stores to host memory from SMs held up the residue products beside
+// them (a column block took 37.5 ms instead of 31), so the CRT writes pinned
+// C in place, link-bound (2.8 ms per 2048 columns instead of 1.4).
+enum class Shape { kNarrow, kDma };
 
 template <typename W>
 cudaError_t copy_words(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows,
                        cudaStream_t st) {
-  constexpr int kT = 256;
-  constexpr size_t kCap = 152 * 2;
+  constexpr int kT = 128;
+  constexpr size_t kCap = 152;
   const size_t w = width / sizeof(W);
   const size_t gx = std::min<size_t>((w + 4 * kT - 1) / (4 * kT), kCap);
   const size_t gy = std::min<size_t>(std::min<size_t>(rows, std::max<size_t>(kCap / gx, 1)), 65535);
@@ -127,11 +135,11 @@ cudaError_t transfer(bool to_host, void* dev, size_t dpitch, const void* host, c
 
 constexpr int kMaxHostBlocks = 8;
 
-// Output columns per block of a host-buffer call: about eight blocks of a
-// multiple of 256 columns (the residue GEMM's tile width), at least 1024.
-int64_t host_block_cols(int64_t n) {
-  if (n <= 2048) return n;
-  int64_t cb = round_up((n + kMaxHostBlocks - 1) / kMaxHostBlocks, 256);
+// Columns of C (rows of op(A)) per block of a host-buffer call: about eight
+// blocks of a multiple of 256 (the residue GEMM's tile width), at least 1024.
+int64_t host_block(int64_t len) {
+  if (len <= 2048) return len;
+  int64_t cb = round_up((len + kMaxHostBlocks - 1) / kMaxHostBlocks, 256);
   return cb < 1024 ? 1024 : cb;
 }
 
@@ -142,7 +150,8 @@ struct Side {
   std::mutex mu;
   cudaStream_t s = nullptr;
   cudaEvent_t start = nullptr, done = nullptr, out = nullptr, last = nullptr;
-  cudaEvent_t in[kMaxHostBlocks] = {};
+  cudaEvent_t in[kMaxHostBlocks] = {};    // columns of B (and C) of a column block
+  cudaEvent_t in_a[kMaxHostBlocks] = {};  // rows of op(A) of a row block
   bool used = false;
 };
 std::mutex g_side_mu;
@@ -161,6 +170,8 @@ cudaError_t side_for_device(Side** out) {
     for (cudaEvent_t* ev : evs)
       if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return e;
     for (cudaEvent_t& ev : sd.in)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    for (cudaEvent_t& ev : sd.in_a)
       if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
   }
   *out = &sd;
@@ -203,7 +214,7 @@ void trace_reset() {
 struct HostCall {
   Side* sd;
   int64_t n;
-  int64_t cb;                 // columns per copy block
+  int64_t cb, mb;             // columns per column block, rows per row block
   char* dC;                   // device copy of C (leading dimension ldc)
   void* C;                    // caller's C
   const void* Cv;             // its device view, or nullptr (pageable)
@@ -218,25 +229,22 @@ emu_status_t wait_inputs(void* ctx, int64_t j0, int64_t nj, cudaStream_t st) {
   return EMU_OK;
 }
 
-// Columns j0.. of C go back on the side stream once the block's CRT is done.
-// Pinned C: by the DMA engines, which leave the SMs to the next block's split
-// and residue products, except the last block, which nothing else overlaps:
-// the copy kernel, the faster of the two on the link.  Pageable C: nothing here (a copy
-// into pageable memory would hold the calling thread until it is done); all
-// of C goes back after the last block.
-emu_status_t output_done(void* ctx, int64_t j0, int64_t nj, cudaStream_t st) {
+emu_status_t wait_rows(void* ctx, int64_t i0, int64_t mi, cudaStream_t st) {
   const HostCall* hc = static_cast<const HostCall*>(ctx);
-  trace(EMU_TRACE_BLOCK_CRT, st);
-  if (!hc->Cv) return EMU_OK;
-  const size_t off = static_cast<size_t>(j0) * hc->pitch;
-  if (cudaEventRecord(hc->sd->out, st) != cudaSuccess || cudaStreamWaitEvent(hc->sd->s, hc->sd->out, 0) != cudaSuccess ||
-      transfer(true, hc->dC + off, hc->pitch, static_cast<char*>(hc->C) + off, static_cast<const char*>(hc->Cv) + off,
-               hc->pitch, hc->width, static_cast<size_t>(nj), j0 + nj == hc->n ? Shape::kKernel : Shape::kDma,
-               hc->sd->s) != cudaSuccess)
-    return EMU_ERR_CUDA;
-  trace(EMU_TRACE_C_OUT, hc->sd->s);
+  for (int64_t r = i0 / hc->mb; r <= (i0 + mi - 1) / hc->mb; ++r)
+    if (cudaStreamWaitEvent(st, hc->sd->in_a[r], 0) != cudaSuccess) return EMU_ERR_CUDA;
   return EMU_OK;
 }
+
+// A column block of C is final once its CRT is done.  Pinned C: the CRT wrote it
+// straight into host memory.  Pageable C: it goes back in one piece after the
+// last block (a copy into pageable memory holds the calling thread).
+emu_status_t output_done(void* /*ctx*/, int64_t /*j0*/, int64_t /*nj*/, cudaStream_t st) {
+  trace(EMU_TRACE_BLOCK_CRT, st);
+  return EMU_OK;
+}
+
+emu_status_t products_start(void* /*ctx*/, cudaStream_t /*st*/) { return EMU_OK; }
 
 emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k,
                        double ar, double ai, const void* A, int64_t lda, const void* B, int64_t ldb, double br,
@@ -257,50 +265,66 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
   if (side_for_device(&sd) != cudaSuccess) return EMU_ERR_CUDA;
   std::lock_guard<std::mutex> lk(sd->mu);
   char* stg = nullptr;
-  s = get_staging(al(bA) + al(bB) + al(bC), &stg);
+  const void* Cv = device_view(C);
+  s = get_staging(al(bA) + al(bB) + (Cv ? 0 : al(bC)), &stg);   // pinned C is written in place
   if (s != EMU_OK) return s;
   char* dA = stg;
   char* dB = stg + al(bA);
   char* dC = dB + al(bB);
-  HostCall hc{sd, n, host_block_cols(n), dC, C, device_view(C), static_cast<size_t>(ldc) * esz,
+  HostCall hc{sd, n, host_block(n), host_block(m), dC, C, Cv, static_cast<size_t>(ldc) * esz,
               static_cast<size_t>(m) * esz};
-  const int64_t nblk = (n + hc.cb - 1) / hc.cb;
+  const int64_t nblk = (n + hc.cb - 1) / hc.cb, mblk = (m + hc.mb - 1) / hc.mb;
+  const size_t lda_b = static_cast<size_t>(lda) * esz, ldb_b = static_cast<size_t>(ldb) * esz;
   const void* Av = device_view(A);
-  const size_t ldb_b = static_cast<size_t>(ldb) * esz;
-  // A first, on the caller's stream, once the previous host-buffer call is done
+  const void* Bv = device_view(B);
+  // once the previous host-buffer call is done, the inputs move on the side
+  // stream in the order the caller's stream needs them; contiguous copies by
+  // the DMA engines, strided ones (from pinned memory) by the narrow copy kernel
   trace_reset();
   if (sd->used && cudaStreamWaitEvent(st, sd->last, 0) != cudaSuccess) return EMU_ERR_CUDA;
   trace(EMU_TRACE_START, st);
-  if (transfer(false, dA, bA, A, Av, bA, bA, 1, Shape::kKernel, st) != cudaSuccess ||
-      cudaEventRecord(sd->start, st) != cudaSuccess || cudaStreamWaitEvent(sd->s, sd->start, 0) != cudaSuccess)
+  if (cudaEventRecord(sd->start, st) != cudaSuccess || cudaStreamWaitEvent(sd->s, sd->start, 0) != cudaSuccess)
     return EMU_ERR_CUDA;
-  trace(EMU_TRACE_A_IN, st);
   sd->used = true;
-  // then each block's columns of B (and of C) on the side stream, by the DMA
-  // engines while A's exponents and planes and the earlier blocks compute
-  emu_status_t res = EMU_OK;
-  for (int64_t c = 0; c < nblk && res == EMU_OK; ++c) {
+  auto bring = [&](char* dst, const void* src, const void* view, size_t off, size_t pitch, size_t width,
+                   size_t rows) -> cudaError_t {
+    const bool contiguous = rows == 1 || pitch == width;
+    return transfer(false, dst + off, pitch, static_cast<const char*>(src) + off,
+                    view ? static_cast<const char*>(view) + off : nullptr, pitch, width, rows,
+                    contiguous || !view ? Shape::kDma : Shape::kNarrow, sd->s);
+  };
+  auto bring_cols = [&](int64_t c) -> cudaError_t {   // columns c0.. of op(B) (and of C)
     const int64_t c0 = c * hc.cb, cn = std::min(hc.cb, n - c0);
     cudaError_t e = cudaSuccess;
-    if (bB) {
-      // columns c0.. of the stored k x n matrix, or rows c0.. of the stored n x k matrix
-      const size_t off = tb == EMU_OP_N ? c0 * ldb_b : c0 * esz;
-      e = transfer(false, dB + off, ldb_b, static_cast<const char*>(B) + off, nullptr, ldb_b,
-                   tb == EMU_OP_N ? static_cast<size_t>(k) * esz : static_cast<size_t>(cn) * esz,
-                   tb == EMU_OP_N ? static_cast<size_t>(cn) : static_cast<size_t>(k), Shape::kDma, sd->s);
-    }
-    if (e == cudaSuccess && use_beta) {
-      const size_t off = static_cast<size_t>(c0) * hc.pitch;
-      e = transfer(false, dC + off, hc.pitch, static_cast<const char*>(C) + off, nullptr, hc.pitch, hc.width,
-                   static_cast<size_t>(cn), Shape::kDma, sd->s);
-    }
+    if (bB)   // columns c0.. of the stored k x n matrix, or rows c0.. of the stored n x k matrix
+      e = tb == EMU_OP_N ? bring(dB, B, Bv, c0 * ldb_b, ldb_b, static_cast<size_t>(k) * esz, static_cast<size_t>(cn))
+                         : bring(dB, B, Bv, c0 * esz, ldb_b, static_cast<size_t>(cn) * esz, static_cast<size_t>(k));
+    if (e == cudaSuccess && use_beta && !Cv)   // pageable C: its columns into the device copy
+      e = bring(dC, C, nullptr, static_cast<size_t>(c0) * hc.pitch, hc.pitch, hc.width, static_cast<size_t>(cn));
     if (e == cudaSuccess) e = cudaEventRecord(sd->in[c], sd->s);
-    if (e != cudaSuccess) res = EMU_ERR_CUDA;
     trace(EMU_TRACE_B_IN, sd->s);
-  }
+    return e;
+  };
+  auto bring_rows = [&](int64_t r) -> cudaError_t {   // rows r0.. of op(A)
+    const int64_t r0 = r * hc.mb, rn = std::min(hc.mb, m - r0);
+    cudaError_t e = cudaSuccess;
+    if (bA)   // rows r0.. of the stored m x k matrix, or columns r0.. of the stored k x m matrix
+      e = ta == EMU_OP_N ? bring(dA, A, Av, r0 * esz, lda_b, static_cast<size_t>(rn) * esz, static_cast<size_t>(k))
+                         : bring(dA, A, Av, r0 * lda_b, lda_b, static_cast<size_t>(k) * esz, static_cast<size_t>(rn));
+    if (e == cudaSuccess) e = cudaEventRecord(sd->in_a[r], sd->s);
+    trace(EMU_TRACE_A_IN, sd->s);
+    return e;
+  };
+  emu_status_t res = EMU_OK;
+  if (bring_cols(0) != cudaSuccess) res = EMU_ERR_CUDA;
+  for (int64_t r = 0; r < mblk && res == EMU_OK; ++r)
+    if (bring_rows(r) != cudaSuccess) res = EMU_ERR_CUDA;
+  for (int64_t c = 1; c < nblk && res == EMU_OK; ++c)
+    if (bring_cols(c) != cudaSuccess) res = EMU_ERR_CUDA;
   if (res == EMU_OK) {
-    const BlockHooks hooks{hc.cb, &hc, wait_inputs, output_done};
-    res = run_gemm(single, real, ta, tb, m, n, k, ar, ai, bA ? dA : nullptr, lda, bB ? dB : nullptr, ldb, br, bi, dC,
+    const BlockHooks hooks{hc.cb, hc.mb, &hc, wait_inputs, wait_rows, output_done, products_start};
+    res = run_gemm(single, real, ta, tb, m, n, k, ar, ai, bA ? dA : nullptr, lda, bB ? dB : nullptr, ldb, br, bi,
+                   Cv ? const_cast<void*>(Cv) : static_cast<void*>(dC),
                    ldc, N, stream, &hooks);
   }
   if (res == EMU_OK && !hc.Cv) {   // pageable C: all of it once the last block is done

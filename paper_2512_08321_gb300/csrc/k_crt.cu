@@ -215,7 +215,8 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
   const int64_t job_stride = n * ldr;
   const int64_t row0 = iblock * kThreads * kRowsPerThread;
   extern __shared__ __align__(16) int8_t crt_smem[];
-  stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, 3 * N, ldr - row0);
+  // rows below round_up(m, 16) only: res may be a block of rows of a taller residue set
+  stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, 3 * N, (m + 15) / 16 * 16 - row0);
   const bool active = i0 < m;
   const int rr = threadIdx.x * kRowsPerThread;
 
@@ -333,7 +334,7 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
   const int64_t job_stride = n * ldr;
   const int64_t row0 = iblock * kThreads * kRowsPerThread;
   extern __shared__ __align__(16) int8_t crt_smem[];
-  stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, N, ldr - row0);
+  stage_residues<kRowsPerThread>(crt_smem, res + j * ldr + row0, job_stride, N, (m + 15) / 16 * 16 - row0);
   const bool active = i0 < m;
   const int rr = threadIdx.x * kRowsPerThread;
   uint64_t acc[kRowsPerThread][L];
@@ -692,7 +693,8 @@ cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl, const 
                        double br, double bi, void* C, int64_t ldc, cudaStream_t st, int rows, bool real,
                        bool robust) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  if (ldr % 16 || n > 2147483647LL) return cudaErrorInvalidValue;
+  if (ldr % 16 || m > ldr || n > 2147483647LL || (reinterpret_cast<uintptr_t>(res) & 15u))
+    return cudaErrorInvalidValue;
   switch (pl.L) {
     case 1: return launch_l<1>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);
     case 2: return launch_l<2>(single, m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc, st, rows, real, robust);

@@ -45,6 +45,7 @@ struct Unit {
   const CUtensorMap* mapB;          // A planes of the problem (MMA operand B)
   int8_t* res;
   int64_t ldr, n;
+  int64_t rcap;                     // residue rows stored per column: those below rcap
 };
 
 struct Sched {
@@ -66,7 +67,7 @@ struct SingleWork {
   const CUtensorMap* mapB;
   Sched s;
   int8_t* res;
-  int64_t ldr, n;
+  int64_t ldr, n, rcap;
   __device__ long long units() const { return s.units; }
   __device__ Unit get(long long u, int& /*hint*/) const {
     Unit w;
@@ -84,6 +85,7 @@ struct SingleWork {
     w.res = res;
     w.ldr = ldr;
     w.n = n;
+    w.rcap = rcap;
     return w;
   }
 };
@@ -128,6 +130,7 @@ struct GroupWork {
     w.res = P.res;
     w.ldr = P.ldr;
     w.n = P.n;
+    w.rcap = P.ldr;
     return w;
   }
 };
@@ -340,7 +343,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                   const int64_t r0 = row0 + cc + 16 * q;
-                  if (r0 < U.ldr)
+                  if (r0 < U.rcap)
                     *reinterpret_cast<uint4*>(out + cc + 16 * q) =
                         make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
                 }
@@ -366,8 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     gemm_f16_kernel(const __grid_constant__ CUtensorMap mapA,   // B planes: MMA operand A
                     const __grid_constant__ CUtensorMap mapB,   // A planes: MMA operand B
                     const __grid_constant__ Plan pl, const Sched s, int8_t* __restrict__ res, int64_t ldr,
-                    int64_t n, unsigned int* status) {
-  const SingleWork W{&mapA, &mapB, s, res, ldr, n};
+                    int64_t n, int64_t rcap, unsigned int* status) {
+  const SingleWork W{&mapA, &mapB, s, res, ldr, n, rcap};
   gemm_body<BN>(W, pl, status, false);
 }
 
@@ -395,13 +398,13 @@ cudaError_t set_smem_attrs() {
 template <int BN>
 cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                           const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group,
-                          unsigned int* status, cudaStream_t st, int ppm) {
+                          unsigned int* status, cudaStream_t st, int ppm, int64_t a_plane_rows, int64_t rcap) {
   cudaError_t e = set_smem_attrs<BN>();
   if (e != cudaSuccess) return e;
   const int J = ppm * pl.N;
   CUtensorMap mapA, mapB;
   if (!make_map(&mapA, planesB, n, kpad, J, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&mapB, planesA, m, kpad, J, BN)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, planesA, m, kpad, J, BN, a_plane_rows)) return cudaErrorInvalidValue;
   Sched s;
   s.J = J;
   s.ppm = ppm;
@@ -416,7 +419,7 @@ cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, co
   s.units = static_cast<long long>(s.pairs) * s.tiles;
   const long long grid = s.units < g_sms ? s.units : g_sms;
   gemm_f16_kernel<BN><<<static_cast<unsigned int>(grid), kThreads, Cfg<BN>::kSmemBytes, st>>>(
-      mapA, mapB, pl, s, res, ldr, n, status);
+      mapA, mapB, pl, s, res, ldr, n, rcap, status);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -425,19 +428,32 @@ cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, co
 
 int g_f16_group = 16;   // tile rasterisation group of grouped launches
 
+// a_plane_rows: rows between consecutive planes of planesA (0: m), so that a
+// block of rows of a larger plane set can be passed; rcap: residue rows stored
+// per column (0: ldr), at most ldr and a multiple of 16.
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                             const void* planesB, int8_t* res, int64_t ldr, int chunk_k, unsigned int* status,
-                            cudaStream_t st, int tile_n, int group, int ppm) {
+                            cudaStream_t st, int tile_n, int group, int ppm, int64_t a_plane_rows, int64_t rcap) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (ppm != 1 && ppm != 3) return cudaErrorInvalidValue;
   if (kpad % BK || ldr % 16 || chunk_k % BK || chunk_k < BK || chunk_k > 960) return cudaErrorInvalidValue;
+  if (a_plane_rows == 0) a_plane_rows = m;
+  if (rcap == 0) rcap = ldr;
+  if (a_plane_rows < m || rcap % 16 || rcap > ldr || rcap < m || (reinterpret_cast<uintptr_t>(res) & 15u))
+    return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u)
     return cudaErrorInvalidValue;
   if (!get_encoder()) return cudaErrorNotSupported;
   switch (tile_n) {
-    case 64: return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm);
-    case 128: return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm);
-    default: return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm);
+    case 64:
+      return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,
+                               a_plane_rows, rcap);
+    case 128:
+      return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,
+                                a_plane_rows, rcap);
+    default:
+      return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,
+                                a_plane_rows, rcap);
   }
 }
 

@@ -140,7 +140,8 @@ template <bool SINGLE, bool ROWS_CONTIG, typename T, int kPerThread, bool R = fa
 __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restrict__ Xv, int64_t rows, int64_t k,
                                             int64_t rs, int64_t hs, bool conj, const int16_t* __restrict__ xexp,
                                             const Plan& pl, int64_t kpad, T* __restrict__ planes, int64_t rtile,
-                                            int64_t htile) {
+                                            int64_t htile, int64_t prow) {
+  // prow: rows between consecutive planes (a block of rows of a larger plane set)
   const int tid = threadIdx.x;
   const int64_t r0 = rtile * kTileR;
   const int64_t h0 = htile * kTileH;
@@ -205,7 +206,7 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
     chunks<SINGLE, TC>(br, flagged ? 0 : x, nch, cre[j]);
     if constexpr (!R) chunks<SINGLE, TC>(bi, flagged ? 0 : x, nch, cim[j]);
   }
-  const int64_t plane_stride = rows * kpad;
+  const int64_t plane_stride = prow * kpad;
   T* base = planes + r * kpad + h0 + hb;
   T* dst = base;
   for (int l = 0; l < pl.N; ++l) {
@@ -353,10 +354,10 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict_
                                                          int64_t k, int64_t rs, int64_t hs,
                                                          bool conj, const int16_t* __restrict__ xexp,
                                                          const __grid_constant__ Plan pl,
-                                                         int64_t kpad, T* __restrict__ planes) {
+                                                         int64_t kpad, T* __restrict__ planes, int64_t prow) {
   __shared__ SplitSmem sm;
   split_block<SINGLE, ROWS_CONTIG, T, E, R, NCH>(sm, Xv, rows, k, rs, hs, conj, xexp, pl, kpad, planes, blockIdx.x,
-                                                 blockIdx.y);
+                                                 blockIdx.y, prow);
 }
 
 // one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
@@ -376,16 +377,16 @@ __global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __rest
   T* planes = static_cast<T*>(g.planes);
   if (g.rows_contig)
     split_block<SINGLE, true, T, 4, false, NCH>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad,
-                                                planes, rt, ht);
+                                                planes, rt, ht, g.rows);
   else
     split_block<SINGLE, false, T, 4, false, NCH>(sm, g.X, g.rows, g.k, g.rs, g.hs, g.conj != 0, g.xexp, pl, g.kpad,
-                                                 planes, rt, ht);
+                                                 planes, rt, ht, g.rows);
 }
 
 template <bool SINGLE, typename T, bool R>
 cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                      const Plan& pl, const int16_t* xexp, int64_t kpad, void* planes,
-                     cudaStream_t st, int elems) {
+                     cudaStream_t st, int elems, int64_t prow) {
   if ((rows + kTileR - 1) / kTileR > 2147483647LL || kpad / kTileH > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>((rows + kTileR - 1) / kTileR),
             static_cast<unsigned int>(kpad / kTileH));
@@ -393,8 +394,8 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
   // the common configuration (fp16 planes, 4 entries per thread) has the chunk count compiled in
   auto fixed = [&](auto nch_tag) {
     constexpr int NC = decltype(nch_tag)::value;
-    if (rs == 1) split_kernel<SINGLE, true, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
-    else split_kernel<SINGLE, false, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    if (rs == 1) split_kernel<SINGLE, true, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
+    else split_kernel<SINGLE, false, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
   };
   bool done = false;
   if constexpr (std::is_same<T, __half>::value) {
@@ -413,11 +414,11 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
   }
   if (done) {
   } else if (elems == 2) {
-    if (rs == 1) split_kernel<SINGLE, true, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
-    else split_kernel<SINGLE, false, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    if (rs == 1) split_kernel<SINGLE, true, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
+    else split_kernel<SINGLE, false, T, 2, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
   } else {
-    if (rs == 1) split_kernel<SINGLE, true, T, 4, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
-    else split_kernel<SINGLE, false, T, 4, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P);
+    if (rs == 1) split_kernel<SINGLE, true, T, 4, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
+    else split_kernel<SINGLE, false, T, 4, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -425,9 +426,10 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
 
 template <bool SINGLE, bool R>
 cudaError_t launch_s(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs, const Plan& pl,
-                     const int16_t* xexp, bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems) {
-  return fp16 ? launch_t<SINGLE, __half, R>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems)
-              : launch_t<SINGLE, int8_t, R>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems);
+                     const int16_t* xexp, bool fp16, int64_t kpad, void* planes, cudaStream_t st, int elems,
+                     int64_t prow) {
+  return fp16 ? launch_t<SINGLE, __half, R>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems, prow)
+              : launch_t<SINGLE, int8_t, R>(conj, X, rows, k, rs, hs, pl, xexp, kpad, planes, st, elems, prow);
 }
 
 }  // namespace
@@ -498,14 +500,16 @@ cudaError_t launch_bound_split(bool single, bool real, const void* X, int64_t ro
 
 cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, int64_t k,
                          int64_t rs, int64_t hs, const Plan& pl, const int16_t* xexp, bool fp16,
-                         int64_t kpad, void* planes, cudaStream_t st, int elems, bool real) {
+                         int64_t kpad, void* planes, cudaStream_t st, int elems, bool real, int64_t plane_rows) {
   if (rows <= 0 || kpad <= 0) return cudaSuccess;
   if (kpad % 64) return cudaErrorInvalidValue;
+  if (plane_rows == 0) plane_rows = rows;
+  if (plane_rows < rows) return cudaErrorInvalidValue;
   if (real)
-    return single ? launch_s<true, true>(false, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems)
-                  : launch_s<false, true>(false, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems);
-  return single ? launch_s<true, false>(conj, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems)
-                : launch_s<false, false>(conj, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems);
+    return single ? launch_s<true, true>(false, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems, plane_rows)
+                  : launch_s<false, true>(false, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems, plane_rows);
+  return single ? launch_s<true, false>(conj, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems, plane_rows)
+                : launch_s<false, false>(conj, X, rows, k, rs, hs, pl, xexp, fp16, kpad, planes, st, elems, plane_rows);
 }
 
 }  // namespace emu

@@ -170,7 +170,7 @@ def test_host_calls_on_two_streams():
 
 
 def test_host_trace_records_the_pipeline():
-    m, n, k, N = 48, 3 * 1024 + 77, 32, 6            # four column blocks
+    m, n, k, N = 2304, 3 * 1024 + 77, 32, 6          # three blocks of rows of A, four column blocks
     A, B, _ = _mats("z", m, n, k, "N", "N", 350)
     hA, pa, _ = _stored(A, m, True)
     hB, pb, _ = _stored(B, k, True)
@@ -183,11 +183,47 @@ def test_host_trace_records_the_pipeline():
     finally:
         emu.emu_host_trace_enable(0)
     names = [t[0] for t in tr]
-    assert names == ["start", "a_in"] + ["b_in"] * 4 + ["block_start", "block_crt", "c_out"] * 4 + ["end"]
-    ms = [t[1] for t in tr]
-    assert ms[0] == 0.0 and min(ms) >= 0.0
-    assert ms[-1] >= max(ms[:-1])                            # the call ends after every step
+    ms = {}
+    for nm, t in tr:
+        ms.setdefault(nm, []).append(t)
+    # side stream: the first column block, A's three blocks of rows, the other column blocks
+    side_in = [nm for nm in names if nm in ("a_in", "b_in")]
+    assert side_in == ["b_in", "a_in", "a_in", "a_in", "b_in", "b_in", "b_in"]
+    assert names[0] == "start" and names[-1] == "end"
+    # pinned C is written in place by each block's CRT: no separate copy back
+    assert [len(ms.get(nm, [])) for nm in ("block_start", "block_crt", "c_out")] == [4, 4, 0]
+    assert ms["start"] == [0.0] and min(t for _, t in tr) >= 0.0
+    assert ms["end"][0] >= max(t for _, t in tr)             # the call ends after every step
+    assert ms["block_crt"][0] >= ms["a_in"][-1]               # the first block used all of A
     for b in range(4):
-        s, c, o = ms[6 + 3 * b: 9 + 3 * b]
-        assert s <= c <= o                                   # block start, its CRT, its copy back
-        assert s >= ms[2 + b]                                # after its columns of B arrived
+        s, c = ms["block_start"][b], ms["block_crt"][b]
+        assert s <= c                                        # block start, its CRT
+        assert s >= ms["b_in"][b]                            # after its columns of B arrived
+
+
+@pytest.mark.parametrize("kind,opA,scaling", [("z", "N", "fast"), ("s", "T", "fast"), ("c", "C", "fast"),
+                                              ("d", "N", "accurate")])
+def test_host_row_blocks_of_a(kind, opA, scaling):
+    # m above 2048: A arrives in blocks of rows and the first column block is
+    # computed row block by row block (fast mode); padded leading dimensions,
+    # a ragged last block of rows, beta != 0
+    m, n, k, N = 2100, 2100, 48, 9
+    A, B, C = _mats(kind, m, n, k, opA, "N", 360)
+    alpha, beta = 0.5, 2.0
+    try:
+        if scaling == "accurate":
+            emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE), "scaling")
+        ref = _device_ref(kind, A, B, C, m, n, k, opA, "N", alpha, beta, N)
+        lda, ldb, ldc = A.shape[0] + 3, k + 1, m + 5
+        hA, pa, _ = _stored(A, lda, True)
+        hB, pb, _ = _stored(B, ldb, True)
+        hC, pc, view = _stored(C, ldc, True, fill=3)
+        f = KINDS[kind][2]
+        emu.check(f(opA, "N", m, n, k, _scal(kind, alpha), pa, lda, pb, ldb, _scal(kind, beta), pc, ldc, N),
+                  "host call")
+        torch.cuda.synchronize()
+    finally:
+        emu.emu_set_scaling(emu.EMU_SCALING_FAST)
+    got = view()
+    assert same_bits(np.ascontiguousarray(got[:m]), np.ascontiguousarray(ref)), mismatch_report(got[:m], ref)
+    assert np.all(got[m:] == 3)
