@@ -34,12 +34,13 @@ struct Plan {
   int p[kMaxModuli];                      // moduli
   uint32_t barrett[kMaxModuli];           // floor(2^32 / p)
   uint32_t two32[kMaxModuli];             // 2^32 mod p
-  float qp[kMaxModuli];                   // q_l / p_l rounded to float
+  float qinv[kMaxLimbs];                  // 2^(32 t) / P rounded to float (0 below the float range)
+  float off128, off255, off382;           // 128, 255, 382 times sum_l q_l / p_l, rounded to float
   uint32_t w[kMaxModuli][kMaxLimbs];      // w_l = (P/p_l) q_l, little endian
   uint32_t negP[kMaxLimbs];               // 2^(32L) - P
   uint32_t K[kMaxLimbs];                  // R0*P - 128*sum_l w_l  (mod 2^(32L)), real input
-  uint32_t KR[kMaxLimbs];                 // R0*P - 255*sum_l w_l, complex real part (D - E)
-  uint32_t KI[kMaxLimbs];                 // R0*P - 382*sum_l w_l, complex imaginary part (F - D - E)
+  uint32_t KR[kMaxLimbs];                 // R0*P - 255*sum_l w_l (mod 2^(32L)), complex real part (D - E)
+  uint32_t KI[kMaxLimbs];                 // R0*P - 382*sum_l w_l (mod 2^(32L)), complex imaginary part
   uint32_t Pw[kMaxLimbs];                 // P
   uint32_t H[kMaxLimbs];                  // (P - 1) / 2
   uint8_t pow2[kMaxModuli][kPow2Table];   // 2^s mod p_l

@@ -44,7 +44,10 @@ __device__ __forceinline__ int sym_small(int v, int p) {   // |v| <= 3 p / 2 + 1
 }
 
 // Round the L-limb two's-complement integer c (exact c') times 2^e2 to the
-// nearest binary64 (ties to even), by integer operations only.
+// nearest binary64 (ties to even), by integer operations only: the magnitude's
+// leading 64 bits (a window of the top nonzero limb and the two below it,
+// shifted up to the leading one) give the 53 kept bits and the round bit, and
+// everything below them only the sticky bit.
 template <int L>
 __device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
   const bool neg = (c[L - 1] >> 31) != 0;
@@ -57,52 +60,47 @@ __device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
       carry = static_cast<uint32_t>(v >> 32);
     }
   }
+  // top nonzero limb and the two below it (no dynamic indexing)
   int top = -1;
-  uint32_t topw = 0;
+  uint32_t w0 = 0, w1 = 0, w2 = 0;
 #pragma unroll
   for (int t = 0; t < L; ++t)
     if (c[t]) {
       top = t;
-      topw = c[t];
+      w0 = c[t];
+      w1 = t >= 1 ? c[t >= 1 ? t - 1 : 0] : 0u;
+      w2 = t >= 2 ? c[t >= 2 ? t - 2 : 0] : 0u;
     }
   if (top < 0) return 0.0;
-  const int b = 32 * top + (31 - __clz(topw));            // leading bit index
-  const int lead = b + e2;
-  const int lsb = max(lead - 52, -1074);
-  const int sh = lsb - e2;                                  // bit index of the result LSB
-  uint64_t q;
-  if (sh <= 0) {
-    // |c'| < 2^53: the value fits in limbs 0..1
-    uint64_t v = static_cast<uint64_t>(c[0]);
-    if constexpr (L > 1) v |= static_cast<uint64_t>(c[1]) << 32;
-    q = v << (-sh);
+  bool sticky = false;
+#pragma unroll
+  for (int t = 0; t + 3 < L; ++t) sticky |= (t + 3 <= top) && c[t] != 0u;
+  const int lz = __clz(w0);
+  uint64_t W = (static_cast<uint64_t>(w0) << 32) | w1;    // leading one moved to bit 63 below
+  if (lz) {
+    W = (W << lz) | (w2 >> (32 - lz));
+    sticky |= (w2 << lz) != 0u;
   } else {
-    // q = bits [sh, sh + 53] of c, plus round and sticky bits
-    q = 0;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const int pos = 32 * t - sh;                          // where limb t lands in q
-      if (pos >= 64 || pos <= -32) continue;
-      const uint64_t limb = c[t];
-      q |= pos >= 0 ? (limb << pos) : (limb >> (-pos));
-    }
-    const int rb = sh - 1;                                  // round bit index
-    uint32_t rw = 0;                                        // limb holding it (no dynamic indexing)
-#pragma unroll
-    for (int t = 0; t < L; ++t)
-      if (t == (rb >> 5)) rw = c[t];
-    const bool half = (rw >> (rb & 31)) & 1u;
-    bool sticky = false;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const int lo = 32 * t;
-      if (lo >= rb) continue;
-      const int nb = min(32, rb - lo);
-      const uint32_t mask = nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u);
-      sticky |= (c[t] & mask) != 0u;
-    }
-    if (half && (sticky || (q & 1ull))) ++q;
+    sticky |= w2 != 0u;
   }
+  const int lead = 32 * top + 31 - lz + e2;                // exponent of the leading bit
+  const int lsb = max(lead - 52, -1074);                   // exponent of the result's LSB
+  const int drop = 63 - (lead - lsb);                      // bits of W below it: >= 11
+  uint64_t q;
+  bool half;
+  if (drop >= 65) {            // below half the smallest subnormal
+    q = 0;
+    half = false;
+  } else if (drop == 64) {     // in [2^(lsb-1), 2^lsb): the round bit is the leading one
+    q = 0;
+    half = true;
+    sticky |= (W << 1) != 0ull;
+  } else {
+    q = W >> drop;
+    half = ((W >> (drop - 1)) & 1ull) != 0ull;
+    sticky |= (W & ((1ull << (drop - 1)) - 1ull)) != 0ull;
+  }
+  if (half && (sticky || (q & 1ull))) ++q;
   uint64_t bits = (static_cast<uint64_t>(lsb + 1074) << 52) + q;
   if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
   if (neg) bits |= 0x8000000000000000ull;
@@ -151,16 +149,25 @@ __device__ __forceinline__ void fix_range(uint32_t (&c)[L], const Plan& pl) {
   }
 }
 
-// Finish one part: add the quotient term, carry once, (accurate mode) fix the
-// range, round.
+// Finish one part.  acc holds sum_l u_l w_l limb by limb (unnormalised), u_l
+// the residues offset to be non-negative by `off` (the offset constant koff =
+// R0 P - off sum_l w_l).  The quotient r = round(sum_l E'_l w_l / P) is
+// estimated in float from the limbs, sum_t acc_t 2^(32 t) / P - off sum_l q_l /
+// p_l (every term below 765 N: the float error stays far under the 1/8 margin
+// of condition (cond)); then c' = acc + koff + (r + R0)(2^(32 L) - P) mod
+// 2^(32 L), carried once, (accurate mode) range-fixed and rounded.
 template <int L, bool ROBUST>
-__device__ __forceinline__ double finish(const uint64_t (&acc)[L], float est, const Plan& pl, int e2) {
+__device__ __forceinline__ double finish(const uint64_t (&acc)[L], const uint32_t* koff, float foff, const Plan& pl,
+                                         int e2) {
+  float est = -foff;
+#pragma unroll
+  for (int t = 0; t < L; ++t) est = fmaf(__ull2float_rn(acc[t]), pl.qinv[t], est);
   const uint32_t rq = static_cast<uint32_t>(static_cast<int>(rintf(est)) + pl.R0);
   uint32_t c[L];
   uint64_t carry = 0;
 #pragma unroll
   for (int t = 0; t < L; ++t) {
-    const uint64_t v = acc[t] + static_cast<uint64_t>(rq) * pl.negP[t] + carry;
+    const uint64_t v = acc[t] + koff[t] + static_cast<uint64_t>(rq) * pl.negP[t] + carry;
     c[t] = static_cast<uint32_t>(v);
     carry = v >> 32;
   }
@@ -220,21 +227,15 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
   const bool active = i0 < m;
   const int rr = threadIdx.x * kRowsPerThread;
 
-  // exact limb accumulators for the real and imaginary parts of 4 rows
+  // exact limb accumulators for the real and imaginary parts of the thread's rows
   uint64_t accR[kRowsPerThread][L], accI[kRowsPerThread][L];
-  float estR[kRowsPerThread], estI[kRowsPerThread];
   if (active) {
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
-    estR[q] = estI[q] = 0.0f;
 #pragma unroll
-    for (int t = 0; t < L; ++t) {
-      accR[q][t] = pl.KR[t];
-      accI[q][t] = pl.KI[t];
-    }
+    for (int t = 0; t < L; ++t) accR[q][t] = accI[q][t] = 0ull;
   }
   for (int l = 0; l < N; ++l) {
-    const float qp = pl.qp[l];
     uint32_t w[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) w[t] = pl.w[l][t];
@@ -255,8 +256,6 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
         accR[q][t] = mad_wide(ur, w[t], accR[q][t]);
         accI[q][t] = mad_wide(ui, w[t], accI[q][t]);
       }
-      estR[q] = fmaf(static_cast<float>(vr), qp, estR[q]);
-      estI[q] = fmaf(static_cast<float>(vi), qp, estI[q]);
     }
   }
   }
@@ -278,8 +277,8 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
         orr = oi = __longlong_as_double(0x7FF8000000000000ll);
       } else {
         const int e2 = -(xi + yj);
-        orr = finish<L, ROBUST>(accR[q], estR[q], pl, e2);
-        oi = finish<L, ROBUST>(accI[q], estI[q], pl, e2);
+        orr = finish<L, ROBUST>(accR[q], pl.KR, pl.off255, pl, e2);
+        oi = finish<L, ROBUST>(accI[q], pl.KI, pl.off382, pl, e2);
       }
       so[rr + q] = make_double2(orr, oi);
     }
@@ -338,16 +337,13 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
   const bool active = i0 < m;
   const int rr = threadIdx.x * kRowsPerThread;
   uint64_t acc[kRowsPerThread][L];
-  float est[kRowsPerThread];
   if (active) {
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
-    est[q] = 0.0f;
 #pragma unroll
-    for (int t = 0; t < L; ++t) acc[q][t] = pl.K[t];
+    for (int t = 0; t < L; ++t) acc[q][t] = 0ull;
   }
   for (int l = 0; l < N; ++l) {
-    const float qp = pl.qp[l];
     uint32_t w[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) w[t] = pl.w[l][t];
@@ -357,7 +353,6 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
       const uint32_t u = (wv >> (8 * q)) & 0xFFu;
 #pragma unroll
       for (int t = 0; t < L; ++t) acc[q][t] = mad_wide(u, w[t], acc[q][t]);
-      est[q] = fmaf(static_cast<float>(static_cast<int>(u) - 128), qp, est[q]);
     }
   }
   }
@@ -372,7 +367,7 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
       if (i >= m) break;
       const int xi = x[i];
       so[rr + q] = (xi == kExpNonfinite || yj == kExpNonfinite) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                                : finish<L, ROBUST>(acc[q], est[q], pl, -(xi + yj));
+                                                                : finish<L, ROBUST>(acc[q], pl.K, pl.off128, pl, -(xi + yj));
     }
   }
   __syncthreads();

@@ -167,6 +167,7 @@ void build(int N, Plan& pl) {
   pl.L = (bitsP + 2 + 31) / 32;
   // Step II and the CRT weights
   Big sumw;
+  double sum_qp = 0.0;                         // sum_l q_l / p_l = sum_l w_l / P
   for (int l = 0; l < N; ++l) {
     const uint32_t p = static_cast<uint32_t>(pl.p[l]);
     Big M = P;
@@ -183,7 +184,7 @@ void build(int N, Plan& pl) {
     mul_small(w, q);
     for (int t = 0; t < kMaxLimbs; ++t) pl.w[l][t] = t < pl.L ? w.v[t] : 0u;
     add(sumw, w);
-    pl.qp[l] = static_cast<float>(static_cast<double>(q) / static_cast<double>(p));
+    sum_qp += static_cast<double>(q) / static_cast<double>(p);
     pl.barrett[l] = static_cast<uint32_t>((1ull << 32) / p);
     pl.two32[l] = static_cast<uint32_t>((1ull << 32) % p);
     uint32_t v = 1 % p;
@@ -233,6 +234,13 @@ void build(int N, Plan& pl) {
     pl.Ph = big_to_double(P);
     pl.Pl = big_minus_double(P, pl.Ph);
   }
+  // the CRT quotient estimate from the accumulated limbs: sum_t acc_t 2^(32 t) / P,
+  // less the offset the unsigned residues carry (u = E' + 128, D - E + 255, F - D - E + 382)
+  for (int t = 0; t < kMaxLimbs; ++t)
+    pl.qinv[t] = t < pl.L ? static_cast<float>(std::ldexp(1.0, 32 * t) / pl.Ph) : 0.0f;
+  pl.off128 = static_cast<float>(128.0 * sum_qp);
+  pl.off255 = static_cast<float>(255.0 * sum_qp);
+  pl.off382 = static_cast<float>(382.0 * sum_qp);
   // negP = 2^(32L) - P, K = R0 P - 128 sum w (mod 2^(32L))
   Big zero;
   Big negP = zero;

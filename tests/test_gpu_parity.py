@@ -257,3 +257,39 @@ def test_paper_fp64_crt_bitexact(single, N):
     finally:
         emu.emu_set_crt_mode(emu.EMU_CRT_EXACT)
     assert same_bits(got, want), mismatch_report(got, want)
+
+
+@pytest.mark.parametrize("single", [False, True])
+def test_outputs_across_the_subnormal_range_and_overflow(single):
+    """Output magnitudes swept by exact power-of-two scalings of rows and
+    columns through the normal range, the subnormals, underflow to (signed)
+    zero and overflow to infinity: the CRT's integer rounding against the
+    oracle's (each scaling only shifts x_i or y_j, so c' is unchanged)."""
+    N = 14
+    m, n, k = 24, 64, 40
+    A = paper_matrix(m, k, 1.0, 401)
+    B = paper_matrix(k, n, 1.0, 402)
+    h = n // 2
+    if single:       # complex64: normal down to 2^-126, subnormal to 2^-149, finite below 2^128
+        a_lo, a_hi, b_under, b_step, b_over = -50, 58, -70, -2, 60
+    else:            # complex128: normal down to 2^-1022, subnormal to 2^-1074, finite below 2^1024
+        a_lo, a_hi, b_under, b_step, b_over = -480, 480, -540, -3, 520
+    A[: m // 2] *= 2.0 ** a_lo
+    A[m // 2:] *= 2.0 ** a_hi
+    for j in range(h):                  # rows scaled by 2^a_lo: outputs near 2^(a_lo + b_under + b_step j)
+        B[:, j] *= 2.0 ** (b_under + b_step * j)
+    for j in range(h, n):               # rows scaled by 2^a_hi: outputs near 2^(a_hi + b_over + j - h)
+        B[:, j] *= 2.0 ** (b_over + j - h)
+    dt = np.complex64 if single else np.complex128
+    A, B = A.astype(dt), B.astype(dt)
+    ref = emulate(A.astype(np.complex128), B.astype(np.complex128), N, keep_residue_planes=False,
+                  out_fmt=fp.BINARY32 if single else fp.BINARY64)
+    got = run_gemm(A, B, N, single=single)
+    want = ref.out
+    assert same_bits(got, want), mismatch_report(got, want)
+    # the sweep reached what it is for
+    w = np.concatenate([want.real.ravel(), want.imag.ravel()])
+    tiny = np.finfo(np.float32 if single else np.float64).tiny
+    assert np.any((w != 0) & (np.abs(w) < tiny))                  # subnormal results
+    assert np.any(w == 0) and np.any(np.signbit(w[w == 0]))       # underflow, with its sign
+    assert np.any(np.isinf(w))                                   # overflow
