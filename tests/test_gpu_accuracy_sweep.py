@@ -5,7 +5,8 @@ ZGEMM 16384^3 with phi in {0, 1, 2} and N = 12..20, CGEMM 8192^3 with phi in
 {0, 0.5, 1} and N = 6..10: the normalised error of the emulation and of native
 cuBLAS against the correctly rounded exact product on 4096 sampled entries
 (the exact reference runs in a process pool started with `spawn`).  The
-report goes to gpurun_out/accuracy_sweep.json when that folder exists."""
+report is also written as accuracy_sweep.json into the output folder, when
+that folder exists."""
 import json
 import multiprocessing as mp
 import os
