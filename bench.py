@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the unfused cuBLAS-INT8 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--overlap", choices=["auto", "on", "off"], default="auto",
+                    help="EMU_TUNE_OVERLAP: split and CRT of neighbouring column blocks beside the products "
+                         "(auto: the library's default, on for the real GEMMs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--scaling", choices=["fast", "accurate"], default="fast",
                     help="scaling vectors of Section III-B (fast or accurate mode)")
@@ -196,6 +199,12 @@ def run_reference(args, wl, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+def overlap_blocks(n):
+    """Column blocks of an overlapped GEMM: about eight of a multiple of 256 columns, at least 1024."""
+    nb = max(1024, (-(-n // 8) + 255) // 256 * 256)
+    return -(-n // nb)
+
+
 def profile_traffic(kernel_file, summary_name):
     """dram bytes per launch from the committed ncu summary, if the kernel source
     is unchanged since the capture (its sha256 is recorded there)."""
@@ -242,6 +251,8 @@ def main():
     emu.lib()
     emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE if args.scaling == "accurate" else emu.EMU_SCALING_FAST),
               "emu_set_scaling")
+    if args.overlap != "auto":
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, 1 if args.overlap == "on" else 0), "overlap")
     m, n, k, N = wl["m"], wl["n"], wl["k"], wl["N"]
     single = wl["single"]
     real = bool(wl.get("real"))
@@ -303,19 +314,48 @@ def main():
     ms = max_over_ranks(total_ms / args.steps, dist)
     flops = flops_per_entry(wl) * m * n * k
     value = world * flops / (ms * 1e-3) * 1e-12
+    ev_ms = lambda row, a, b: statistics.mean(row[i][a].elapsed_time(row[i][b]) for i in range(len(row)))
+    # overlapped column blocks (EMU_TUNE_OVERLAP; by default on for the real GEMMs): the step's phase events mark
+    # the planes of A and of the first block (0 -> 2), the residue products of all blocks back to
+    # back (2 -> 3) and the last block's CRT (3 -> 4); the other blocks' exponents, planes and CRTs
+    # run beside the products.  The per-phase times below come from one more step with overlap off.
+    ov_setting = emu.emu_get_tuning(emu.EMU_TUNE_OVERLAP)
+    overlapped = ((ov_setting == 1 or (ov_setting < 0 and real)) and args.scaling == "fast" and n >= 2048)
+    nblk = overlap_blocks(n) if overlapped else 1
+    if overlapped:
+        overlap_ms = {"planes_before_first_products": ev_ms(evs, 0, 2), "residue_products_all_blocks": ev_ms(evs, 2, 3),
+                      "last_crt": ev_ms(evs, 3, 4)}
+        t_gemm_step = overlap_ms["residue_products_all_blocks"] * 1e-3
+        sev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]]
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, 0), "overlap off")
+        try:
+            step()
+            emu.check(emu.emu_set_phase_events(sev[0]), "phase events")
+            step()
+            emu.emu_set_phase_events(None)
+        finally:
+            emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, ov_setting)
+        torch.cuda.synchronize()
+        pev_rows = sev
+    else:
+        pev_rows = evs
     phase_names = ["exponents", "split", "residue_gemm", "crt"]
-    phases = {nm: statistics.mean(evs[i][p].elapsed_time(evs[i][p + 1]) for i in range(args.steps))
-              for p, nm in enumerate(phase_names)}
+    phases = {nm: ev_ms(pev_rows, p, p + 1) for p, nm in enumerate(phase_names)}
     pk, pk_src = peaks()
-    t_gemm = phases["residue_gemm"] * 1e-3
+    if not overlapped:
+        t_gemm_step = phases["residue_gemm"] * 1e-3
     gemm_flops = 2.0 * ppm * N * m * n * k
+    t_gemm = t_gemm_step
     achieved = gemm_flops / t_gemm * 1e-12
     peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
     traffic = profile_traffic("k_gemm_f16.cu", f"gemm_f16_{args.workload}.txt")
     roofline = {"bound": "tensor", "kernel": "gemm_f16_kernel (tcgen05.mma kind::f16, exact residue products)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": f"{pk_src} bf16_tflops_sustained (fp16 = bf16 rate)",
-                "algorithmic_flops_per_launch": gemm_flops}
+                "traffic": (traffic / nblk if traffic else traffic),
+                "peak_source": f"{pk_src} bf16_tflops_sustained (fp16 = bf16 rate)",
+                "launches_per_step": nblk, "algorithmic_flops_per_launch": gemm_flops / nblk,
+                "timing": ("the step's residue-product launches back to back on their stream (CUDA events), "
+                           "divided by the launches" if overlapped else "the one launch of the step (CUDA events)")}
     hbm = float(pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     byts = {"exponents": 2 * esz * k * (m + n), "split": esz * k * (m + n) + ppm * N * 2 * k * (m + n),
             "crt": ppm * N * m * n + esz * m * n}
@@ -334,6 +374,9 @@ def main():
                       "tuning": dict(zip(["tile_n", "group", "chunk_k", "crt_rows", "split_elems"], tuned))
                       if tuned else "defaults"},
            "roofline": roofline, "phases_ms": phases, "memory_phases": mem_phases,
+           "overlap": ({"column_blocks": nblk, "step_ms": overlap_ms,
+                        "phases_ms_from": "one more step with EMU_TUNE_OVERLAP = 0 (one phase after another)"}
+                       if overlapped else None),
            # the paper counts the residue products as INT8 operations (6N mnk complex, 2N mnk real):
            # their rate here, beside GB300's dense INT8 peak from its Table 1 (B300 row)
            "int8_equivalent": {"tops": gemm_flops / t_gemm * 1e-12, "table1_int8_peak_tops": 150.0,
@@ -344,6 +387,8 @@ def main():
     # ---- the paper's floating-point CRT on the same step (one run, phase events)
     pev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     emu.check(emu.emu_set_crt_mode(emu.EMU_CRT_PAPER_FP64), "crt mode")
+    overlap_setting = emu.emu_get_tuning(emu.EMU_TUNE_OVERLAP)
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, 0), "overlap off")     # phases one after another
     try:
         step()
         emu.check(emu.emu_set_phase_events(pev), "phase events")
@@ -351,6 +396,7 @@ def main():
         emu.emu_set_phase_events(None)
     finally:
         emu.emu_set_crt_mode(emu.EMU_CRT_EXACT)
+        emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, overlap_setting)
     torch.cuda.synchronize()
     out["crt_modes_ms"] = {"exact_integer": phases["crt"], "paper_fp64_double_double": pev[3].elapsed_time(pev[4])}
 

@@ -307,6 +307,20 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *   EMU_TUNE_SPLIT_ELEMS residue split: entries per thread, 2/4
  *   EMU_TUNE_NBLOCK      output columns per block, 0 (automatic) or a multiple of 128;
  *                        a process setting only, never autotuned
+ *   EMU_TUNE_OVERLAP     1: device-buffer GEMMs in fast scaling on the tcgen05
+ *                        engine with n >= 2048 run in column blocks (the
+ *                        EMU_TUNE_NBLOCK width, else about eight blocks of a
+ *                        multiple of 256 columns, at least 1024), and a
+ *                        library-owned stream forms the next block's exponents
+ *                        and planes and the previous block's CRT beside each
+ *                        block's residue products (planes of B and residues
+ *                        double-buffered); 0: one phase after another; -1
+ *                        (default): 1 for emu_dgemm/emu_sgemm, 0 for the complex
+ *                        GEMMs.  On a power-capped GB300 the residue products
+ *                        slow down beside the other phases: for the complex
+ *                        GEMMs by about what the overlap hides, for the real
+ *                        ones (a third of the products per output) by less.  A
+ *                        process setting only, never autotuned
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
  * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
@@ -321,6 +335,7 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 #define EMU_TUNE_CRT_ROWS 4
 #define EMU_TUNE_SPLIT_ELEMS 5
 #define EMU_TUNE_NBLOCK 6
+#define EMU_TUNE_OVERLAP 7
 emu_status_t emu_set_tuning(int key, int value);
 int emu_get_tuning(int key);
 emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int num_moduli, int* best);

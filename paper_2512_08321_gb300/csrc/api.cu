@@ -33,7 +33,27 @@ struct DeviceState {
   int* chosen_host = nullptr;
   void* stage = nullptr;       // staging of the host-buffer entry points
   size_t stage_bytes = 0;
+  // overlapped column blocks: the library's second stream and its events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_split[2] = {}, ev_gemm[2] = {}, ev_crt[2] = {};
 };
+
+cudaError_t aux_stream(DeviceState* ds) {
+  if (ds->aux) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&ds->aux, cudaStreamNonBlocking);
+  cudaEvent_t* evs[] = {&ds->ev_start, &ds->ev_done, &ds->ev_split[0], &ds->ev_split[1], &ds->ev_gemm[0],
+                        &ds->ev_gemm[1], &ds->ev_crt[0], &ds->ev_crt[1]};
+  for (cudaEvent_t* ev : evs)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  return e;
+}
+
+// Columns per block of an overlapped GEMM: about eight blocks of a multiple of
+// 256 (the residue GEMM's tile width), at least 1024.
+int64_t overlap_block(int64_t n) {
+  const int64_t nb = round_up((n + 7) / 8, 256);
+  return nb < 1024 ? 1024 : nb;
+}
 
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
@@ -74,14 +94,16 @@ emu_status_t device_init(int dev, DeviceState*& ds) {
 
 // Workspace layout of one GEMM whose output columns are processed nb at a time
 // (nb == n: one pass).  ppm = residue planes per modulus (3 complex, 1 real).
+// bufs = 2: two sets of B planes and residues (column blocks overlapped).
 struct Layout {
   int64_t kpad, ldr;
   size_t off_x, off_y, off_scr, off_acc, off_pa, off_pb, off_res, total;
+  size_t pb_bytes, res_bytes;   // one set
 };
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
-Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm = 3, int64_t nb = -1) {
+Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm = 3, int64_t nb = -1, int bufs = 1) {
   if (nb < 0 || nb > n) nb = n;
   Layout L;
   L.kpad = round_up(k > 0 ? k : 1, 64);
@@ -93,8 +115,10 @@ Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm = 3, in
   L.off_scr = o; o += al(exponents_scratch_bytes(m > nb ? m : nb));
   L.off_acc = o; o += al(static_cast<size_t>(12) * (m + n));   // accurate mode: e, flag, bound maxima
   L.off_pa = o;  o += al(static_cast<size_t>(ppm * N) * m * L.kpad * esz);
-  L.off_pb = o;  o += al(static_cast<size_t>(ppm * N) * nb * L.kpad * esz);
-  L.off_res = o; o += al(static_cast<size_t>(ppm * N) * nb * L.ldr);
+  L.pb_bytes = al(static_cast<size_t>(ppm * N) * nb * L.kpad * esz);
+  L.res_bytes = al(static_cast<size_t>(ppm * N) * nb * L.ldr);
+  L.off_pb = o;  o += bufs * L.pb_bytes;
+  L.off_res = o; o += bufs * L.res_bytes;
   L.total = o;
   return L;
 }
@@ -181,33 +205,34 @@ struct Dt {
 
 constexpr size_t kFreeMargin = size_t(256) << 20;   // device memory left to others when blocking
 
-// Output columns per block.  The knob (if set) wins; otherwise one block when
-// the whole workspace fits (the caller's buffer, or the library's plus free
-// device memory), else the widest multiple of 128 columns that fits.
+// Output columns per block.  The knob (if set) wins; otherwise `want` columns
+// (0: all n) when that workspace fits (the caller's buffer, or the library's
+// plus free device memory), else the widest multiple of 128 columns that fits.
 int64_t choose_nblock(const DeviceState* ds, int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm,
-                      const Tune& t) {
+                      const Tune& t, int64_t want = 0, int bufs = 1) {
   if (t.nblock > 0) return t.nblock < n ? t.nblock : n;
-  const size_t full = layout(m, n, k, N, fp16, ppm, n).total;
+  if (want <= 0 || want > n) want = n;
+  const size_t full = layout(m, n, k, N, fp16, ppm, want, bufs).total;
   size_t limit;
   if (ds->user) {
     limit = ds->user_bytes;
   } else {
-    if (full <= ds->own_bytes) return n;
+    if (full <= ds->own_bytes) return want;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
       cudaGetLastError();
-      return n;
+      return want;
     }
     limit = fr + ds->own_bytes;
     limit = limit > kFreeMargin ? limit - kFreeMargin : 0;
   }
-  if (full <= limit || n <= 128) return n;
-  int64_t lo = 0, hi = (n - 1) / 128;     // widths 128 * [1, hi] are candidates
+  if (full <= limit || want <= 128) return want;
+  int64_t lo = 0, hi = (want - 1) / 128;  // widths 128 * [1, hi] are candidates
   while (lo < hi) {
     const int64_t mid = (lo + hi + 1) / 2;
-    if (layout(m, n, k, N, fp16, ppm, 128 * mid).total <= limit) lo = mid; else hi = mid - 1;
+    if (layout(m, n, k, N, fp16, ppm, 128 * mid, bufs).total <= limit) lo = mid; else hi = mid - 1;
   }
-  return lo > 0 ? 128 * lo : n;            // nothing fits: one block, and the workspace check reports it
+  return lo > 0 ? 128 * lo : want;         // nothing fits: one block, and the workspace check reports it
 }
 
 // hooks (host-buffer calls): the operands move in blocks on another stream and
@@ -232,11 +257,21 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   char* ws = nullptr;
   int64_t nb;
   Layout L;
+  const bool accurate = (g_scaling == EMU_SCALING_ACCURATE);
+  // overlapped column blocks: device-buffer calls in fast mode on the tcgen05 engine
+  bool overlap = !hooks && (tn.overlap == 1 || (tn.overlap < 0 && dt.real)) && k > 0 && !accurate && fp16 &&
+                 n >= 2048;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    nb = choose_nblock(ds, m, n, k, N, fp16, ppm, tn);
-    if (hooks && hooks->nb > 0 && hooks->nb < nb) nb = hooks->nb;
-    L = layout(m, n, k, N, fp16, ppm, nb);
+    if (overlap) {
+      nb = choose_nblock(ds, m, n, k, N, fp16, ppm, tn, overlap_block(n), 2);
+      overlap = nb < n && aux_stream(ds) == cudaSuccess;
+    }
+    if (!overlap) {
+      nb = choose_nblock(ds, m, n, k, N, fp16, ppm, tn);
+      if (hooks && hooks->nb > 0 && hooks->nb < nb) nb = hooks->nb;
+    }
+    L = layout(m, n, k, N, fp16, ppm, nb, overlap ? 2 : 1);
     s = get_workspace(ds, L.total, &ws);
   }
   if (s != EMU_OK) return s;
@@ -253,7 +288,6 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   // element sizes of B and C, to step to a column block
   const size_t in_esz = (dt.real ? 1 : 2) * (dt.single ? 4 : 8);
   const bool conj_a = !dt.real && ta == EMU_OP_C, conj_b = !dt.real && tb == EMU_OP_C;
-  const bool accurate = (g_scaling == EMU_SCALING_ACCURATE);
   // accurate-mode exponents reach 7 bits further: the split covers them with more chunks
   Plan pls = *pl;
   if (accurate) pls.nchunk = pl->nchunk_accu;
@@ -261,15 +295,80 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     return k > 0 ? static_cast<const void*>(static_cast<const char*>(B) + static_cast<size_t>(j0) * rsb * in_esz)
                  : B;
   };
-  auto crt = [&](int64_t mi, int64_t nj, const int8_t* r, const int16_t* xi, const int16_t* yj, void* Ci) {
+  auto crt_on = [&](cudaStream_t cs, int64_t mi, int64_t nj, const int8_t* r, const int16_t* xi,
+                    const int16_t* yj, void* Ci) {
     return cuda_status(g_crt_mode == 1
-                           ? launch_crt_fp(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, st,
+                           ? launch_crt_fp(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
                                            dt.real)
-                           : launch_crt(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, st,
+                           : launch_crt(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
                                         tn.crt_rows, dt.real, accurate));
+  };
+  auto crt = [&](int64_t mi, int64_t nj, const int8_t* r, const int16_t* xi, const int16_t* yj, void* Ci) {
+    return crt_on(st, mi, nj, r, xi, yj, Ci);
   };
   cudaError_t e;
   phase(0, st);
+  if (overlap) {
+    // Column block b's residue products on the caller's stream; beside them,
+    // on the library's stream, block b+1's exponents and planes (into the
+    // other set of B planes, free once block b-1's products are done) and
+    // block b-1's CRT (from the other set of residues, which block b+1's
+    // products then overwrite).  Phase events: 1 and 2 when A's and the first
+    // block's planes are ready, 3 after the last products, 4 at the end.
+    cudaStream_t ax = ds->aux;
+    const int64_t nblk = (n + nb - 1) / nb;
+    auto pbuf = [&](int64_t b) { return static_cast<char*>(pb) + (b & 1) * L.pb_bytes; };
+    auto rbuf = [&](int64_t b) { return res + (b & 1) * L.res_bytes; };
+    auto width = [&](int64_t b) { return (n - b * nb) < nb ? (n - b * nb) : nb; };
+    auto prepare = [&](int64_t b) -> cudaError_t {   // exponents and planes of block b's columns of B
+      const int64_t j0 = b * nb, nj = width(b);
+      cudaError_t err = launch_exponents(dt.single, block_ptr(j0), nj, k, rsb, hsb, *pl, y + j0, scr, ax, dt.real);
+      if (err == cudaSuccess)
+        err = launch_split(dt.single, conj_b, block_ptr(j0), nj, k, rsb, hsb, pls, y + j0, fp16, L.kpad, pbuf(b), ax,
+                           tn.split_elems, dt.real);
+      if (err == cudaSuccess) err = cudaEventRecord(ds->ev_split[b & 1], ax);
+      return err;
+    };
+    auto finish_block = [&](int64_t b) -> emu_status_t {   // CRT of block b, once its products are done
+      if (cudaStreamWaitEvent(ax, ds->ev_gemm[b & 1], 0) != cudaSuccess) return EMU_ERR_CUDA;
+      const int64_t j0 = b * nb;
+      void* Cj = static_cast<char*>(C) + static_cast<size_t>(j0) * ldc * in_esz;
+      const emu_status_t r = crt_on(ax, m, width(b), rbuf(b), x, y + j0, Cj);
+      if (r != EMU_OK) return r;
+      return cuda_status(cudaEventRecord(ds->ev_crt[b & 1], ax));
+    };
+    if (cudaEventRecord(ds->ev_start, st) != cudaSuccess || cudaStreamWaitEvent(ax, ds->ev_start, 0) != cudaSuccess ||
+        launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, ax, dt.real) != cudaSuccess ||
+        launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, ax, tn.split_elems, dt.real) !=
+            cudaSuccess ||
+        prepare(0) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    for (int64_t b = 0; b < nblk; ++b) {
+      if (cudaStreamWaitEvent(st, ds->ev_split[b & 1], 0) != cudaSuccess ||
+          (b >= 2 && cudaStreamWaitEvent(st, ds->ev_crt[b & 1], 0) != cudaSuccess))
+        return EMU_ERR_CUDA;
+      if (b == 0) {
+        phase(1, st);
+        phase(2, st);
+      }
+      if ((s = run_residue_gemm(eng, m, width(b), L.kpad, *pl, pa, pbuf(b), rbuf(b), L.ldr, ds, st, tn, ppm)) !=
+          EMU_OK)
+        return s;
+      if (cudaEventRecord(ds->ev_gemm[b & 1], st) != cudaSuccess) return EMU_ERR_CUDA;
+      if (b + 1 < nblk) {
+        if ((b >= 1 && cudaStreamWaitEvent(ax, ds->ev_gemm[(b + 1) & 1], 0) != cudaSuccess) ||
+            prepare(b + 1) != cudaSuccess)
+          return EMU_ERR_CUDA;
+      }
+      if (b >= 1 && (s = finish_block(b - 1)) != EMU_OK) return s;
+    }
+    phase(3, st);
+    if ((s = finish_block(nblk - 1)) != EMU_OK) return s;
+    if (cudaEventRecord(ds->ev_done, ax) != cudaSuccess || cudaStreamWaitEvent(st, ds->ev_done, 0) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    phase(4, st);
+    return EMU_OK;
+  }
   // rows_piped: the first column block row block by row block as A arrives
   const bool rows_piped = hooks && hooks->mb > 0 && hooks->mb % 16 == 0 && k > 0 && !accurate && fp16;
   if (hooks && !rows_piped && (s = hooks->wait_rows(hooks->ctx, 0, m, st)) != EMU_OK) return s;

@@ -95,6 +95,8 @@ struct Tune {
   int crt_rows = 4;      // CRT: rows per thread (1, 2, 4)
   int split_elems = 4;   // split: entries per thread (2, 4)
   int nblock = 0;        // output columns per block (0: automatic, by workspace size)
+  int overlap = -1;      // split and CRT of neighbouring column blocks beside the residue products:
+                         // 1 on, 0 off, -1 (default) on for the real GEMMs only
 };
 
 // Tuning of a call of this shape: the autotuned entry of its (dtype, N, shape
@@ -232,5 +234,14 @@ emu_status_t get_staging(size_t need, char** out);
 void count_launches(int n);
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// Kernels that may run beside the residue GEMM ask for the largest shared-memory
+// carveout, the configuration an SM holding a residue-GEMM block already has.
+template <typename K>
+inline void max_shared_carveout(K* kern) {
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributePreferredSharedMemoryCarveout,
+                           static_cast<int>(cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    cudaGetLastError();
+}
 
 }  // namespace emu

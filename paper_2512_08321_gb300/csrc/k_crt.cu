@@ -441,8 +441,10 @@ void launch_lrr(bool single, bool real, dim3 grid, int64_t m, int64_t n, const P
     if (single) crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
     else crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
   } else if (single) {
+    max_shared_carveout(crt_kernel<L, true, R, ROBUST>);
     crt_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   } else {
+    max_shared_carveout(crt_kernel<L, false, R, ROBUST>);
     crt_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
   }
 }

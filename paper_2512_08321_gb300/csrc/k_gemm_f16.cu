@@ -382,6 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   gemm_body<BN>(W, pl, status, true);
 }
 
+// The largest shared-memory carveout: an SM holding one block of this kernel
+// then keeps the rest of its shared memory (about 34 KB at 256-wide tiles) for
+// blocks of other kernels, instead of the smallest configuration that fits.
 template <int BN>
 cudaError_t set_smem_attrs() {
   static cudaError_t err = [] {
@@ -390,6 +393,12 @@ cudaError_t set_smem_attrs() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gemm_f16_grouped_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                Cfg<BN>::kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_f16_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               static_cast<int>(cudaSharedmemCarveoutMaxShared));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_f16_grouped_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               static_cast<int>(cudaSharedmemCarveoutMaxShared));
     return e;
   }();
   return err;

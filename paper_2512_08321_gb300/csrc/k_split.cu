@@ -394,8 +394,13 @@ cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
   // the common configuration (fp16 planes, 4 entries per thread) has the chunk count compiled in
   auto fixed = [&](auto nch_tag) {
     constexpr int NC = decltype(nch_tag)::value;
-    if (rs == 1) split_kernel<SINGLE, true, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
-    else split_kernel<SINGLE, false, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
+    if (rs == 1) {
+      max_shared_carveout(split_kernel<SINGLE, true, T, 4, R, NC>);
+      split_kernel<SINGLE, true, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
+    } else {
+      max_shared_carveout(split_kernel<SINGLE, false, T, 4, R, NC>);
+      split_kernel<SINGLE, false, T, 4, R, NC><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, conj, xexp, pl, kpad, P, prow);
+    }
   };
   bool done = false;
   if constexpr (std::is_same<T, __half>::value) {

@@ -92,6 +92,7 @@ bool valid(int key, int v) {
     case EMU_TUNE_CRT_ROWS: return v == 1 || v == 2 || v == 4;
     case EMU_TUNE_SPLIT_ELEMS: return v == 2 || v == 4;
     case EMU_TUNE_NBLOCK: return v == 0 || (v >= 128 && v % 128 == 0);
+    case EMU_TUNE_OVERLAP: return v == -1 || v == 0 || v == 1;
     default: return false;
   }
 }
@@ -104,6 +105,7 @@ void set(Tune& t, int key, int v) {
     case EMU_TUNE_CRT_ROWS: t.crt_rows = v; break;
     case EMU_TUNE_SPLIT_ELEMS: t.split_elems = v; break;
     case EMU_TUNE_NBLOCK: t.nblock = v; break;
+    case EMU_TUNE_OVERLAP: t.overlap = v; break;
     default: break;
   }
 }
@@ -158,7 +160,8 @@ Tune tune_for(int dtype, int N, int64_t m, int64_t n, int64_t k) {
   auto it = g_table.find(key_of(dtype, N, m, n, k));
   if (it == g_table.end()) return g_default;
   Tune t = it->second;
-  t.nblock = g_default.nblock;          // column blocking is a process setting, not tuned
+  t.nblock = g_default.nblock;          // column blocking and overlap are process settings, not tuned
+  t.overlap = g_default.overlap;
   return t;
 }
 
@@ -187,6 +190,7 @@ int emu_get_tuning(int key) {
     case EMU_TUNE_CRT_ROWS: return t.crt_rows;
     case EMU_TUNE_SPLIT_ELEMS: return t.split_elems;
     case EMU_TUNE_NBLOCK: return t.nblock;
+    case EMU_TUNE_OVERLAP: return t.overlap;
     default: return -1;
   }
 }

@@ -378,6 +378,7 @@ def emu_set_engine(engine, chunk_k=0):
 EMU_CRT_EXACT, EMU_CRT_PAPER_FP64 = 0, 1
 EMU_TUNE_TILE_N, EMU_TUNE_GROUP, EMU_TUNE_CHUNK_K, EMU_TUNE_CRT_ROWS, EMU_TUNE_SPLIT_ELEMS = 1, 2, 3, 4, 5
 EMU_TUNE_NBLOCK = 6
+EMU_TUNE_OVERLAP = 7
 
 
 def emu_set_tuning(key, value):
