@@ -111,7 +111,7 @@ emu_status_t emu_sgemm(emu_op_t transa, emu_op_t transb, int64_t m, int64_t n, i
  * arguments, layouts and results as the device forms; alpha/beta as there).
  * The inputs go through a library-owned device staging buffer in blocks: the
  * output columns in blocks, and the rows of op(A) in blocks (each about an
- * eighth, a multiple of 256 and at least 1024; one block when the dimension is
+ * eighth, a multiple of 256 and at least 2048; one block when the dimension is
  * at most 2048; narrower column blocks when column blocking below asks for
  * them).  A library-owned side stream brings op(B)'s (and, for pageable C with
  * beta != 0, C's) first column block, then op(A) block of rows by block of
