@@ -33,6 +33,8 @@ struct DeviceState {
   int* chosen_host = nullptr;
   void* stage = nullptr;       // staging of the host-buffer entry points
   size_t stage_bytes = 0;
+  void* tol_scr = nullptr;     // exponent sums and features of the tolerance path
+  size_t tol_scr_bytes = 0;
   // overlapped column blocks: the library's second stream and its events
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_split[2] = {}, ev_gemm[2] = {}, ev_crt[2] = {};
@@ -236,10 +238,14 @@ int64_t choose_nblock(const DeviceState* ds, int64_t m, int64_t n, int64_t k, in
 }
 
 // hooks (host-buffer calls): the operands move in blocks on another stream and
-// each step waits for the blocks it reads (BlockHooks).
+// each step waits for the blocks it reads (BlockHooks).  presums (fast scaling):
+// the exponent sums of op(A)'s rows and op(B)'s columns already formed
+// (launch_exponent_sums), so only the N-dependent last step of the exponent
+// rule runs here.
 emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, double ar, double ai,
                   const void* A, int64_t lda, const void* B, int64_t ldb, double br, double bi,
-                  void* C, int64_t ldc, int N, void* stream, const BlockHooks* hooks = nullptr) {
+                  void* C, int64_t ldc, int N, void* stream, const BlockHooks* hooks = nullptr,
+                  void* const* presums = nullptr) {
   emu_status_t s = check_common(ta, tb, m, n, k, lda, ldb, ldc, N, true);
   if (s != EMU_OK) return s;
   if (m == 0 || n == 0) return EMU_OK;
@@ -258,6 +264,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   int64_t nb;
   Layout L;
   const bool accurate = (g_scaling == EMU_SCALING_ACCURATE);
+  const bool presummed = presums && !accurate && k > 0;
   // overlapped column blocks: device-buffer calls in fast mode on the tcgen05 engine
   bool overlap = !hooks && (tn.overlap == 1 || (tn.overlap < 0 && dt.real)) && k > 0 && !accurate && fp16 &&
                  n >= 2048;
@@ -322,7 +329,9 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     auto width = [&](int64_t b) { return (n - b * nb) < nb ? (n - b * nb) : nb; };
     auto prepare = [&](int64_t b) -> cudaError_t {   // exponents and planes of block b's columns of B
       const int64_t j0 = b * nb, nj = width(b);
-      cudaError_t err = launch_exponents(dt.single, block_ptr(j0), nj, k, rsb, hsb, *pl, y + j0, scr, ax, dt.real);
+      cudaError_t err = presummed ? cudaSuccess
+                                  : launch_exponents(dt.single, block_ptr(j0), nj, k, rsb, hsb, *pl, y + j0, scr, ax,
+                                                     dt.real);
       if (err == cudaSuccess)
         err = launch_split(dt.single, conj_b, block_ptr(j0), nj, k, rsb, hsb, pls, y + j0, fp16, L.kpad, pbuf(b), ax,
                            tn.split_elems, dt.real);
@@ -337,8 +346,10 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
       if (r != EMU_OK) return r;
       return cuda_status(cudaEventRecord(ds->ev_crt[b & 1], ax));
     };
-    if (cudaEventRecord(ds->ev_start, st) != cudaSuccess || cudaStreamWaitEvent(ax, ds->ev_start, 0) != cudaSuccess ||
-        launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, ax, dt.real) != cudaSuccess ||
+    if ((presummed && (launch_exponent_finalize(m, presums[0], *pl, x, st) != cudaSuccess ||
+                       launch_exponent_finalize(n, presums[1], *pl, y, st) != cudaSuccess)) ||
+        cudaEventRecord(ds->ev_start, st) != cudaSuccess || cudaStreamWaitEvent(ax, ds->ev_start, 0) != cudaSuccess ||
+        (!presummed && launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, ax, dt.real) != cudaSuccess) ||
         launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, ax, tn.split_elems, dt.real) !=
             cudaSuccess ||
         prepare(0) != cudaSuccess)
@@ -405,6 +416,10 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     if (launch_accu_finalize(m, emA, fA, MA, *pl, x, st) != cudaSuccess ||
         launch_accu_finalize(n, emB, fB, NB, *pl, y, st) != cudaSuccess)
       return EMU_ERR_CUDA;
+  } else if (presummed) {
+    if (launch_exponent_finalize(m, presums[0], *pl, x, st) != cudaSuccess ||
+        launch_exponent_finalize(n, presums[1], *pl, y, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
   } else if (!rows_piped) {
     if ((e = launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, st, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
@@ -423,7 +438,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
       if ((e = cudaMemsetAsync(res, 0, static_cast<size_t>(ppm * N) * nj * L.ldr, st)) != cudaSuccess)
         return EMU_ERR_CUDA;
     } else {
-      if (!accurate &&
+      if (!accurate && !presummed &&
           (e = launch_exponents(dt.single, Bj, nj, k, rsb, hsb, *pl, yj, scr, st, dt.real)) != cudaSuccess)
         return EMU_ERR_CUDA;
       phase(1, st);
@@ -829,14 +844,13 @@ emu_status_t emu_moduli_features(int is_single, emu_op_t transa, emu_op_t transb
   s = emu::device_init(emu::current_device(), ds);
   if (s != EMU_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t rmax = m > n ? m : n;
   void* scr = nullptr;
-  if (cudaMallocAsync(&scr, emu::features_scratch_bytes(rmax > 0 ? rmax : 1), st) != cudaSuccess) return EMU_ERR_ALLOC;
+  if (cudaMallocAsync(&scr, emu::features_scratch_bytes(m, n), st) != cudaSuccess) return EMU_ERR_ALLOC;
   int64_t rsa, hsa, rsb, hsb;
   emu::strides_a(transa, lda, rsa, hsa);
   emu::strides_b(transb, ldb, rsb, hsb);
-  const cudaError_t e = emu::launch_features(is_single != 0, A, m, rsa, hsa, B, n, rsb, hsb, k, target,
-                                             *emu::get_plan(EMU_MIN_MODULI), features, scr, st);
+  const cudaError_t e =
+      emu::launch_features(is_single != 0, A, m, rsa, hsa, B, n, rsb, hsb, k, target, features, scr, st);
   cudaFreeAsync(scr, st);
   return emu::cuda_status(e);
 }
@@ -853,14 +867,32 @@ static emu_status_t gemm_tol(int single, emu_op_t ta, emu_op_t tb, int64_t m, in
     s = emu::device_init(emu::current_device(), ds);
     if (s != EMU_OK) return s;
     if (ds->mlp_loaded) {
+      // The features come from the exponent passes the GEMM needs anyway (their
+      // row maxima and sums do not depend on N): formed once here, with the
+      // histograms, and handed to the GEMM, which adds only the N-dependent step.
       cudaStream_t st = static_cast<cudaStream_t>(stream);
+      const size_t need = emu::features_scratch_bytes(m, n);
       {
         std::lock_guard<std::mutex> lk(emu::g_mu);
         if (!ds->feat && cudaMalloc(&ds->feat, 64 * sizeof(float)) != cudaSuccess) return EMU_ERR_ALLOC;
         if (!ds->chosen_host && cudaMallocHost(&ds->chosen_host, sizeof(int)) != cudaSuccess) return EMU_ERR_ALLOC;
+        if (ds->tol_scr_bytes < need) {
+          if (ds->tol_scr) cudaFree(ds->tol_scr);
+          ds->tol_scr = nullptr;
+          ds->tol_scr_bytes = 0;
+          if (cudaMalloc(&ds->tol_scr, need) != cudaSuccess) {
+            cudaGetLastError();
+            return EMU_ERR_ALLOC;
+          }
+          ds->tol_scr_bytes = need;
+        }
       }
-      s = emu_moduli_features(single, ta, tb, m, n, k, A, lda, B, ldb, target, ds->feat, stream);
-      if (s != EMU_OK) return s;
+      int64_t rsa, hsa, rsb, hsb;
+      emu::strides_a(ta, lda, rsa, hsa);
+      emu::strides_b(tb, ldb, rsb, hsb);
+      if (emu::launch_features(single != 0, A, m, rsa, hsa, B, n, rsb, hsb, k, target, ds->feat, ds->tol_scr, st) !=
+          cudaSuccess)
+        return EMU_ERR_CUDA;
       int* dn = reinterpret_cast<int*>(ds->feat + 48);
       if (emu::launch_mlp_choose(ds->mlp, ds->feat, 0.99f, dn, st) != cudaSuccess) return EMU_ERR_CUDA;
       if (cudaMemcpyAsync(ds->chosen_host, dn, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -868,6 +900,10 @@ static emu_status_t gemm_tol(int single, emu_op_t ta, emu_op_t tb, int64_t m, in
         return EMU_ERR_CUDA;
       const int Nm = *ds->chosen_host;
       if (Nm >= EMU_MIN_MODULI && Nm <= EMU_MAX_MODULI) N = Nm;   // else: the a priori rule
+      if (n_used) *n_used = N;
+      void* const presums[2] = {ds->tol_scr, static_cast<char*>(ds->tol_scr) + emu::exponents_scratch_bytes(m)};
+      return emu::gemm(emu::Dt{single != 0, false}, ta, tb, m, n, k, ar, ai, A, lda, B, ldb, br, bi, C, ldc, N,
+                       stream, nullptr, presums);
     }
   }
   if (n_used) *n_used = N;

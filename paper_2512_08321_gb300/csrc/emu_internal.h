@@ -195,10 +195,19 @@ cudaError_t launch_mlp_backward(const float* th, const float* X, const float* Y,
                                 float* loss, cudaStream_t st);
 cudaError_t launch_mlp_adam(float* th, const float* g, float* m, float* v, int step, float lr, cudaStream_t st);
 cudaError_t launch_mlp_choose(const float* th, const float* x, float threshold, int* out, cudaStream_t st);
-size_t features_scratch_bytes(int64_t rows);
+// The N-independent part of the exponents (passes 1 and 2: row maxima, flags,
+// quantised sums of squares) into a scratch of exponents_scratch_bytes(rows),
+// with the moduli-selection histogram when hist is given (complex only); the
+// exponents of a plan then need only launch_exponent_finalize.
+cudaError_t launch_exponent_sums(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs,
+                                 int64_t hs, void* scratch, unsigned long long* hist, cudaStream_t st);
+cudaError_t launch_exponent_finalize(int64_t rows, void* scratch, const Plan& pl, int16_t* xout, cudaStream_t st);
+// features of the moduli-selection network; the scratch (features_scratch_bytes(m, n))
+// keeps A's exponent sums and then B's
+size_t features_scratch_bytes(int64_t m, int64_t n);
 cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, int64_t hsa, const void* B,
-                            int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, const Plan& pl,
-                            float* feat, void* scratch, cudaStream_t st);
+                            int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, float* feat,
+                            void* scratch, cudaStream_t st);
 extern int g_f16_group;
 
 // Block hooks of a host-buffer call (host.cu).  The output columns are

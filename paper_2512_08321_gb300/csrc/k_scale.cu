@@ -216,6 +216,86 @@ __device__ __forceinline__ void exp_sum_block(const void* __restrict__ X, int64_
   if (acc) atomicAdd(sum + r, acc);
 }
 
+// ---- pass 2 for the moduli-selection features: the sums of exp_sum_block and,
+// over every entry of every row (flagged and zero rows included), the 16-bin
+// histogram of exponent spans d = e_r - ilogb|v| (zero and non-finite
+// entries, and entries of zero rows: bin 15).  Each thread counts in two
+// words, 8 bits a bin, emptied into 16 totals every 127 pairs of entries;
+// warps and then the block add the totals before one global add per bin.
+template <bool S>
+__device__ __forceinline__ int span_bin(typename Bits<S>::U u, int eo) {
+  return (u && !nonfinite<S>(u) && eo) ? min(eo - ilogb_off<S>(u), 15) : 15;
+}
+
+struct SpanCounts {
+  unsigned long long lo = 0, hi = 0;   // bins 0..7 and 8..15, 8 bits each
+  unsigned int tot[16] = {};
+  __device__ __forceinline__ void add(int bin) {
+    if (bin < 8) lo += 1ull << (8 * bin);
+    else hi += 1ull << (8 * (bin - 8));
+  }
+  __device__ __forceinline__ void empty() {
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      tot[b] += static_cast<unsigned int>((lo >> (8 * b)) & 0xFFu);
+      tot[b + 8] += static_cast<unsigned int>((hi >> (8 * b)) & 0xFFu);
+    }
+    lo = hi = 0;
+  }
+};
+
+template <bool S, bool ROWS_CONTIG>
+__global__ void __launch_bounds__(kThreads) exp_sum_hist_kernel(const void* __restrict__ X, int64_t rows, int64_t k,
+                                                                int64_t rs, int64_t hs, const int* __restrict__ emax,
+                                                                const unsigned int* __restrict__ flag,
+                                                                unsigned long long* __restrict__ sum,
+                                                                unsigned long long* __restrict__ hist) {
+  using B = Bits<S>;
+  __shared__ unsigned int block_hist[16];
+  if (threadIdx.x < 16) block_hist[threadIdx.x] = 0;
+  __syncthreads();
+  SpanCounts cnt;
+  unsigned long long acc = 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ROWS_CONTIG ? static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x
+                                : static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+  const bool valid = r < rows;
+  const int eo = valid ? emax[r] : 0;
+  const bool summing = valid && !flag[r] && eo != 0;
+  const int e = eo - 2048;
+  const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
+  const int64_t h1 = min(k, h0 + kChunkH);
+  if (valid) {
+    int since = 0;
+    for (int64_t h = ROWS_CONTIG ? h0 : h0 + lane; h < h1; h += ROWS_CONTIG ? 1 : 32) {
+      typename B::U ua, ub;
+      load_mag<S, false>(X, ROWS_CONTIG ? r + h * hs : r * rs + h, ua, ub);
+      if (summing) {
+        const unsigned long long a = ceil_q<S>(ua, e), b = ceil_q<S>(ub, e);
+        acc += a * a + b * b;
+      }
+      cnt.add(span_bin<S>(ua, eo));
+      cnt.add(span_bin<S>(ub, eo));
+      if (++since == 127) {
+        cnt.empty();
+        since = 0;
+      }
+    }
+  }
+  cnt.empty();
+  if (!ROWS_CONTIG)
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (summing && acc && (ROWS_CONTIG || lane == 0)) atomicAdd(sum + r, acc);
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    const unsigned int v = __reduce_add_sync(0xffffffffu, cnt.tot[b]);
+    if (lane == 0 && v) atomicAdd(&block_hist[b], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 16 && block_hist[threadIdx.x])
+    atomicAdd(&hist[threadIdx.x], static_cast<unsigned long long>(block_hist[threadIdx.x]));
+}
+
 template <bool S, bool ROWS_CONTIG, bool R>
 __global__ void __launch_bounds__(kThreads) exp_sum_kernel(const void* __restrict__ X,
                                                            int64_t rows, int64_t k, int64_t rs,
@@ -288,33 +368,63 @@ __global__ void exp_finalize_grouped(const ExpSeg* __restrict__ segs, int nseg,
   g.xout[i] = finalize_row(pl, g.emax[i], g.flag[i], g.sum[i]);
 }
 
+// scratch of rows: emax (int), flag (uint) and sum (uint64) arrays, each padded to 64 rows
+struct ExpScratch {
+  int* emax;
+  unsigned int* flag;
+  unsigned long long* sum;
+  ExpScratch(void* scratch, int64_t rows)
+      : emax(static_cast<int*>(scratch)),
+        flag(reinterpret_cast<unsigned int*>(emax + round_up(rows, 64))),
+        sum(reinterpret_cast<unsigned long long*>(flag + round_up(rows, 64))) {}
+};
+
+// passes 1 and 2 (the N-independent part of the exponents), with the
+// features' histogram when hist is given (complex input only)
 template <bool S, bool R = false>
-cudaError_t launch_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
-                     const Plan& pl, int16_t* xout, void* scratch, cudaStream_t st) {
-  int* emax = static_cast<int*>(scratch);
-  unsigned int* flag = reinterpret_cast<unsigned int*>(emax + round_up(rows, 64));
-  unsigned long long* sum = reinterpret_cast<unsigned long long*>(flag + round_up(rows, 64));
+cudaError_t launch_sums_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs, void* scratch,
+                          unsigned long long* hist, cudaStream_t st) {
+  const ExpScratch sc(scratch, rows);
   cudaError_t err = cudaMemsetAsync(scratch, 0, exponents_scratch_bytes(rows), st);
   if (err != cudaSuccess) return err;
   const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
   if (ychunks > 0) {
     const bool rows_contig = (rs == 1);
-    if (rows_contig) {
-      dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
-      exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
-      exp_sum_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
-      count_launches(2);
-    } else {
-      dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
-      exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
-      exp_sum_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, sum);
-      count_launches(2);
+    const dim3 grid(static_cast<unsigned int>(rows_contig ? (rows + kThreads - 1) / kThreads : (rows + 7) / 8),
+                    ychunks);
+    if (rows_contig) exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag);
+    else exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag);
+    if constexpr (!R) {
+      if (hist) {
+        if (rows_contig)
+          exp_sum_hist_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, hist);
+        else
+          exp_sum_hist_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, hist);
+        count_launches(2);
+        return cudaGetLastError();
+      }
     }
+    if (rows_contig) exp_sum_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum);
+    else exp_sum_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum);
+    count_launches(2);
   }
-  exp_finalize_kernel<<<static_cast<unsigned int>((rows + 255) / 256), 256, 0, st>>>(
-      rows, emax, flag, sum, pl, xout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_t(int64_t rows, void* scratch, const Plan& pl, int16_t* xout, cudaStream_t st) {
+  const ExpScratch sc(scratch, rows);
+  exp_finalize_kernel<<<static_cast<unsigned int>((rows + 255) / 256), 256, 0, st>>>(rows, sc.emax, sc.flag, sc.sum,
+                                                                                    pl, xout);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <bool S, bool R = false>
+cudaError_t launch_t(const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
+                     const Plan& pl, int16_t* xout, void* scratch, cudaStream_t st) {
+  const cudaError_t err = launch_sums_t<S, R>(X, rows, k, rs, hs, scratch, nullptr, st);
+  if (err != cudaSuccess) return err;
+  return launch_finalize_t(rows, scratch, pl, xout, st);
 }
 
 // ---- accurate mode (Section III-B, eqs. mu-accu / nu-accu): x_r = 5 - e_r + E_r with
@@ -354,51 +464,6 @@ cudaError_t launch_max_t(const void* X, int64_t rows, int64_t k, int64_t rs, int
 }
 
 // ---- features of the moduli-selection network
-// 16-bin histogram of exponent spans d = e_r - ilogb|v| (zero entries: bin 15)
-template <bool S, bool ROWS_CONTIG>
-__global__ void __launch_bounds__(kThreads) feat_hist_kernel(const typename Bits<S>::V* __restrict__ X, int64_t rows,
-                                                             int64_t k, int64_t rs, int64_t hs,
-                                                             const int* __restrict__ emax,
-                                                             unsigned long long* __restrict__ hist) {
-  using B = Bits<S>;
-  __shared__ unsigned int h[16];
-  if (threadIdx.x < 16) h[threadIdx.x] = 0;
-  __syncthreads();
-  auto add = [&](typename B::U u, int e_off) {
-    int bin = 15;
-    if (u && !nonfinite<S>(u) && e_off) bin = min(e_off - ilogb_off<S>(u), 15);
-    atomicAdd(&h[bin], 1u);
-  };
-  if (ROWS_CONTIG) {
-    const int64_t r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
-    if (r < rows) {
-      const int e = emax[r];
-      const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
-      const int64_t h1 = min(k, h0 + kChunkH);
-      for (int64_t c = h0; c < h1; ++c) {
-        const typename B::V v = X[r + c * hs];
-        add(B::re(v), e);
-        add(B::im(v), e);
-      }
-    }
-  } else {
-    const int lane = threadIdx.x & 31;
-    const int64_t r = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
-    if (r < rows) {
-      const int e = emax[r];
-      const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
-      const int64_t h1 = min(k, h0 + kChunkH);
-      for (int64_t c = h0 + lane; c < h1; c += 32) {
-        const typename B::V v = X[r * rs + c];
-        add(B::re(v), e);
-        add(B::im(v), e);
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 16 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], static_cast<unsigned long long>(h[threadIdx.x]));
-}
-
 // mean and max over rows of L = 0.5 log2(max(S, 1)) - 15
 __global__ void __launch_bounds__(1024) feat_stats_kernel(const unsigned long long* __restrict__ sum, int64_t rows,
                                                           float* __restrict__ out) {
@@ -446,61 +511,53 @@ __global__ void feat_assemble_kernel(const unsigned long long* __restrict__ hist
   else if (i == 38) f[i] = single;
 }
 
-template <bool S>
-cudaError_t features_side(const void* Xv, int64_t rows, int64_t k, int64_t rs, int64_t hs, const Plan& pl,
-                          char* scr, unsigned long long* hist, float* stats, int16_t* xdummy, cudaStream_t st) {
-  using V = typename Bits<S>::V;
-  const V* X = static_cast<const V*>(Xv);
-  cudaError_t e = launch_t<S>(Xv, rows, k, rs, hs, pl, xdummy, scr, st);   // emax, flag, sums (+ exponents)
-  if (e != cudaSuccess) return e;
-  const int* emax = reinterpret_cast<const int*>(scr);
-  const unsigned long long* sum =
-      reinterpret_cast<const unsigned long long*>(scr + 8 * round_up(rows, 64));
-  const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
-  if (ychunks > 0) {
-    if (rs == 1) {
-      dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
-      feat_hist_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, hist);
-    } else {
-      dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
-      feat_hist_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, hist);
-    }
-    count_launches(1);
-  }
-  feat_stats_kernel<<<1, 1024, 0, st>>>(sum, rows, stats);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
-size_t features_scratch_bytes(int64_t rows) {
-  return exponents_scratch_bytes(rows) + static_cast<size_t>(round_up(rows, 64)) * 2 + 512;
+// Scratch of emu_moduli_features / the tolerance path: the exponent sums of A
+// (m rows) and of B (n columns), then 32 histogram bins and 4 statistics.
+size_t features_scratch_bytes(int64_t m, int64_t n) {
+  return exponents_scratch_bytes(m) + exponents_scratch_bytes(n) + 32 * sizeof(unsigned long long) + 64;
 }
 
-// Feature vector (39 floats) of op(A) (m x k) and op(B) (k x n) into feat.
+cudaError_t launch_exponent_sums(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs,
+                                 int64_t hs, void* scratch, unsigned long long* hist, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  if (real && hist) return cudaErrorInvalidValue;
+  if (real)
+    return single ? launch_sums_t<true, true>(X, rows, k, rs, hs, scratch, nullptr, st)
+                  : launch_sums_t<false, true>(X, rows, k, rs, hs, scratch, nullptr, st);
+  return single ? launch_sums_t<true>(X, rows, k, rs, hs, scratch, hist, st)
+                : launch_sums_t<false>(X, rows, k, rs, hs, scratch, hist, st);
+}
+
+cudaError_t launch_exponent_finalize(int64_t rows, void* scratch, const Plan& pl, int16_t* xout, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  return launch_finalize_t(rows, scratch, pl, xout, st);
+}
+
+// Feature vector (39 floats) of op(A) (m x k) and op(B) (k x n) into feat.  The
+// exponent sums of both operands stay in the scratch (features_scratch_bytes(m,
+// n)), A's first, then B's, ready for launch_exponent_finalize.
 cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, int64_t hsa, const void* B,
-                            int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, const Plan& pl,
-                            float* feat, void* scratch, cudaStream_t st) {
-  const int64_t rmax = m > n ? m : n;
+                            int64_t n, int64_t rsb, int64_t hsb, int64_t k, double target, float* feat,
+                            void* scratch, cudaStream_t st) {
   char* scr = static_cast<char*>(scratch);
-  int16_t* xdummy = reinterpret_cast<int16_t*>(scr + exponents_scratch_bytes(rmax));
-  unsigned long long* hist = reinterpret_cast<unsigned long long*>(
-      scr + exponents_scratch_bytes(rmax) + round_up(rmax, 64) * 2);
+  void* scrA = scr;
+  void* scrB = scr + exponents_scratch_bytes(m);
+  unsigned long long* hist =
+      reinterpret_cast<unsigned long long*>(scr + exponents_scratch_bytes(m) + exponents_scratch_bytes(n));
   float* stats = reinterpret_cast<float*>(hist + 32);
   cudaError_t e = cudaMemsetAsync(hist, 0, 32 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = launch_exponent_sums(single, false, A, m, k, rsa, hsa, scrA, hist, st);
+  if (e == cudaSuccess) e = launch_exponent_sums(single, false, B, n, k, rsb, hsb, scrB, hist + 16, st);
   if (e != cudaSuccess) return e;
-  e = single ? features_side<true>(A, m, k, rsa, hsa, pl, scr, hist, stats, xdummy, st)
-             : features_side<false>(A, m, k, rsa, hsa, pl, scr, hist, stats, xdummy, st);
-  if (e != cudaSuccess) return e;
-  e = single ? features_side<true>(B, n, k, rsb, hsb, pl, scr, hist + 16, stats + 2, xdummy, st)
-             : features_side<false>(B, n, k, rsb, hsb, pl, scr, hist + 16, stats + 2, xdummy, st);
-  if (e != cudaSuccess) return e;
+  feat_stats_kernel<<<1, 1024, 0, st>>>(ExpScratch(scrA, m).sum, m, stats);
+  feat_stats_kernel<<<1, 1024, 0, st>>>(ExpScratch(scrB, n).sum, n, stats + 2);
   const double ta = m > 0 && k > 0 ? 2.0 * m * k : 1.0, tb = n > 0 && k > 0 ? 2.0 * k * n : 1.0;
   const float logk = static_cast<float>(std::log2(static_cast<double>(k > 1 ? k : 1)) / 17.0);
   const float tgt = static_cast<float>(-std::log10(target) / 16.0);
   feat_assemble_kernel<<<1, 64, 0, st>>>(hist, stats, ta, tb, logk, tgt, single ? 1.0f : 0.0f, feat);
-  count_launches(1);
+  count_launches(3);
   return cudaGetLastError();
 }
 
