@@ -296,7 +296,8 @@ emu_status_t emu_set_workspace(void* ptr, size_t bytes);
 
 /* Select the residue-product engine (default EMU_ENGINE_AUTO = F16) and the
  * k chunk after which the F16 engine reduces its accumulator (multiple of 64,
- * 64..960; 0 keeps the default 512). */
+ * 64..960; 0 keeps the default 960, the largest that keeps the FP32 sums
+ * exact). */
 emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 
 /* Launch-configuration knobs of emu_zgemm/cgemm/dgemm/sgemm (no effect on results):

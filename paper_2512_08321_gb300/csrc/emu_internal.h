@@ -91,7 +91,8 @@ cudaError_t launch_accu_finalize(int64_t rows, const int* emax, const unsigned i
 struct Tune {
   int tile_n = 256;      // residue products: output rows per tile (64, 128, 256)
   int group = 16;        // residue products: tile rasterisation group
-  int chunk_k = 512;     // residue products: k between in-TMEM reductions (64..960)
+  int chunk_k = 960;     // residue products: k between in-TMEM reductions (64..960; 960 the largest
+                         // exact one: 960 products of at most 2^14 plus a residue stay below 2^24)
   int crt_rows = 4;      // CRT: rows per thread (1, 2, 4)
   int split_elems = 4;   // split: entries per thread (2, 4)
   int nblock = 0;        // output columns per block (0: automatic, by workspace size)

@@ -270,7 +270,7 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
     const bool big = static_cast<double>(m) * n * k * num_moduli > 4e13;
     const std::vector<int> tiles = m <= 256 ? std::vector<int>{64, 128, 256} : std::vector<int>{128, 256};
     const std::vector<int> groups = big ? std::vector<int>{16, 32} : std::vector<int>{8, 16, 32};
-    const std::vector<int> chunks = big ? std::vector<int>{512} : std::vector<int>{512, 960};
+    const std::vector<int> chunks = big ? std::vector<int>{960} : std::vector<int>{960, 512};
     if (prepare_gemm_f16() != cudaSuccess) ok = false;
     for (int tn : tiles)
       for (int g : groups)

@@ -22,7 +22,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 KNOBS = [(emu.EMU_TUNE_TILE_N, v) for v in (64, 128, 256)] + \
         [(emu.EMU_TUNE_GROUP, v) for v in (1, 3, 32)] + \
-        [(emu.EMU_TUNE_CHUNK_K, v) for v in (64, 960)] + \
+        [(emu.EMU_TUNE_CHUNK_K, v) for v in (64, 512, 960)] + \
         [(emu.EMU_TUNE_CRT_ROWS, v) for v in (1, 2, 4)] + \
         [(emu.EMU_TUNE_SPLIT_ELEMS, v) for v in (2, 4)]
 
