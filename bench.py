@@ -674,7 +674,7 @@ def run_grouped(args, wl, world, rank, local):
                         "timing": "grouped phases run once more outside the graph with events"},
            "phases_ms": phases, "gpu_launches": int(per_replay * args.steps),
            "clocks": clk.summary()}
-    if rank == 0:
+    if rank == 0 and not args.no_plain:
         # the plain per-problem loop on the same data (one emu_zgemm per problem)
         def loop():
             for (m, n, k), (A, B, C) in zip(shapes, tensors):
@@ -693,6 +693,7 @@ def run_grouped(args, wl, world, rank, local):
         out["plain_loop"] = {"ms": lms, "tflops": flops / (lms * 1e-3) * 1e-12,
                              "speedup_of_grouped": lms / ms,
                              "launches": 10 * len(shapes)}
+    if rank == 0:
         print(json.dumps(out), flush=True)
     emu.emu_grouped_destroy(plan)
     if dist:
