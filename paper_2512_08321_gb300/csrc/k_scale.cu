@@ -22,7 +22,7 @@
 namespace emu {
 namespace {
 
-constexpr int kChunkH = 512;      // h handled by one block in the row-contiguous form
+constexpr int kChunkH = 512;      // h handled by one block (grouped forms; the most for single calls)
 constexpr int kThreads = 256;
 
 template <bool SINGLE>
@@ -128,7 +128,8 @@ __device__ __forceinline__ int exponent_from_sum(const Plan& pl, unsigned long l
 template <bool S, bool ROWS_CONTIG, bool R = false>
 __device__ __forceinline__ void exp_max_block(const void* __restrict__ X, int64_t rows, int64_t k,
                                               int64_t rs, int64_t hs, int* __restrict__ emax,
-                                              unsigned int* __restrict__ flag, int64_t rb, int64_t hc) {
+                                              unsigned int* __restrict__ flag, int64_t rb, int64_t hc,
+                                              int64_t chunk) {
   using B = Bits<S>;
   int best = 0;
   bool bad = false;
@@ -136,8 +137,8 @@ __device__ __forceinline__ void exp_max_block(const void* __restrict__ X, int64_
   if (ROWS_CONTIG) {
     r = rb * kThreads + threadIdx.x;
     if (r >= rows) return;
-    const int64_t h0 = hc * kChunkH;
-    const int64_t h1 = min(k, h0 + kChunkH);
+    const int64_t h0 = hc * chunk;
+    const int64_t h1 = min(k, h0 + chunk);
     for (int64_t h = h0; h < h1; ++h) {
       typename B::U a, b;
       load_mag<S, R>(X, r + h * hs, a, b);
@@ -149,8 +150,8 @@ __device__ __forceinline__ void exp_max_block(const void* __restrict__ X, int64_
     const int lane = threadIdx.x & 31;
     r = rb * (kThreads / 32) + (threadIdx.x >> 5);
     if (r >= rows) return;
-    const int64_t h0 = hc * kChunkH;
-    const int64_t h1 = min(k, h0 + kChunkH);
+    const int64_t h0 = hc * chunk;
+    const int64_t h1 = min(k, h0 + chunk);
     for (int64_t h = h0 + lane; h < h1; h += 32) {
       typename B::U a, b;
       load_mag<S, R>(X, r * rs + h, a, b);
@@ -172,8 +173,8 @@ template <bool S, bool ROWS_CONTIG, bool R>
 __global__ void __launch_bounds__(kThreads) exp_max_kernel(const void* __restrict__ X,
                                                            int64_t rows, int64_t k, int64_t rs,
                                                            int64_t hs, int* __restrict__ emax,
-                                                           unsigned int* __restrict__ flag) {
-  exp_max_block<S, ROWS_CONTIG, R>(X, rows, k, rs, hs, emax, flag, blockIdx.x, blockIdx.y);
+                                                           unsigned int* __restrict__ flag, int64_t chunk) {
+  exp_max_block<S, ROWS_CONTIG, R>(X, rows, k, rs, hs, emax, flag, blockIdx.x, blockIdx.y, chunk);
 }
 
 // ---- pass 2: exact quantised sum of squares (one block)
@@ -181,7 +182,8 @@ template <bool S, bool ROWS_CONTIG, bool R = false>
 __device__ __forceinline__ void exp_sum_block(const void* __restrict__ X, int64_t rows, int64_t k,
                                               int64_t rs, int64_t hs, const int* __restrict__ emax,
                                               const unsigned int* __restrict__ flag,
-                                              unsigned long long* __restrict__ sum, int64_t rb, int64_t hc) {
+                                              unsigned long long* __restrict__ sum, int64_t rb, int64_t hc,
+                                              int64_t chunk) {
   using B = Bits<S>;
   unsigned long long acc = 0;
   int64_t r;
@@ -189,8 +191,8 @@ __device__ __forceinline__ void exp_sum_block(const void* __restrict__ X, int64_
     r = rb * kThreads + threadIdx.x;
     if (r >= rows || flag[r] || emax[r] == 0) return;
     const int e = emax[r] - 2048;
-    const int64_t h0 = hc * kChunkH;
-    const int64_t h1 = min(k, h0 + kChunkH);
+    const int64_t h0 = hc * chunk;
+    const int64_t h1 = min(k, h0 + chunk);
     for (int64_t h = h0; h < h1; ++h) {
       typename B::U ua, ub;
       load_mag<S, R>(X, r + h * hs, ua, ub);
@@ -202,8 +204,8 @@ __device__ __forceinline__ void exp_sum_block(const void* __restrict__ X, int64_
     r = rb * (kThreads / 32) + (threadIdx.x >> 5);
     if (r >= rows || flag[r] || emax[r] == 0) return;
     const int e = emax[r] - 2048;
-    const int64_t h0 = hc * kChunkH;
-    const int64_t h1 = min(k, h0 + kChunkH);
+    const int64_t h0 = hc * chunk;
+    const int64_t h1 = min(k, h0 + chunk);
     for (int64_t h = h0 + lane; h < h1; h += 32) {
       typename B::U ua, ub;
       load_mag<S, R>(X, r * rs + h, ua, ub);
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) exp_sum_hist_kernel(const void* __re
                                                                 int64_t rs, int64_t hs, const int* __restrict__ emax,
                                                                 const unsigned int* __restrict__ flag,
                                                                 unsigned long long* __restrict__ sum,
-                                                                unsigned long long* __restrict__ hist) {
+                                                                unsigned long long* __restrict__ hist, int64_t chunk) {
   using B = Bits<S>;
   __shared__ unsigned int block_hist[16];
   if (threadIdx.x < 16) block_hist[threadIdx.x] = 0;
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(kThreads) exp_sum_hist_kernel(const void* __re
   const int eo = valid ? emax[r] : 0;
   const bool summing = valid && !flag[r] && eo != 0;
   const int e = eo - 2048;
-  const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kChunkH;
-  const int64_t h1 = min(k, h0 + kChunkH);
+  const int64_t h0 = static_cast<int64_t>(blockIdx.y) * chunk;
+  const int64_t h1 = min(k, h0 + chunk);
   if (valid) {
     int since = 0;
     for (int64_t h = ROWS_CONTIG ? h0 : h0 + lane; h < h1; h += ROWS_CONTIG ? 1 : 32) {
@@ -301,8 +303,8 @@ __global__ void __launch_bounds__(kThreads) exp_sum_kernel(const void* __restric
                                                            int64_t rows, int64_t k, int64_t rs,
                                                            int64_t hs, const int* __restrict__ emax,
                                                            const unsigned int* __restrict__ flag,
-                                                           unsigned long long* __restrict__ sum) {
-  exp_sum_block<S, ROWS_CONTIG, R>(X, rows, k, rs, hs, emax, flag, sum, blockIdx.x, blockIdx.y);
+                                                           unsigned long long* __restrict__ sum, int64_t chunk) {
+  exp_sum_block<S, ROWS_CONTIG, R>(X, rows, k, rs, hs, emax, flag, sum, blockIdx.x, blockIdx.y, chunk);
 }
 
 __device__ __forceinline__ int16_t finalize_row(const Plan& pl, int em, unsigned int fl, unsigned long long S) {
@@ -336,9 +338,11 @@ __global__ void __launch_bounds__(kThreads) exp_max_grouped(const ExpSeg* __rest
   const long long local = blockIdx.x - g.block_begin;
   const void* X = g.X;
   if (g.rows_contig)
-    exp_max_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks);
+    exp_max_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks,
+                          kChunkH);
   else
-    exp_max_block<S, false>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks);
+    exp_max_block<S, false>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, local / g.hchunks, local % g.hchunks,
+                          kChunkH);
 }
 
 template <bool S>
@@ -347,9 +351,11 @@ __global__ void __launch_bounds__(kThreads) exp_sum_grouped(const ExpSeg* __rest
   const long long local = blockIdx.x - g.block_begin;
   const void* X = g.X;
   if (g.rows_contig)
-    exp_sum_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks);
+    exp_sum_block<S, true>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks,
+                          kChunkH);
   else
-    exp_sum_block<S, false>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks);
+    exp_sum_block<S, false>(X, g.rows, g.k, g.rs, g.hs, g.emax, g.flag, g.sum, local / g.hchunks, local % g.hchunks,
+                          kChunkH);
 }
 
 // one thread per row of every segment; row_begin holds the prefix sums of rows
@@ -366,6 +372,26 @@ __global__ void exp_finalize_grouped(const ExpSeg* __restrict__ segs, int nseg,
   const ExpSeg& g = segs[lo];
   const long long i = r - row_begin[lo];
   g.xout[i] = finalize_row(pl, g.emax[i], g.flag[i], g.sum[i]);
+}
+
+// h per block for a single call: kChunkH, halved (down to 64) while the grid
+// would hold fewer than 8 blocks per SM, so that short-and-wide operands (few
+// row blocks) still keep every SM's loads in flight
+int64_t num_sms() {
+  static std::once_flag once;
+  static int sms = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  return sms > 0 ? sms : 1;
+}
+
+int64_t pick_chunk(int64_t rowblocks, int64_t k) {
+  int64_t chunk = kChunkH;
+  while (chunk > 64 && rowblocks * ((k + chunk - 1) / chunk) < 8 * num_sms()) chunk /= 2;
+  return chunk;
 }
 
 // scratch of rows: emax (int), flag (uint) and sum (uint64) arrays, each padded to 64 rows
@@ -387,25 +413,31 @@ cudaError_t launch_sums_t(const void* X, int64_t rows, int64_t k, int64_t rs, in
   const ExpScratch sc(scratch, rows);
   cudaError_t err = cudaMemsetAsync(scratch, 0, exponents_scratch_bytes(rows), st);
   if (err != cudaSuccess) return err;
-  const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
-  if (ychunks > 0) {
+  if (k > 0) {
     const bool rows_contig = (rs == 1);
-    const dim3 grid(static_cast<unsigned int>(rows_contig ? (rows + kThreads - 1) / kThreads : (rows + 7) / 8),
-                    ychunks);
-    if (rows_contig) exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag);
-    else exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag);
+    const int64_t rowblocks = rows_contig ? (rows + kThreads - 1) / kThreads : (rows + 7) / 8;
+    const int64_t chunk = pick_chunk(rowblocks, k);
+    const dim3 grid(static_cast<unsigned int>(rowblocks), static_cast<unsigned int>((k + chunk - 1) / chunk));
+    if (rows_contig)
+      exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, chunk);
+    else
+      exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, chunk);
     if constexpr (!R) {
       if (hist) {
         if (rows_contig)
-          exp_sum_hist_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, hist);
+          exp_sum_hist_kernel<S, true><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, hist,
+                                                                  chunk);
         else
-          exp_sum_hist_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, hist);
+          exp_sum_hist_kernel<S, false><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, hist,
+                                                                   chunk);
         count_launches(2);
         return cudaGetLastError();
       }
     }
-    if (rows_contig) exp_sum_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum);
-    else exp_sum_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum);
+    if (rows_contig)
+      exp_sum_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, chunk);
+    else
+      exp_sum_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, sc.emax, sc.flag, sc.sum, chunk);
     count_launches(2);
   }
   return cudaGetLastError();
@@ -450,15 +482,12 @@ cudaError_t launch_max_t(const void* X, int64_t rows, int64_t k, int64_t rs, int
   cudaError_t e = cudaMemsetAsync(emax, 0, static_cast<size_t>(rows) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, static_cast<size_t>(rows) * 4, st);
   if (e != cudaSuccess) return e;
-  const unsigned int ychunks = static_cast<unsigned int>(k > 0 ? (k + kChunkH - 1) / kChunkH : 0);
-  if (ychunks == 0) return cudaSuccess;
-  if (rs == 1) {
-    dim3 grid(static_cast<unsigned int>((rows + kThreads - 1) / kThreads), ychunks);
-    exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
-  } else {
-    dim3 grid(static_cast<unsigned int>((rows + 7) / 8), ychunks);
-    exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag);
-  }
+  if (k <= 0) return cudaSuccess;
+  const int64_t rowblocks = rs == 1 ? (rows + kThreads - 1) / kThreads : (rows + 7) / 8;
+  const int64_t chunk = pick_chunk(rowblocks, k);
+  const dim3 grid(static_cast<unsigned int>(rowblocks), static_cast<unsigned int>((k + chunk - 1) / chunk));
+  if (rs == 1) exp_max_kernel<S, true, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, chunk);
+  else exp_max_kernel<S, false, R><<<grid, kThreads, 0, st>>>(X, rows, k, rs, hs, emax, flag, chunk);
   count_launches(1);
   return cudaGetLastError();
 }
