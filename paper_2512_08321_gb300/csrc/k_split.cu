@@ -14,15 +14,17 @@
 // Per modulus, a' == sum_t c_t w_t (mod p) with w_t = 2^(13t) mod p in
 // [-128, 127]: every product is below 2^20 and the sum below 2^23, so the FP32
 // sum is exact; one rint-based reduction and a symmetric fix-up give the
-// residue.  This keeps the per-modulus work on the FP32 pipe.
+// residue.  The sums run as packed FP32 pairs (two entries of a row per
+// instruction).
 //
 // Real input (DGEMM/SGEMM emulation) has one plane per modulus:
 // plane l = mod(trunc(v 2^x_r), p_l).
 //
 // Output layout: planes[(3l+c) * rows * kpad + r * kpad + h] (real: plane l);
-// h in [k, kpad) is zero.  A block handles 32 rows x 32 h: the tile goes through shared
+// h in [k, kpad) is zero.  A block handles 32 rows x 64 h: the tile goes through shared
 // memory so global reads are coalesced whichever of r or h is contiguous;
-// each thread then owns 4 consecutive h of one row, 8 threads per row.
+// each thread then owns 4 consecutive h of one row, 16 threads per row, so a
+// row of a block covers a whole 128-byte line of every fp16 plane.
 #include <cuda_fp16.h>
 
 #include <type_traits>
@@ -33,13 +35,16 @@ namespace emu {
 namespace {
 
 constexpr int kTileR = 32;
-constexpr int kTileH = 32;
+constexpr int kTileH = 32;     // accurate-mode bound planes
+constexpr int kSplitH = 64;    // residue planes
 constexpr int kThreads = 256;
 
-struct SplitSmem {
-  uint64_t tre[kTileR][kTileH + 1];     // raw bits of the tile, [r][h], one element of padding
-  uint64_t tim[kTileR][kTileH + 1];
+template <int H>
+struct TileSmem {
+  uint64_t tre[kTileR][H + 1];     // raw bits of the tile, [r][h], one element of padding
+  uint64_t tim[kTileR][H + 1];
 };
+using SplitSmem = TileSmem<kSplitH>;
 
 // Signed 13-bit chunks of a' = trunc(v 2^x) (exact floats, least significant first).
 template <bool SINGLE, int TC>
@@ -88,10 +93,33 @@ __device__ __forceinline__ void chunks(uint64_t bits, int x, int nchunk, float (
   }
 }
 
+// ---- packed FP32 pairs: one instruction for two lanes
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{.reg .b64 a2, b2, c2, d2;\n\tmov.b64 a2, {%2, %3};\n\tmov.b64 b2, {%4, %5};\n\t"
+      "mov.b64 c2, {%6, %7};\n\tfma.rn.f32x2 d2, a2, b2, c2;\n\tmov.b64 {%0, %1}, d2;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 a2, b2, d2;\n\tmov.b64 a2, {%2, %3};\n\tmov.b64 b2, {%4, %5};\n\t"
+      "mul.rn.f32x2 d2, a2, b2;\n\tmov.b64 {%0, %1}, d2;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 // Symmetric residue (ties up) of the exact float integer z, |z| < 2^23;
 // ph = p/2 (exact).
 __device__ __forceinline__ float sym_mod_f(float z, float p, float ph, float inv_p) {
-  float r = fmaf(-rintf(z * inv_p), p, z);      // exact; |r| <= p/2 + 2
+  float r = fmaf(-rintf(z * inv_p), p, z);      // exact; |r| <= p/2 + 1
+  if (r >= ph) r -= p;
+  if (r < -ph) r += p;
+  return r;
+}
+__device__ __forceinline__ float sym_fix_f(float r, float p, float ph) {
   if (r >= ph) r -= p;
   if (r < -ph) r += p;
   return r;
@@ -144,18 +172,18 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   // prow: rows between consecutive planes (a block of rows of a larger plane set)
   const int tid = threadIdx.x;
   const int64_t r0 = rtile * kTileR;
-  const int64_t h0 = htile * kTileH;
+  const int64_t h0 = htile * kSplitH;
 
-  // load phase: 1024 elements, 4 per thread, coalesced along the contiguous index
+  // load phase: 2048 elements, 8 per thread, coalesced along the contiguous index
 #pragma unroll
-  for (int it = 0; it < (kTileR * kTileH) / kThreads; ++it) {
+  for (int it = 0; it < (kTileR * kSplitH) / kThreads; ++it) {
     int rr, hh;
     if (ROWS_CONTIG) {
-      rr = tid & 31;
-      hh = (tid >> 5) + 8 * it;
+      rr = tid % kTileR;
+      hh = tid / kTileR + (kThreads / kTileR) * it;
     } else {
-      hh = tid & 31;
-      rr = (tid >> 5) + 8 * it;
+      hh = tid % kSplitH;
+      rr = tid / kSplitH + (kThreads / kSplitH) * it;
     }
     const int64_t r = r0 + rr, h = h0 + hh;
     uint64_t bre = 0, bim = 0;
@@ -180,8 +208,8 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   __syncthreads();
 
   // compute phase: each thread owns kPerThread consecutive h of one row; the
-  // block covers kTileR rows x kTileH h in 1024 / (256 kPerThread) passes
-  constexpr int kThreadsPerRow = kTileH / kPerThread;
+  // block covers kTileR rows x kSplitH h in 2048 / (256 kPerThread) passes
+  constexpr int kThreadsPerRow = kSplitH / kPerThread;
   constexpr int kRowsPerPass = kThreads / kThreadsPerRow;
 #pragma unroll 1
   for (int pass = 0; pass < kTileR / kRowsPerPass; ++pass) {
@@ -194,7 +222,10 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
   const int nch = NCH ? NCH : pl.nchunk;
   constexpr int TC = NCH ? NCH : kMaxChunks;
 
-  float cre[kPerThread][TC], cim[kPerThread][TC];
+  // chunks of entries 2i and 2i+1 side by side: the per-modulus steps run on pairs
+  static_assert(kPerThread % 2 == 0, "entries are processed in pairs");
+  constexpr int kPairs = kPerThread / 2;
+  float2 cre[kPairs][TC], cim[kPairs][TC];
 #pragma unroll
   for (int j = 0; j < kPerThread; ++j) {
     uint64_t br = sm.tre[rr][hb + j], bi = sm.tim[rr][hb + j];
@@ -203,50 +234,62 @@ __device__ __forceinline__ void split_block(SplitSmem& sm, const void* __restric
                      (SINGLE ? (((br >> 23) & 0xFF) == 0xFF || ((bi >> 23) & 0xFF) == 0xFF)
                              : (((br >> 52) & 0x7FF) == 0x7FF || ((bi >> 52) & 0x7FF) == 0x7FF));
     if (bad) br = bi = 0;
-    chunks<SINGLE, TC>(br, flagged ? 0 : x, nch, cre[j]);
-    if constexpr (!R) chunks<SINGLE, TC>(bi, flagged ? 0 : x, nch, cim[j]);
+    float c[TC];
+    chunks<SINGLE, TC>(br, flagged ? 0 : x, nch, c);
+#pragma unroll
+    for (int t = 0; t < TC; ++t) {
+      if (j & 1) cre[j / 2][t].y = c[t];
+      else cre[j / 2][t].x = c[t];
+    }
+    if constexpr (!R) {
+      chunks<SINGLE, TC>(bi, flagged ? 0 : x, nch, c);
+#pragma unroll
+      for (int t = 0; t < TC; ++t) {
+        if (j & 1) cim[j / 2][t].y = c[t];
+        else cim[j / 2][t].x = c[t];
+      }
+    }
   }
   const int64_t plane_stride = prow * kpad;
-  T* base = planes + r * kpad + h0 + hb;
-  T* dst = base;
+  T* dst = planes + r * kpad + h0 + hb;
   for (int l = 0; l < pl.N; ++l) {
     const float p = static_cast<float>(pl.p[l]);
     const float ph = 0.5f * p;
     const float ip = pl.inv_p[l];
-    float w[TC];
+    float2 w[TC];
 #pragma unroll
-    for (int t = 0; t < TC; ++t) w[t] = pl.w13[l][t];
+    for (int t = 0; t < TC; ++t) w[t] = make_float2(pl.w13[l][t], pl.w13[l][t]);
+    // z = sum_t c_t w_t for one pair of entries (exact: |z| < 2^23)
+    auto dot = [&](const float2 (&c)[TC]) {
+      float2 z = mul2(c[0], w[0]);
+#pragma unroll
+      for (int t = 1; t < TC; ++t)
+        if (NCH || t < nch) z = fma2(c[t], w[t], z);
+      return z;
+    };
+    float vr[kPerThread];
     if constexpr (R) {
       // real input: one plane per modulus
-      float vr[kPerThread];
 #pragma unroll
-      for (int j = 0; j < kPerThread; ++j) {
-        float zr = 0.0f;
-#pragma unroll
-        for (int t = 0; t < TC; ++t)
-          if (NCH || t < nch) zr = fmaf(cre[j][t], w[t], zr);
-        vr[j] = sym_mod_f(zr, p, ph, ip);
+      for (int i = 0; i < kPairs; ++i) {
+        const float2 z = dot(cre[i]);
+        vr[2 * i] = sym_mod_f(z.x, p, ph, ip);
+        vr[2 * i + 1] = sym_mod_f(z.y, p, ph, ip);
       }
       StoreE<T, kPerThread>::put(dst, vr);
       dst += plane_stride;
     } else {
-      float vr[kPerThread], vi[kPerThread], vs[kPerThread];
+      float vi[kPerThread], vs[kPerThread];
 #pragma unroll
-      for (int j = 0; j < kPerThread; ++j) {
-        float zr = 0.0f, zi = 0.0f;
-#pragma unroll
-        for (int t = 0; t < TC; ++t) {
-          if (NCH || t < nch) {
-            zr = fmaf(cre[j][t], w[t], zr);
-            zi = fmaf(cim[j][t], w[t], zi);
-          }
-        }
-        vr[j] = sym_mod_f(zr, p, ph, ip);
-        vi[j] = sym_mod_f(zi, p, ph, ip);
-        float sr = vr[j] + vi[j];
-        if (sr >= ph) sr -= p;
-        if (sr < -ph) sr += p;
-        vs[j] = sr;
+      for (int i = 0; i < kPairs; ++i) {
+        const float2 zr = dot(cre[i]), zi = dot(cim[i]);
+        vr[2 * i] = sym_mod_f(zr.x, p, ph, ip);
+        vr[2 * i + 1] = sym_mod_f(zr.y, p, ph, ip);
+        vi[2 * i] = sym_mod_f(zi.x, p, ph, ip);
+        vi[2 * i + 1] = sym_mod_f(zi.y, p, ph, ip);
+        // Karatsuba sum plane: |vr + vi| <= p
+        vs[2 * i] = sym_fix_f(vr[2 * i] + vi[2 * i], p, ph);
+        vs[2 * i + 1] = sym_fix_f(vr[2 * i + 1] + vi[2 * i + 1], p, ph);
       }
       StoreE<T, kPerThread>::put(dst, vr);
       StoreE<T, kPerThread>::put(dst + plane_stride, vi);
@@ -291,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) bound_split_kernel(const void* __res
                                                                int64_t rs, int64_t hs, const int* __restrict__ emax,
                                                                const unsigned int* __restrict__ flag, int64_t kpad,
                                                                __half* __restrict__ planes) {
-  __shared__ SplitSmem sm;
+  __shared__ TileSmem<kTileH> sm;
   const int tid = threadIdx.x;
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kTileR;
   const int64_t h0 = static_cast<int64_t>(blockIdx.y) * kTileH;
@@ -387,9 +430,9 @@ template <bool SINGLE, typename T, bool R>
 cudaError_t launch_t(bool conj, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                      const Plan& pl, const int16_t* xexp, int64_t kpad, void* planes,
                      cudaStream_t st, int elems, int64_t prow) {
-  if ((rows + kTileR - 1) / kTileR > 2147483647LL || kpad / kTileH > 65535) return cudaErrorInvalidValue;
+  if ((rows + kTileR - 1) / kTileR > 2147483647LL || kpad / kSplitH > 65535) return cudaErrorInvalidValue;
   dim3 grid(static_cast<unsigned int>((rows + kTileR - 1) / kTileR),
-            static_cast<unsigned int>(kpad / kTileH));
+            static_cast<unsigned int>(kpad / kSplitH));
   T* P = static_cast<T*>(planes);
   // the common configuration (fp16 planes, 4 entries per thread) has the chunk count compiled in
   auto fixed = [&](auto nch_tag) {
@@ -441,7 +484,7 @@ cudaError_t launch_s(bool conj, const void* X, int64_t rows, int64_t k, int64_t 
 
 long long split_seg_blocks(SplitSeg& g) {
   g.rows_contig = (g.rs == 1) ? 1 : 0;
-  g.htiles = static_cast<int>(g.kpad / kTileH);
+  g.htiles = static_cast<int>(g.kpad / kSplitH);
   return ((g.rows + kTileR - 1) / kTileR) * g.htiles;
 }
 
