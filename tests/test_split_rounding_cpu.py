@@ -1,16 +1,16 @@
 """The residue step of the split kernel, checked exhaustively on the CPU.
 
-The split forms, for every exact float integer |z| < 2^23 and modulus p, the
-symmetric residue (Section II, ties rounded up) in two float32 steps:
-    q = RN(z * RN(1/p) + 1.5 2^23) - 1.5 2^23,   r = z - q p
-    f = RN((r + 1/4) * RN(1/p) + 1.5 2^23) - 1.5 2^23,   result r - f p
-and applies the second step alone to the Karatsuba sum of two residues
-(|s| <= p).  Its correctness rests on a rounding argument (q within
-1/2 + 1/(2p) of z/p; (r + 1/4)/p at least 1/(4p) from a half-integer).
-This test replays both steps with exact integer arithmetic (float32
-round-to-nearest-even of a fused product-sum, written out) over every
-z in (-2^23, 2^23) for every modulus the plans use, and checks the result
-against the definition.
+For every exact float integer |z| < 2^23 (a sum of chunk products) and
+modulus p, the split forms the symmetric residue (Section II, ties rounded
+up) in float32 as
+    q = rint(RN(z * RN(1/p))),   r = z - q p   (one fused multiply-add),
+then moves r into [-p/2, p/2) by at most one subtraction or addition of p;
+the Karatsuba sum plane applies the same correction to the sum of two
+residues.  This is right only if the rounded quotient leaves |r| <= 3p/2 and
+z - q p is exact, which rests on a rounding argument (|r| <= p/2 + 1).
+This test replays the float32 steps with exact integer arithmetic
+(round-to-nearest-even written out) over every z in (-2^23, 2^23) for every
+modulus the plans use and checks the result against the definition.
 """
 import math
 
@@ -19,40 +19,36 @@ import pytest
 
 from oracle.moduli import choose_moduli
 
-ROUND = 3 * 2 ** 22                  # 1.5 2^23
-
 
 def _inv_p(p):
     # the plan's RN(1/p): the double quotient rounded to float32
     m, e = math.frexp(float(np.float32(1.0 / p)))     # value = m 2^e, 0.5 <= m < 1
-    mi = int(m * 2 ** 24)
-    return mi, 24 - e                                # value = mi 2^-sh
+    return int(m * 2 ** 24), 24 - e                  # value = mi 2^-sh
 
 
 def _rne_shift(a, sh):
-    """Round-half-even of a / 2^sh for int64 arrays a (sh >= 1)."""
+    """Round-half-even of a / 2^sh for int64 arrays a and shifts sh >= 1 (array or scalar)."""
     fl = a >> sh
     rem = a - (fl << sh)
-    half = 1 << (sh - 1)
+    half = np.left_shift(1, sh - 1)
     return fl + (rem > half) + ((rem == half) & (fl & 1))
 
 
-def _fused_round(num, sh):
-    """RN(num 2^-sh + 1.5 2^23) - 1.5 2^23 in float32 (|num 2^-sh| < 2^22):
-    the sum lies in [2^23, 2^24), where float32 spacing is 1 and 1.5 2^23
-    is even, so this is round-half-even of num 2^-sh."""
-    return _rne_shift(num, sh)
+def _quotient(z, mi, sh):
+    """rint(RN_float32(z mi 2^-sh)) for int64 z with |z| < 2^23."""
+    n = np.abs(z) * mi                               # exact, < 2^47
+    bits = np.frexp(n.astype(np.float64))[1]         # bit length of n (exact: n < 2^53)
+    drop = np.maximum(bits - 24, 0)                  # RN to 24 significant bits
+    m = np.where(drop > 0, _rne_shift(n, np.maximum(drop, 1)), n)
+    # value = m 2^(drop - sh); sh > drop for every z here (the quotient is below 2^23)
+    assert np.all(sh - drop >= 1)
+    q = _rne_shift(m, sh - drop)
+    return np.where(z < 0, -q, q)
 
 
-def _fix(r, p, mi, sh):
-    f = _fused_round((4 * r + 1) * mi, sh + 2)      # (r + 1/4) RN(1/p), exact product
-    return r - f * p
-
-
-def _sym_mod_step(z, p, mi, sh):
-    q = _fused_round(z * mi, sh)
-    r = z - q * p
-    return _fix(r, p, mi, sh), r
+def _correct(r, p):
+    r = np.where(2 * r >= p, r - p, r)
+    return np.where(2 * r < -p, r + p, r)
 
 
 def _check_definition(z, out, p):
@@ -68,16 +64,16 @@ def test_residue_step_is_the_symmetric_remainder(p):
     worst = 0
     for lo in range(-lim + 1, lim, step):
         z = np.arange(lo, min(lo + step, lim), dtype=np.int64)
-        out, r = _sym_mod_step(z, p, mi, sh)
+        r = z - _quotient(z, mi, sh) * p             # |z - q p| < 2^24: exact in float32
         worst = max(worst, int(np.abs(2 * r).max()))
-        _check_definition(z, out, p)
-    # the first step alone already lands within p/2 + 1/2
-    assert worst <= p + 1
+        _check_definition(z, _correct(r, p), p)
+    # the rounded quotient leaves |r| <= p/2 + 1, so one correction suffices
+    assert worst <= p + 2
 
 
 @pytest.mark.parametrize("p", choose_moduli(20))
 def test_karatsuba_sum_correction(p):
-    mi, sh = _inv_p(p)
-    # every sum of two symmetric residues, and the whole range |s| <= p + 1
-    s = np.arange(-p - 1, p + 2, dtype=np.int64)
-    _check_definition(s, _fix(s, p, mi, sh), p)
+    # every sum of two symmetric residues
+    a = np.arange(-(p // 2), (p + 1) // 2, dtype=np.int64)
+    s = (a[:, None] + a[None, :]).ravel()
+    _check_definition(s, _correct(s, p), p)
