@@ -34,6 +34,8 @@ METRIC_REAL = "emulated DGEMM/SGEMM TFLOPS (2mnk/s) vs cuBLAS native at matched 
 WORKLOADS = {
     "zgemm16384": dict(single=False, m=16384, n=16384, k=16384, phi=1.0, N=15, seed=20251208),
     "cgemm8192": dict(single=True, m=8192, n=8192, k=8192, phi=0.5, N=8, seed=20251209),
+    # the paper's CGEMM size (its speed-ups over cublasCgemm are quoted at 16384^3)
+    "cgemm16384": dict(single=True, m=16384, n=16384, k=16384, phi=0.5, N=8, seed=20251217),
     # real matrices (one residue product per modulus)
     "dgemm16384": dict(single=False, real=True, m=16384, n=16384, k=16384, phi=1.0, N=15, seed=20251215),
     "sgemm16384": dict(single=True, real=True, m=16384, n=16384, k=16384, phi=0.5, N=8, seed=20251216),
