@@ -24,7 +24,8 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(os.environ.get("EMU_ACCURACY_SWEEP") != "1",
                                  reason="opt-in full-size accuracy sweep (EMU_ACCURACY_SWEEP=1)")]
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# measured figures are written as JSON into this directory when it is set and exists
+OUT = os.environ.get("EMU_RESULTS_DIR", "")
 SAMPLES = 4096
 SWEEPS = [  # name, m=n=k, complex64, phis, moduli, tolerance
     ("zgemm16384", 16384, False, (0.0, 1.0, 2.0), tuple(range(12, 21)), 1e-15),
@@ -92,6 +93,6 @@ def test_accuracy_sweep(pool):
             assert entry["by_moduli"][moduli[-1]]["max_normalised_error"] <= tol
             del A, B
             torch.cuda.empty_cache()
-    if os.path.isdir(OUT):
+    if OUT and os.path.isdir(OUT):
         with open(os.path.join(OUT, "accuracy_sweep.json"), "w") as fh:
             json.dump(report, fh, indent=1)

@@ -19,11 +19,12 @@ from paper_2512_08321_gb300.workloads import paper_matrix_device
 
 pytestmark = pytest.mark.gpu
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# measured figures are written as JSON into this directory when it is set and exists
+OUT = os.environ.get("EMU_RESULTS_DIR", "")
 
 
 def _record(name, data):
-    if os.path.isdir(OUT):
+    if OUT and os.path.isdir(OUT):
         with open(os.path.join(OUT, name), "w") as f:
             json.dump(data, f, indent=1)
 

@@ -20,7 +20,8 @@ from .helpers import dev
 
 pytestmark = pytest.mark.gpu
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# measured figures are written as JSON into this directory when it is set and exists
+OUT = os.environ.get("EMU_RESULTS_DIR", "")
 
 
 def _cuda(a):
@@ -129,7 +130,7 @@ def test_learned_selection_gain_over_apriori():
                 rows.append(dict(m=m, n=n, k=k, phi=phi, target=T, N_learned=Nm, N_apriori=Na,
                                  err_learned=err_m, err_apriori=err_a))
     moduli.unload()
-    if os.path.isdir(OUT):
+    if OUT and os.path.isdir(OUT):
         with open(os.path.join(OUT, "learned_moduli_heldout.json"), "w") as f:
             json.dump(rows, f, indent=1)
     print(json.dumps(rows))
