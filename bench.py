@@ -207,18 +207,27 @@ def overlap_blocks(n):
     return -(-n // nb)
 
 
-def profile_traffic(kernel_file, summary_name):
-    """dram bytes per launch from the committed ncu summary, if the kernel source
-    is unchanged since the capture (its sha256 is recorded there)."""
+def source_sha256(files):
+    """sha256 over the kernel's source files, in order."""
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2512_08321_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profile_traffic(kernel_files, summary_name):
+    """dram bytes per launch from the committed ncu summary, if the kernel's sources
+    (its .cu file and the shared tcgen05/TMA header) are unchanged since the capture
+    (their sha256 is recorded there)."""
     path = os.path.join(ROOT, "profiles", summary_name)
-    src = os.path.join(ROOT, "paper_2512_08321_gb300", "csrc", kernel_file)
     try:
         kv = {}
         for ln in open(path):
             if ":" in ln and not ln.startswith("#"):
                 a, b = ln.split(":", 1)
                 kv[a.strip()] = b.strip()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = source_sha256(kernel_files)
         if kv.get("source_sha256") != sha:
             return None
         return float(kv["dram_bytes_per_launch_full_size"])
@@ -350,7 +359,7 @@ def main():
     t_gemm = t_gemm_step
     achieved = gemm_flops / t_gemm * 1e-12
     peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
-    traffic = profile_traffic("k_gemm_f16.cu", f"gemm_f16_{args.workload}.txt")
+    traffic = profile_traffic(("k_gemm_f16.cu", "tc_common.cuh"), f"gemm_f16_{args.workload}.txt")
     roofline = {"bound": "tensor", "kernel": "gemm_f16_kernel (tcgen05.mma kind::f16, exact residue products)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": (traffic / nblk if traffic else traffic),
