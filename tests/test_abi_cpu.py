@@ -1,6 +1,7 @@
 """The C-ABI library loads and exports every symbol include/*.h declares; the
 host-side plan and argument checks agree with the oracle.  No GPU needed:
 nothing here launches device work."""
+import ctypes
 import glob
 import os
 import re
@@ -129,3 +130,49 @@ def test_plan_exponent_accu_matches_oracle(L, N):
     for M in Ms:
         assert emu.emu_plan_exponent_accu(N, M) == exponent_accu(M, P), M
     assert emu.emu_plan_exponent_accu(N, 2 ** 35) == -100000
+
+
+def _prototypes():
+    """name -> parameter list of every function declared in include/ozaki2_emu.h"""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ozaki2_emu.h")).read(), flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    return {m.group(1): m.group(2) for m in re.finditer(r"\b(emu_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S)}
+
+
+def _c_kind(param):
+    p = " ".join(param.split())
+    if p in ("", "void"):
+        return None
+    if "*" in p or "[" in p or re.search(r"\b(cudaStream_t|emu_grouped_t)\b", p):
+        return "pointer"
+    if re.search(r"\b(int64_t|long long)\b", p):
+        return "int64"
+    if re.search(r"\b(uint64_t|size_t)\b", p):
+        return "uint64"
+    if re.search(r"\bdouble\b", p):
+        return "double"
+    if re.search(r"\bfloat\b", p):
+        return "float"
+    if re.search(r"\b(u?int(32_t)?|unsigned( int)?|emu_[a-z_]+_t)\b", p):
+        return "int32"
+    raise AssertionError(f"unclassified parameter: {p}")
+
+
+def _py_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "pointer"
+    for kind, types in (("int64", (ctypes.c_int64, ctypes.c_longlong)), ("uint64", (ctypes.c_uint64, ctypes.c_size_t)),
+                        ("double", (ctypes.c_double,)), ("float", (ctypes.c_float,)),
+                        ("int32", (ctypes.c_int, ctypes.c_uint, ctypes.c_int32, ctypes.c_uint32))):
+        if t in types:
+            return kind
+    raise AssertionError(f"unclassified ctypes type: {t}")
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature of the binding has the header's parameter count and kinds, in order."""
+    protos = _prototypes()
+    assert set(protos) == set(emu.exported_names())
+    for name, _res, args in emu._SIGS:
+        want = [k for k in (_c_kind(p) for p in protos[name].split(",")) if k is not None]
+        assert [_py_kind(a) for a in args] == want, name
