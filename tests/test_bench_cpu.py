@@ -42,3 +42,42 @@ def test_traffic_missing_summary_is_none(tmp_path, monkeypatch):
     root = _tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.profile_traffic(SOURCES, "no_such_summary.txt") is None
+
+
+# ---------------------------------------------------------------- comparators
+def _calls_in_main():
+    """(callee name, argument names) of every call in bench.main."""
+    import ast
+    import inspect
+    tree = ast.parse(inspect.getsource(bench.main))
+    out = []
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Call) and isinstance(node.func, ast.Name):
+            out.append((node.func.id, [a.id for a in node.args if isinstance(a, ast.Name)]))
+    return out
+
+
+def test_plain_comparator_reference_is_a_private_snapshot():
+    """The buffer the unfused pipeline is checked against is passed to no other
+    comparator, and cuBLAS's 3M GEMM writes into a buffer of its own."""
+    import inspect
+    calls = _calls_in_main()
+    plain = [args for name, args in calls if name == "plain_emulation"]
+    assert plain, "main() no longer runs the plain comparator"
+    ref = plain[0][-1]
+    assert ref not in ("C", "A", "B")
+    others = [name for name, args in calls if ref in args and name != "plain_emulation"]
+    assert not others, f"the comparator's reference buffer {ref} is also passed to {others}"
+    assert "C" not in inspect.signature(bench.gemm3m).parameters
+
+
+def test_plain_comparator_compares_against_the_reference(monkeypatch):
+    import torch
+    wl = dict(m=4, n=3, k=5, N=2, single=False)
+    ref = torch.arange(12, dtype=torch.float64).reshape(3, 4).to(torch.complex128)
+    monkeypatch.setattr(bench, "plain_emulation_run", lambda *a: (ref.clone(), 1.0))
+    assert bench.plain_emulation(None, torch, None, None, wl, ref)["bitexact_vs_fused"] is True
+    other = ref.clone()
+    other[1, 2] += 1.0
+    monkeypatch.setattr(bench, "plain_emulation_run", lambda *a: (other, 1.0))
+    assert bench.plain_emulation(None, torch, None, None, wl, ref)["bitexact_vs_fused"] is False
