@@ -382,8 +382,7 @@ def main():
                       "engine": "tcgen05 kind::f16 (exact residues), integer CRT", "scaling": args.scaling,
                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                       "seed": wl["seed"],
-                      "tuning": dict(zip(["tile_n", "group", "chunk_k", "crt_rows", "split_elems"], tuned))
-                      if tuned else "defaults"},
+                      "tuning": tuning_record(emu, dtype_code, N, m, n, k, tuned)},
            "roofline": roofline, "phases_ms": phases, "memory_phases": mem_phases,
            "overlap": ({"column_blocks": nblk, "step_ms": overlap_ms,
                         "phases_ms_from": "one more step with EMU_TUNE_OVERLAP = 0 (one phase after another)"}
@@ -531,6 +530,19 @@ def gemm3m(torch, A, B, m, n, k, single, stream):
                 "tflops": 8.0 * m * n * k / (ms * 1e-3) * 1e-12}
     except Exception:
         return None
+
+
+def tuning_record(emu, dtype_code, N, m, n, k, tuned):
+    """The launch configuration the timed calls used: the autotuned knobs (or the
+    defaults) and the residue products' modulus-loop schedule."""
+    keys = {"tile_n": emu.EMU_TUNE_TILE_N, "group": emu.EMU_TUNE_GROUP, "chunk_k": emu.EMU_TUNE_CHUNK_K,
+            "crt_rows": emu.EMU_TUNE_CRT_ROWS, "split_elems": emu.EMU_TUNE_SPLIT_ELEMS}
+    rec = {nm: emu.emu_tuned_value(dtype_code, N, m, n, k, key) for nm, key in keys.items()}
+    rec["schedule"] = {nm: emu.emu_tuned_value(dtype_code, N, m, n, k, key) for nm, key in emu.SCHEDULE_KNOBS.items()}
+    names = {0: "modulus outer", 1: "tile outer", 2: "column bands (the paper's n-blocking)"}
+    rec["schedule"]["order_name"] = names.get(rec["schedule"]["order"], "?")
+    rec["source"] = "autotuned (emu_autotune_gemm)" if tuned else "defaults"
+    return rec
 
 
 def max_over_ranks(ms, dist):

@@ -322,6 +322,21 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *                        GEMMs by about what the overlap hides, for the real
  *                        ones (a third of the products per output) by less.  A
  *                        process setting only, never autotuned
+ *   EMU_TUNE_ORDER       residue products, modulus-loop schedule: order of the
+ *                        (tile, job pair) units.  0 modulus outer (every tile of
+ *                        one job pair before the next pair), 1 tile outer (every
+ *                        job pair of one tile before the next tile), 2 column
+ *                        bands of EMU_TUNE_BAND columns, modulus outer inside a
+ *                        band (the n-blocking of Section III-A)
+ *   EMU_TUNE_PAIRING     residue products: the two jobs that share a unit (and
+ *                        alternate in its two accumulators).  0 adjacent jobs of
+ *                        the sequence D_0 E_0 F_0 D_1 ..., 1 job p with job
+ *                        p + ceil(J/2), 2 adjacent jobs of the component-major
+ *                        sequence D_0 .. D_N-1 E_0 .. F_N-1 (J = 3N complex, N real)
+ *   EMU_TUNE_KDIR        residue products: 0 k chunks ascending, 1 descending on
+ *                        every other unit of a persistent block
+ *   EMU_TUNE_BAND        columns per band for EMU_TUNE_ORDER 2, a multiple of
+ *                        128 (default 8192, the paper's block)
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
  * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
@@ -329,7 +344,11 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  * set.  Tuning state is per process; emu_autotune_gemm allocates its own
  * temporary buffers (inputs, planes, residues of the shape), synchronises, and
  * frees them.  dtype is an EMU_DTYPE_* code.  best (may be NULL) receives the
- * first 5 knobs' chosen values in key order. */
+ * first 5 knobs' chosen values in key order; emu_tuned_value gives any knob's
+ * value that a call of the given dtype, N and shape will use (the autotuned
+ * entry of its bucket, else the process default; -1 for an unknown key).
+ * The autotuner searches the tile width, group and chunk, then the schedule
+ * knobs 8-11 one at a time, then the CRT rows and split entries. */
 #define EMU_TUNE_TILE_N 1
 #define EMU_TUNE_GROUP 2
 #define EMU_TUNE_CHUNK_K 3
@@ -337,8 +356,13 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 #define EMU_TUNE_SPLIT_ELEMS 5
 #define EMU_TUNE_NBLOCK 6
 #define EMU_TUNE_OVERLAP 7
+#define EMU_TUNE_ORDER 8
+#define EMU_TUNE_PAIRING 9
+#define EMU_TUNE_KDIR 10
+#define EMU_TUNE_BAND 11
 emu_status_t emu_set_tuning(int key, int value);
 int emu_get_tuning(int key);
+int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, int key);
 emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int num_moduli, int* best);
 /* Forget the autotuned entries (the defaults stay). */
 emu_status_t emu_autotune_clear(void);
@@ -422,13 +446,18 @@ emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli,
  * instead of memory allocated per call.  Nothing is allocated: no cudaMalloc,
  * cudaFree or allocating library routine is called.
  * - m and n are limited to EMU_STATIC_EXP_MAX_ROWS; larger sizes return
- *   EMU_ERR_SIZE_LIMIT before any GPU work.  Other arguments as in
- *   emu_stage_exponents.
+ *   EMU_ERR_SIZE_LIMIT before any GPU work.
  * - The array (1 MiB) stays resident on every GPU that loads the library
  *   until the process exits.
  * - The first call made with a device current looks up the array's device
  *   address (cudaGetSymbolAddress) for that device; make that first call
- *   before any stream capture.
+ *   before any stream capture.  The address is kept per device together with
+ *   the id of the context it belongs to; after a device reset (a new primary
+ *   context, the library's module loaded again) the next call looks it up
+ *   again, and that call too belongs outside any stream capture.
+ * - Argument errors as in emu_stage_exponents (the same checks, the same
+ *   emu_last_bad_param() positions); a NULL A, B, x or y that would be used
+ *   is EMU_ERR_INVALID_ARG with position 7, 9, 12 or 13.
  * - Every call on a device shares the one array, which keeps the last call's
  *   contents; each call clears the part it uses before using it.  Calls that
  *   can overlap on the GPU (different streams, no ordering between them)

@@ -193,7 +193,7 @@ emu_status_t run_residue_gemm(emu_engine_t eng, int64_t m, int64_t n, int64_t kp
                                       static_cast<const int8_t*>(pb), res, ldr, st, ppm));
   }
   const cudaError_t e = launch_gemm_f16(m, n, kpad, pl, pa, pb, res, ldr, t.chunk_k, ds->status, st, t.tile_n,
-                                        t.group, ppm, a_plane_rows, rcap);
+                                        t.group, ppm, a_plane_rows, rcap, t.sched);
   if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
   return cuda_status(e);
 }
@@ -501,6 +501,11 @@ emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int
 }
 
 emu_status_t set_bad_param(int idx) { return bad(idx); }
+
+emu_status_t check_stage_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
+                              int N) {
+  return check_common(ta, tb, m, n, k, lda, ldb, 1, N, false);
+}
 
 // Per-device staging buffer of the host-buffer entry points (grown on demand).
 emu_status_t get_staging(size_t need, char** out) {

@@ -87,6 +87,20 @@ cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, con
 cudaError_t launch_accu_finalize(int64_t rows, const int* emax, const unsigned int* flag, const unsigned int* Mb,
                                  const Plan& pl, int16_t* xout, cudaStream_t st);
 
+// Modulus-loop schedule of the residue-product kernel (k_gemm_f16.cu): the
+// order of its (tile, job pair) units, which jobs share a unit, and the k
+// direction.  None of it changes a result.
+struct GemmSchedule {
+  int order = 0;          // 0 modulus outer, 1 tile outer, 2 column bands (modulus outer inside a band)
+  int pairing = 0;        // 0 adjacent jobs, 1 halves (p, p + ceil(J/2)), 2 component-major (all D, E, F)
+  int kalt = 0;           // 1: a CTA's odd units run their k chunks in descending order
+  int band_cols = 8192;   // columns per band for order 2 (the paper's n-block), a multiple of 128
+  bool valid() const {
+    return order >= 0 && order <= 2 && pairing >= 0 && pairing <= 2 && (kalt == 0 || kalt == 1) &&
+           band_cols >= 128 && band_cols <= 65536 && band_cols % 128 == 0;
+  }
+};
+
 // Launch-configuration knobs of one GEMM (process defaults, autotuned per shape bucket).
 struct Tune {
   int tile_n = 256;      // residue products: output rows per tile (64, 128, 256)
@@ -98,6 +112,7 @@ struct Tune {
   int nblock = 0;        // output columns per block (0: automatic, by workspace size)
   int overlap = -1;      // split and CRT of neighbouring column blocks beside the residue products:
                          // 1 on, 0 off, -1 (default) on for the real GEMMs only
+  GemmSchedule sched;    // residue products: modulus-loop schedule
 };
 
 // Tuning of a call of this shape: the autotuned entry of its (dtype, N, shape
@@ -119,7 +134,7 @@ cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                             const void* planesA, const void* planesB, int8_t* res,
                             int64_t ldr, int chunk_k, unsigned int* status, cudaStream_t st,
                             int tile_n = 256, int group = 16, int ppm = 3, int64_t a_plane_rows = 0,
-                            int64_t rcap = 0);
+                            int64_t rcap = 0, const GemmSchedule& sched = GemmSchedule());
 
 cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        const int8_t* res, int64_t ldr, const int16_t* x, const int16_t* y,
@@ -186,7 +201,7 @@ cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob,
 size_t group_problem_bytes();
 bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, const void* planesA,
                         const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,
-                        long long* unit_begin);
+                        long long* unit_begin, const GemmSchedule& sched = GemmSchedule());
 cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long total_units, const Plan& pl,
                                     int tile_n, unsigned int* status, cudaStream_t st);
 cudaError_t prepare_gemm_f16();
@@ -238,6 +253,9 @@ emu_status_t run_gemm(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t 
 emu_status_t check_gemm_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
                              int64_t ldc, int N);
 emu_status_t set_bad_param(int idx);
+// the checks of the stage entry points (operands, sizes, leading dimensions, N, k; no C)
+emu_status_t check_stage_args(emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
+                              int N);
 emu_status_t get_staging(size_t need, char** out);
 
 // Launch accounting (api.cu): launchers report each kernel they enqueue.

@@ -21,6 +21,20 @@
 // columns).  A work unit is one 128 x 256 tile and a pair of jobs; the two
 // jobs alternate chunk by chunk in two TMEM slots of 256 columns, so the
 // epilogue reduces one slot while the tensor core fills the other.
+//
+// The modulus-loop schedule is a launch parameter (Sched, searched by the
+// autotuner); every choice gives the same residues:
+//   order    0  modulus outer: every tile of job pair 0, then of pair 1, ...
+//            1  tile outer: every job pair of tile 0, then of tile 1, ...
+//            2  column bands: the output columns in bands of `band` tiles
+//               (the n-blocking of Section III-A), modulus outer inside a band
+//   pairing  0  adjacent jobs (2p, 2p+1): D_l E_l, F_l D_l+1, ...
+//            1  halves (p, p + ceil(J/2))
+//            2  component-major job sequence D_0..D_N-1, E_0.., F_0.., adjacent pairs
+//   kalt     1  a CTA runs the k chunks of its odd-numbered units in
+//               descending order, so a unit starts on the operands the
+//               previous wave read last (still in L2).  The reductions keep
+//               every partial sum exact in any chunk order.
 // Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner),
 // 2..9 = epilogue (warp w reads TMEM lanes 32*(w%4).. and half of the columns).
 // Every mbarrier wait is bounded; on expiry the kernel records
@@ -39,6 +53,7 @@ namespace {
 // (jb < 0 when the job count is odd and this is the last pair).
 struct Unit {
   int ja, jb, tj, ti;
+  bool desc;                        // k chunks in descending order
   int ppm;                          // planes (jobs) per modulus: 3 complex, 1 real
   int nkb, ck, nch;                 // k-blocks, k-blocks per chunk, chunks
   const CUtensorMap* mapA;          // B planes of the problem (MMA operand A)
@@ -59,7 +74,55 @@ struct Sched {
   int ck;         // k-blocks per chunk
   int nch;        // chunks
   long long units;
+  int order;      // 0 modulus outer, 1 tile outer, 2 column bands
+  int pairing;    // 0 adjacent, 1 halves, 2 component-major
+  int kalt;       // 1: descending k chunks on a CTA's odd units
+  int band;       // column tiles per band (order 2)
 };
+
+// unit index v of one problem -> (pair, tile coordinates) under the schedule
+__device__ __forceinline__ void unit_coords(long long v, int pairs, int tiles, int TJ, int TI, int group, int order,
+                                            int band, int& pair, int& tj, int& ti) {
+  if (order == 1) {                          // tile outer
+    pair = static_cast<int>(v % pairs);
+    tile_coords(static_cast<int>(v / pairs), TJ, TI, group, tj, ti);
+  } else if (order == 2) {                   // column bands, modulus outer inside
+    const long long full = static_cast<long long>(pairs) * band * TI;
+    const int b = static_cast<int>(v / full);
+    const long long r = v - b * full;
+    const int nbt = min(band, TJ - b * band);
+    const int bt = nbt * TI;
+    pair = static_cast<int>(r / bt);
+    tile_coords(static_cast<int>(r - static_cast<long long>(pair) * bt), nbt, TI, group, tj, ti);
+    tj += b * band;
+  } else {                                   // modulus outer
+    pair = static_cast<int>(v / tiles);
+    tile_coords(static_cast<int>(v % tiles), TJ, TI, group, tj, ti);
+  }
+}
+
+// jobs of pair p; J = ppm N
+__device__ __forceinline__ void pair_jobs(int p, int J, int ppm, int pairing, int& ja, int& jb) {
+  if (pairing == 1) {
+    const int h = (J + 1) >> 1;
+    ja = p;
+    jb = p + h < J ? p + h : -1;
+  } else if (pairing == 2 && ppm > 1) {      // sequence position s -> job 3 (s mod N) + s / N
+    const int N = J / ppm;
+    const int sa = 2 * p, sb = 2 * p + 1;
+    ja = (sa % N) * ppm + sa / N;
+    jb = sb < J ? (sb % N) * ppm + sb / N : -1;
+  } else {
+    ja = 2 * p;
+    jb = 2 * p + 1 < J ? 2 * p + 1 : -1;
+  }
+}
+
+// descending k chunks on the odd units a CTA processes (its units are
+// blockIdx.x, blockIdx.x + gridDim.x, ...)
+__device__ __forceinline__ bool unit_desc(long long u, int kalt) {
+  return kalt && (((u - blockIdx.x) / gridDim.x) & 1);
+}
 
 // one GEMM: tensor maps are kernel parameters
 struct SingleWork {
@@ -71,12 +134,11 @@ struct SingleWork {
   __device__ long long units() const { return s.units; }
   __device__ Unit get(long long u, int& /*hint*/) const {
     Unit w;
-    const int pair = static_cast<int>(u / s.tiles);
-    const int t = static_cast<int>(u % s.tiles);
-    w.ja = 2 * pair;
-    w.jb = (2 * pair + 1 < s.J) ? 2 * pair + 1 : -1;
+    int pair;
+    unit_coords(u, s.pairs, s.tiles, s.TJ, s.TI, s.group, s.order, s.band, pair, w.tj, w.ti);
+    pair_jobs(pair, s.J, s.ppm, s.pairing, w.ja, w.jb);
+    w.desc = unit_desc(u, s.kalt);
     w.ppm = s.ppm;
-    tile_coords(t, s.TJ, s.TI, s.group, w.tj, w.ti);
     w.nkb = s.nkb;
     w.ck = s.ck;
     w.nch = s.nch;
@@ -98,6 +160,7 @@ struct GroupProblem {  // CUtensorMap members give it 64-byte alignment
   int64_t ldr, n;
   long long unit_begin;             // first unit of this problem
   int TJ, TI, tiles, group, nkb, ck, nch, J, ppm;
+  int order, pairing, kalt, band;   // schedule, as in Sched
 };
 
 struct GroupWork {
@@ -116,12 +179,11 @@ struct GroupWork {
     const GroupProblem& P = probs[lo];
     const long long v = u - P.unit_begin;
     Unit w;
-    const int pair = static_cast<int>(v / P.tiles);
-    const int t = static_cast<int>(v % P.tiles);
-    w.ja = 2 * pair;
-    w.jb = (2 * pair + 1 < P.J) ? 2 * pair + 1 : -1;
+    int pair;
+    unit_coords(v, (P.J + 1) / 2, P.tiles, P.TJ, P.TI, P.group, P.order, P.band, pair, w.tj, w.ti);
+    pair_jobs(pair, P.J, P.ppm, P.pairing, w.ja, w.jb);
+    w.desc = unit_desc(u, P.kalt);
     w.ppm = P.ppm;
-    tile_coords(t, P.TJ, P.TI, P.group, w.tj, w.ti);
     w.nkb = P.nkb;
     w.ck = P.ck;
     w.nch = P.nch;
@@ -196,11 +258,12 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
           fenced = U.mapA;
         }
         for (int c = 0; ok && c < U.nch; ++c) {
+          const int a = U.desc ? U.nch - 1 - c : c;              // chunk of k processed c-th
           for (int which = 0; ok && which < 2; ++which) {
             const int job = which ? U.jb : U.ja;
             if (job < 0) continue;
-            const int kb1 = min(U.nkb, (c + 1) * U.ck);
-            for (int kb = c * U.ck; kb < kb1; ++kb, ++it) {
+            const int kb1 = min(U.nkb, (a + 1) * U.ck);
+            for (int kb = a * U.ck; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
@@ -239,7 +302,8 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
             if (!mbar_wait(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u, ctl)) { ok = false; break; }
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
-            const int kb0 = c * U.ck, kb1 = min(U.nkb, (c + 1) * U.ck);
+            const int a = U.desc ? U.nch - 1 - c : c;
+            const int kb0 = a * U.ck, kb1 = min(U.nkb, (a + 1) * U.ck);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
@@ -407,7 +471,8 @@ cudaError_t set_smem_attrs() {
 template <int BN>
 cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                           const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group,
-                          unsigned int* status, cudaStream_t st, int ppm, int64_t a_plane_rows, int64_t rcap) {
+                          unsigned int* status, cudaStream_t st, int ppm, int64_t a_plane_rows, int64_t rcap,
+                          const GemmSchedule& sc) {
   cudaError_t e = set_smem_attrs<BN>();
   if (e != cudaSuccess) return e;
   const int J = ppm * pl.N;
@@ -426,6 +491,10 @@ cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, co
   s.ck = chunk_k / BK;
   s.nch = (s.nkb + s.ck - 1) / s.ck;
   s.units = static_cast<long long>(s.pairs) * s.tiles;
+  s.order = sc.order;
+  s.pairing = sc.pairing;
+  s.kalt = sc.kalt;
+  s.band = sc.band_cols / BM;
   const long long grid = s.units < g_sms ? s.units : g_sms;
   gemm_f16_kernel<BN><<<static_cast<unsigned int>(grid), kThreads, Cfg<BN>::kSmemBytes, st>>>(
       mapA, mapB, pl, s, res, ldr, n, rcap, status);
@@ -442,8 +511,10 @@ int g_f16_group = 16;   // tile rasterisation group of grouped launches
 // per column (0: ldr), at most ldr and a multiple of 16.
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA,
                             const void* planesB, int8_t* res, int64_t ldr, int chunk_k, unsigned int* status,
-                            cudaStream_t st, int tile_n, int group, int ppm, int64_t a_plane_rows, int64_t rcap) {
+                            cudaStream_t st, int tile_n, int group, int ppm, int64_t a_plane_rows, int64_t rcap,
+                            const GemmSchedule& sc) {
   if (m <= 0 || n <= 0) return cudaSuccess;
+  if (!sc.valid()) return cudaErrorInvalidValue;
   if (ppm != 1 && ppm != 3) return cudaErrorInvalidValue;
   if (kpad % BK || ldr % 16 || chunk_k % BK || chunk_k < BK || chunk_k > 960) return cudaErrorInvalidValue;
   if (a_plane_rows == 0) a_plane_rows = m;
@@ -456,13 +527,13 @@ cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, 
   switch (tile_n) {
     case 64:
       return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,
-                               a_plane_rows, rcap);
+                               a_plane_rows, rcap, sc);
     case 128:
       return launch_single<128>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,
-                                a_plane_rows, rcap);
+                                a_plane_rows, rcap, sc);
     default:
       return launch_single<256>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,
-                                a_plane_rows, rcap);
+                                a_plane_rows, rcap, sc);
   }
 }
 
@@ -484,8 +555,8 @@ cudaError_t prepare_gemm_f16() {
 // running unit count, advanced past this problem's units.
 bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, const void* planesA,
                         const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,
-                        long long* unit_begin) {
-  if (!get_encoder()) return false;
+                        long long* unit_begin, const GemmSchedule& sc) {
+  if (!get_encoder() || !sc.valid()) return false;
   GroupProblem& P = *static_cast<GroupProblem*>(desc);
   std::memset(&P, 0, sizeof(P));
   const int J = 3 * N;
@@ -503,6 +574,10 @@ bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, c
   P.nkb = static_cast<int>(kpad / BK);
   P.ck = chunk_k / BK;
   P.nch = (P.nkb + P.ck - 1) / P.ck;
+  P.order = sc.order;
+  P.pairing = sc.pairing;
+  P.kalt = sc.kalt;
+  P.band = sc.band_cols / BM;
   P.unit_begin = *unit_begin;
   *unit_begin += static_cast<long long>((J + 1) / 2) * P.tiles;
   return true;

@@ -14,6 +14,8 @@
 // Element (r, h) of the source is X[r*rs + h*hs] (complex, in elements);
 // either rs == 1 (rows contiguous: one thread per row, coalesced along r) or
 // hs == 1 (entries of a row contiguous: one warp per row).
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -676,25 +678,58 @@ constexpr int64_t kStaticExpMaxRows = EMU_STATIC_EXP_MAX_ROWS;
 constexpr int kStaticMaxDevices = 64;
 
 // host code sees only a stand-in symbol: its device address comes from
-// cudaGetSymbolAddress, taken once per device in static_scratch() below
+// cudaGetSymbolAddress, taken per device (and per context) in static_scratch() below
 static __device__ __align__(256) unsigned char g_exp_scratch[kStaticExpMaxRows * 16];
 
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {};
+unsigned long long g_static_ctx[kStaticMaxDevices] = {};   // context id the address belongs to
 
-// Device address of g_exp_scratch on the current device; looked up on the
-// first call made with that device current.
+// Unique id of the calling thread's current context (cuCtxGetId, found through
+// the runtime's driver entry points); 0 when it cannot be had.  A device reset
+// makes a new primary context with a new id, and the module (with the array)
+// is loaded again at another address.
+unsigned long long current_ctx_id() {
+  using GetCur = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<GetCur>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_cur || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of g_exp_scratch on the current device.  It is looked up on
+// the first call made with that device current, and again whenever the
+// device's context has changed since (a device reset), so a stale address is
+// never used; without a context id it is looked up on every call.
 cudaError_t static_scratch(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long ctx = current_ctx_id();   // 0 before the runtime has made a context current
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  if (!g_static_ptr[dev] || ctx == 0 || g_static_ctx[dev] != ctx) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_exp_scratch);
+    e = cudaGetSymbolAddress(&p, g_exp_scratch);       // also makes the device's primary context current
     if (e != cudaSuccess) return e;
     g_static_ptr[dev] = p;
+    g_static_ctx[dev] = current_ctx_id();
   }
   *out = g_static_ptr[dev];
   return cudaSuccess;
@@ -706,16 +741,14 @@ extern "C" emu_status_t emu_stage_exponents_static(int is_single, emu_op_t trans
                                                    int64_t m, int64_t n, int64_t k, const void* A,
                                                    int64_t lda, const void* B, int64_t ldb, int num_moduli,
                                                    int16_t* x, int16_t* y, void* stream) {
-  const bool ok_ops = (transa == EMU_OP_N || transa == EMU_OP_T || transa == EMU_OP_C) &&
-                      (transb == EMU_OP_N || transb == EMU_OP_T || transb == EMU_OP_C);
-  if (!ok_ops || m < 0 || n < 0 || k < 0) return EMU_ERR_INVALID_ARG;
-  const int64_t rows_a = transa == EMU_OP_N ? m : k;
-  const int64_t rows_b = transb == EMU_OP_N ? k : n;
-  if (lda < (rows_a > 1 ? rows_a : 1) || ldb < (rows_b > 1 ? rows_b : 1)) return EMU_ERR_INVALID_ARG;
-  if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
-  if (k > EMU_MAX_K) return EMU_ERR_K_TOO_LARGE;
+  // argument checks, and the bad-parameter index, as in emu_stage_exponents
+  emu_status_t s = emu::check_stage_args(transa, transb, m, n, k, lda, ldb, num_moduli);
+  if (s != EMU_OK) return s;
   if (m > kStaticExpMaxRows || n > kStaticExpMaxRows) return EMU_ERR_SIZE_LIMIT;
-  if ((m > 0 && !x) || (n > 0 && !y) || (k > 0 && ((m > 0 && !A) || (n > 0 && !B)))) return EMU_ERR_INVALID_ARG;
+  if (k > 0 && m > 0 && !A) return emu::set_bad_param(7);
+  if (k > 0 && n > 0 && !B) return emu::set_bad_param(9);
+  if (m > 0 && !x) return emu::set_bad_param(12);
+  if (n > 0 && !y) return emu::set_bad_param(13);
   void* scratch = nullptr;
   if (static_scratch(&scratch) != cudaSuccess) return EMU_ERR_CUDA;
   const emu::Plan* pl = emu::get_plan(num_moduli);

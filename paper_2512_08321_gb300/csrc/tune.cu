@@ -1,11 +1,15 @@
 // Autotuner of the single-GEMM launch configuration.  For one problem shape it
-// times, on synthetic data of that shape and with CUDA events, every
-// candidate of each phase's knobs (the phases are independent, so each is
-// timed on its own): the residue-product tile width, rasterisation group and
-// reduction chunk; the CRT rows per thread; the split entries per thread.  The
-// winners are kept per (dtype, N, ceil(log2) of m, n, k) and used by later
-// calls in that bucket; EMU_AUTOTUNE_CACHE names a file that keeps the table
-// across processes.
+// times, on synthetic data of that shape and with CUDA events, the candidates
+// of each phase's knobs (the phases are independent, so each is timed on its
+// own): the residue-product tile width, rasterisation group and reduction
+// chunk, then the modulus-loop schedule of those products (unit order, among
+// them the paper's n-blocked order of Section III-A; k direction; job
+// pairing), searched one knob at a time from the best so far; the CRT rows per
+// thread; the split entries per thread.  A candidate replaces the incumbent
+// only when it is at least 0.5 % faster, so timing noise does not move the
+// choice.  The winners are kept per (dtype, N, ceil(log2) of m, n, k) and used
+// by later calls in that bucket; EMU_AUTOTUNE_CACHE names a file that keeps
+// the table across processes.
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -20,6 +24,10 @@ namespace emu {
 namespace {
 
 using Key = std::tuple<int, int, int, int, int>;
+
+// cache lines: tag, dtype, N, the three log2 buckets, then tile_n group chunk_k
+// crt_rows split_elems order pairing kdir band
+constexpr const char* kCacheTag = "gemm2";
 
 std::mutex g_mu;
 Tune g_default;
@@ -36,6 +44,23 @@ Key key_of(int dtype, int N, int64_t m, int64_t n, int64_t k) {
   return Key(dtype, N, bucket(m), bucket(n), bucket(k));
 }
 
+bool valid(int key, int v) {
+  switch (key) {
+    case EMU_TUNE_TILE_N: return v == 64 || v == 128 || v == 256;
+    case EMU_TUNE_GROUP: return v >= 1 && v <= 64;
+    case EMU_TUNE_CHUNK_K: return v >= 64 && v <= 960 && v % 64 == 0;
+    case EMU_TUNE_CRT_ROWS: return v == 1 || v == 2 || v == 4;
+    case EMU_TUNE_SPLIT_ELEMS: return v == 2 || v == 4;
+    case EMU_TUNE_NBLOCK: return v == 0 || (v >= 128 && v % 128 == 0);
+    case EMU_TUNE_OVERLAP: return v == -1 || v == 0 || v == 1;
+    case EMU_TUNE_ORDER: return v >= 0 && v <= 2;
+    case EMU_TUNE_PAIRING: return v >= 0 && v <= 2;
+    case EMU_TUNE_KDIR: return v == 0 || v == 1;
+    case EMU_TUNE_BAND: return v >= 128 && v <= 65536 && v % 128 == 0;
+    default: return false;
+  }
+}
+
 void load_locked() {
   if (g_loaded) return;
   g_loaded = true;
@@ -47,16 +72,23 @@ void load_locked() {
   int s, N, bm, bn, bk;
   Tune t;
   while (std::fscanf(f, "%63s", tag) == 1) {
-    if (std::string(tag) != "gemm") {   // other tables share the file: skip the line
+    if (std::string(tag) != kCacheTag) {   // other tables (or older formats) share the file: skip the line
       int c;
       while ((c = std::fgetc(f)) != EOF && c != '\n') {
       }
       continue;
     }
-    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n, &t.group, &t.chunk_k,
-                    &t.crt_rows, &t.split_elems) != 10)
+    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n, &t.group,
+                    &t.chunk_k, &t.crt_rows, &t.split_elems, &t.sched.order, &t.sched.pairing, &t.sched.kalt,
+                    &t.sched.band_cols) != 14)
       break;
-    g_table[Key(s, N, bm, bn, bk)] = t;
+    // a stale or hand-edited entry with a value the launchers would refuse is skipped,
+    // so the defaults stay in force for its bucket
+    if (valid(EMU_TUNE_TILE_N, t.tile_n) && valid(EMU_TUNE_GROUP, t.group) && valid(EMU_TUNE_CHUNK_K, t.chunk_k) &&
+        valid(EMU_TUNE_CRT_ROWS, t.crt_rows) && valid(EMU_TUNE_SPLIT_ELEMS, t.split_elems) && t.sched.valid())
+      g_table[Key(s, N, bm, bn, bk)] = t;
+    else
+      std::fprintf(stderr, "ozaki2emu: ignoring invalid autotune cache entry for dtype %d, N %d\n", s, N);
   }
   std::fclose(f);
 }
@@ -69,7 +101,7 @@ void save_locked() {
   if (FILE* f = std::fopen(path, "r")) {
     char line[4096];
     while (std::fgets(line, sizeof(line), f))
-      if (std::string(line).rfind("gemm ", 0) != 0) keep.push_back(line);
+      if (std::string(line).rfind(std::string(kCacheTag) + " ", 0) != 0) keep.push_back(line);
     std::fclose(f);
   }
   FILE* f = std::fopen(path, "w");
@@ -78,23 +110,11 @@ void save_locked() {
   for (const auto& kv : g_table) {
     const Key& k = kv.first;
     const Tune& t = kv.second;
-    std::fprintf(f, "gemm %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-                 std::get<3>(k), std::get<4>(k), t.tile_n, t.group, t.chunk_k, t.crt_rows, t.split_elems);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", kCacheTag, std::get<0>(k), std::get<1>(k),
+                 std::get<2>(k), std::get<3>(k), std::get<4>(k), t.tile_n, t.group, t.chunk_k, t.crt_rows,
+                 t.split_elems, t.sched.order, t.sched.pairing, t.sched.kalt, t.sched.band_cols);
   }
   std::fclose(f);
-}
-
-bool valid(int key, int v) {
-  switch (key) {
-    case EMU_TUNE_TILE_N: return v == 64 || v == 128 || v == 256;
-    case EMU_TUNE_GROUP: return v >= 1 && v <= 64;
-    case EMU_TUNE_CHUNK_K: return v >= 64 && v <= 960 && v % 64 == 0;
-    case EMU_TUNE_CRT_ROWS: return v == 1 || v == 2 || v == 4;
-    case EMU_TUNE_SPLIT_ELEMS: return v == 2 || v == 4;
-    case EMU_TUNE_NBLOCK: return v == 0 || (v >= 128 && v % 128 == 0);
-    case EMU_TUNE_OVERLAP: return v == -1 || v == 0 || v == 1;
-    default: return false;
-  }
 }
 
 void set(Tune& t, int key, int v) {
@@ -106,6 +126,10 @@ void set(Tune& t, int key, int v) {
     case EMU_TUNE_SPLIT_ELEMS: t.split_elems = v; break;
     case EMU_TUNE_NBLOCK: t.nblock = v; break;
     case EMU_TUNE_OVERLAP: t.overlap = v; break;
+    case EMU_TUNE_ORDER: t.sched.order = v; break;
+    case EMU_TUNE_PAIRING: t.sched.pairing = v; break;
+    case EMU_TUNE_KDIR: t.sched.kalt = v; break;
+    case EMU_TUNE_BAND: t.sched.band_cols = v; break;
     default: break;
   }
 }
@@ -152,6 +176,8 @@ float time_min(cudaStream_t st, cudaEvent_t a, cudaEvent_t b, int reps, F fn) {
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
+constexpr float kKeep = 0.995f;   // a candidate must beat the incumbent by 0.5 %
+
 }  // namespace
 
 Tune tune_for(int dtype, int N, int64_t m, int64_t n, int64_t k) {
@@ -191,6 +217,28 @@ int emu_get_tuning(int key) {
     case EMU_TUNE_SPLIT_ELEMS: return t.split_elems;
     case EMU_TUNE_NBLOCK: return t.nblock;
     case EMU_TUNE_OVERLAP: return t.overlap;
+    case EMU_TUNE_ORDER: return t.sched.order;
+    case EMU_TUNE_PAIRING: return t.sched.pairing;
+    case EMU_TUNE_KDIR: return t.sched.kalt;
+    case EMU_TUNE_BAND: return t.sched.band_cols;
+    default: return -1;
+  }
+}
+
+int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, int key) {
+  const emu::Tune t = emu::tune_for(dtype, num_moduli, m, n, k);
+  switch (key) {
+    case EMU_TUNE_TILE_N: return t.tile_n;
+    case EMU_TUNE_GROUP: return t.group;
+    case EMU_TUNE_CHUNK_K: return t.chunk_k;
+    case EMU_TUNE_CRT_ROWS: return t.crt_rows;
+    case EMU_TUNE_SPLIT_ELEMS: return t.split_elems;
+    case EMU_TUNE_NBLOCK: return t.nblock;
+    case EMU_TUNE_OVERLAP: return t.overlap;
+    case EMU_TUNE_ORDER: return t.sched.order;
+    case EMU_TUNE_PAIRING: return t.sched.pairing;
+    case EMU_TUNE_KDIR: return t.sched.kalt;
+    case EMU_TUNE_BAND: return t.sched.band_cols;
     default: return -1;
   }
 }
@@ -260,7 +308,7 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
         launch_split(single, false, M + oA, m, k, 1, m, *pl, x, true, kpad, M + opa, st, e, real);
         launch_split(single, false, M + oB, n, k, k, 1, *pl, y, true, kpad, M + opb, st, e, real);
       });
-      if (ms < bt) {
+      if (ms < kKeep * bt) {
         bt = ms;
         t.split_elems = e;
       }
@@ -268,8 +316,9 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
     // residue products: tile width x group x chunk
     bt = 1e30f;
     const bool big = static_cast<double>(m) * n * k * num_moduli > 4e13;
-    const std::vector<int> tiles = m <= 256 ? std::vector<int>{64, 128, 256} : std::vector<int>{128, 256};
-    const std::vector<int> groups = big ? std::vector<int>{16, 32} : std::vector<int>{8, 16, 32};
+    // the defaults first: a candidate must beat the incumbent by 0.5 % to replace it
+    const std::vector<int> tiles = m <= 256 ? std::vector<int>{256, 128, 64} : std::vector<int>{256, 128};
+    const std::vector<int> groups = big ? std::vector<int>{16, 32} : std::vector<int>{16, 8, 32};
     const std::vector<int> chunks = big ? std::vector<int>{960} : std::vector<int>{960, 512};
     if (prepare_gemm_f16() != cudaSuccess) ok = false;
     for (int tn : tiles)
@@ -278,15 +327,65 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
           if (!ok) break;
           const float ms = time_min(st, a, b, reps, [&] {
             launch_gemm_f16(m, n, kpad, *pl, M + opa, M + opb, reinterpret_cast<int8_t*>(M + ores), ldr, c, status,
-                            st, tn, g, ppm);
+                            st, tn, g, ppm, 0, 0, GemmSchedule());
           });
-          if (ms < bt) {
+          if (ms < kKeep * bt) {
             bt = ms;
             t.tile_n = tn;
             t.group = g;
             t.chunk_k = c;
           }
         }
+    // modulus-loop schedule of the residue products, one knob at a time from the best so far:
+    // unit order (modulus outer; tile outer; column bands of the paper's 8192 columns and of 2048),
+    // then alternating k direction, then job pairing
+    GemmSchedule sc;
+    auto time_sched = [&](const GemmSchedule& cand) {
+      return time_min(st, a, b, reps, [&] {
+        launch_gemm_f16(m, n, kpad, *pl, M + opa, M + opb, reinterpret_cast<int8_t*>(M + ores), ldr, t.chunk_k,
+                        status, st, t.tile_n, t.group, ppm, 0, 0, cand);
+      });
+    };
+    std::vector<GemmSchedule> orders;
+    {
+      GemmSchedule c = sc;
+      c.order = 1;
+      orders.push_back(c);
+      for (int bc : {8192, 2048}) {
+        if (n <= bc) continue;                 // one band: the same order as modulus outer
+        c.order = 2;
+        c.band_cols = bc;
+        orders.push_back(c);
+      }
+    }
+    for (const GemmSchedule& c : orders) {
+      if (!ok) break;
+      const float ms = time_sched(c);
+      if (ms < kKeep * bt) {
+        bt = ms;
+        sc = c;
+      }
+    }
+    {
+      GemmSchedule c = sc;
+      c.kalt = 1;
+      const float ms = time_sched(c);
+      if (ms < kKeep * bt) {
+        bt = ms;
+        sc = c;
+      }
+    }
+    for (int pr : {1, 2}) {
+      if (real && pr == 2) continue;           // one job per modulus: the same as adjacent
+      GemmSchedule c = sc;
+      c.pairing = pr;
+      const float ms = time_sched(c);
+      if (ms < kKeep * bt) {
+        bt = ms;
+        sc = c;
+      }
+    }
+    t.sched = sc;
     // CRT: rows per thread
     bt = 1e30f;
     for (int r : {4, 2, 1}) {
@@ -294,7 +393,7 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
         launch_crt(single, m, n, *pl, reinterpret_cast<int8_t*>(M + ores), ldr, x, y, 1.0, 0.0, 0.0, 0.0, M + oC, m,
                    st, r, real);
       });
-      if (ms < bt) {
+      if (ms < kKeep * bt) {
         bt = ms;
         t.crt_rows = r;
       }

@@ -98,6 +98,7 @@ _SIGS = [
     ("emu_set_crt_mode", _c_int, [_c_int]),
     ("emu_set_tuning", _c_int, [_c_int, _c_int]),
     ("emu_get_tuning", _c_int, [_c_int]),
+    ("emu_tuned_value", _c_int, [_c_int, _c_int, _c_i64, _c_i64, _c_i64, _c_int]),
     ("emu_autotune_gemm", _c_int, [_c_int, _c_i64, _c_i64, _c_i64, _c_int, ctypes.POINTER(_c_int)]),
     ("emu_autotune_clear", _c_int, []),
     ("emu_set_scaling", _c_int, [_c_int]),
@@ -379,6 +380,9 @@ EMU_CRT_EXACT, EMU_CRT_PAPER_FP64 = 0, 1
 EMU_TUNE_TILE_N, EMU_TUNE_GROUP, EMU_TUNE_CHUNK_K, EMU_TUNE_CRT_ROWS, EMU_TUNE_SPLIT_ELEMS = 1, 2, 3, 4, 5
 EMU_TUNE_NBLOCK = 6
 EMU_TUNE_OVERLAP = 7
+EMU_TUNE_ORDER, EMU_TUNE_PAIRING, EMU_TUNE_KDIR, EMU_TUNE_BAND = 8, 9, 10, 11
+SCHEDULE_KNOBS = {"order": EMU_TUNE_ORDER, "pairing": EMU_TUNE_PAIRING, "kdir": EMU_TUNE_KDIR,
+                  "band": EMU_TUNE_BAND}
 
 
 def emu_set_tuning(key, value):
@@ -387,6 +391,10 @@ def emu_set_tuning(key, value):
 
 def emu_get_tuning(key):
     return lib().emu_get_tuning(int(key))
+
+
+def emu_tuned_value(dtype, num_moduli, m, n, k, key):
+    return lib().emu_tuned_value(int(dtype), int(num_moduli), m, n, k, int(key))
 
 
 def emu_autotune_gemm(dtype, m, n, k, num_moduli):

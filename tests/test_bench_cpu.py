@@ -11,22 +11,28 @@ SUMMARY = "gemm_f16_zgemm16384.txt"
 
 
 def _tree(tmp_path):
-    """A copy of the summary and the kernel sources in the layout bench.py reads."""
+    """The kernel sources in the layout bench.py reads, and a summary in the
+    committed summaries' format recording their current sha256."""
     root = tmp_path / "repo"
     (root / "profiles").mkdir(parents=True)
     csrc = root / "paper_2512_08321_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", SUMMARY), root / "profiles" / SUMMARY)
     for f in SOURCES:
         shutil.copy(os.path.join(bench.ROOT, "paper_2512_08321_gb300", "csrc", f), csrc / f)
+    import hashlib
+    h = hashlib.sha256()
+    for f in SOURCES:
+        h.update((csrc / f).read_bytes())
+    (root / "profiles" / SUMMARY).write_text(
+        "# a summary\nkernel: gemm_f16_kernel\ndram_bytes_per_launch_full_size: 1.5e11\n"
+        f"source_sha256: {h.hexdigest()}\n")
     return root
 
 
 def test_traffic_read_while_sources_match(tmp_path, monkeypatch):
     root = _tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    v = bench.profile_traffic(SOURCES, SUMMARY)
-    assert v is not None and v > 0
+    assert bench.profile_traffic(SOURCES, SUMMARY) == 1.5e11
 
 
 def test_traffic_dropped_when_either_source_changes(tmp_path, monkeypatch):

@@ -7,6 +7,8 @@ scratch is a fixed array inside the library.  Its results must equal those of
 emu_stage_exponents, on consecutive calls that reuse the same array.  This
 file is collected last so a failure here stops a -x run only after every
 other test has run."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -57,3 +59,74 @@ def test_static_rejects_sizes_beyond_its_array():
     assert st == emu.EMU_ERR_SIZE_LIMIT
     st = emu.emu_stage_exponents_static(0, "N", "N", 4, big, 4, 0, 4, 0, 4, 14, 0, 0)
     assert st == emu.EMU_ERR_SIZE_LIMIT
+
+
+def _cudart():
+    """The CUDA runtime already loaded into this process (by the library or torch)."""
+    for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("no CUDA runtime library found by name")
+
+
+_USED_MEM_CURRENT, _USED_MEM_HIGH = 7, 8      # cudaMemPoolAttrUsedMemCurrent / cudaMemPoolAttrUsedMemHigh
+
+
+def _pool_attr(rt, pool, attr):
+    v = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolGetAttribute(pool, attr, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_static_allocates_nothing():
+    """Across a warmed-up static call neither the device's free memory nor the
+    stream-ordered pool's high-water mark moves: no cudaMalloc and no
+    cudaMallocAsync happened (the allocating entry point uses the latter)."""
+    rt = _cudart()
+    A = paper_matrix(4000, 600, 2.0, 11)
+    B = paper_matrix(600, 3000, 2.0, 12)
+    dA, dB = dev(A), dev(B)
+    m, k = A.shape
+    n = B.shape[1]
+    x = torch.empty(m, dtype=torch.int16, device="cuda")
+    y = torch.empty(n, dtype=torch.int16, device="cuda")
+
+    def call():
+        emu.check(emu.emu_stage_exponents_static(0, "N", "N", m, n, k, dA.data_ptr(), dA.shape[1], dB.data_ptr(),
+                                                 dB.shape[1], 16, x.data_ptr(), y.data_ptr()), "static")
+        torch.cuda.synchronize()
+
+    call()                                            # modules loaded, address looked up
+    dev_id = torch.cuda.current_device()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), dev_id) == 0
+    zero = ctypes.c_uint64(0)
+    assert rt.cudaMemPoolSetAttribute(pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0   # reset to current
+    used0 = _pool_attr(rt, pool, _USED_MEM_CURRENT)
+    free0, total = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert rt.cudaMemGetInfo(ctypes.byref(free0), ctypes.byref(total)) == 0
+    for _ in range(3):
+        call()
+    free1 = ctypes.c_size_t(0)
+    assert rt.cudaMemGetInfo(ctypes.byref(free1), ctypes.byref(total)) == 0
+    assert _pool_attr(rt, pool, _USED_MEM_HIGH) == used0
+    assert free1.value == free0.value
+    # the check itself can see an allocation: the allocating entry point raises the pool's mark
+    xa = torch.empty(m, dtype=torch.int16, device="cuda")
+    ya = torch.empty(n, dtype=torch.int16, device="cuda")
+    emu.check(emu.emu_stage_exponents(0, "N", "N", m, n, k, dA.data_ptr(), dA.shape[1], dB.data_ptr(), dB.shape[1],
+                                      16, xa.data_ptr(), ya.data_ptr()), "allocating")
+    torch.cuda.synchronize()
+    assert _pool_attr(rt, pool, _USED_MEM_HIGH) > used0
+    assert torch.equal(xa, x) and torch.equal(ya, y)
+
+
+def test_static_bad_pointer_sets_the_parameter_index():
+    st = emu.emu_stage_exponents_static(0, "N", "N", 8, 8, 8, 0, 8, 0, 8, 14, 0, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 7
+    st = emu.emu_stage_exponents_static(0, 7, "N", 8, 8, 8, 0, 8, 0, 8, 14, 0, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 1
+    st = emu.emu_stage_exponents_static(0, "N", "N", 8, 8, 8, 0, 4, 0, 8, 14, 0, 0)
+    assert st == emu.EMU_ERR_INVALID_ARG and emu.emu_last_bad_param() == 8
