@@ -337,6 +337,11 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *                        every other unit of a persistent block
  *   EMU_TUNE_BAND        columns per band for EMU_TUNE_ORDER 2, a multiple of
  *                        128 (default 8192, the paper's block)
+ *   EMU_TUNE_CRT_ENGINE  CRT: 1 (default) the sum over moduli as an exact fp16
+ *                        product with digits of the CRT weights on the tensor
+ *                        cores, 0 limb products on the CUDA cores (also used,
+ *                        whatever the setting, for a CRT running beside residue
+ *                        products on the library's second stream)
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
  * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
@@ -348,7 +353,8 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  * value that a call of the given dtype, N and shape will use (the autotuned
  * entry of its bucket, else the process default; -1 for an unknown key).
  * The autotuner searches the tile width, group and chunk, then the schedule
- * knobs 8-11 one at a time, then the CRT rows and split entries. */
+ * knobs 8-11 one at a time, then the CRT engine (and the CUDA-core kernel's
+ * rows) and the split entries. */
 #define EMU_TUNE_TILE_N 1
 #define EMU_TUNE_GROUP 2
 #define EMU_TUNE_CHUNK_K 3
@@ -360,6 +366,7 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 #define EMU_TUNE_PAIRING 9
 #define EMU_TUNE_KDIR 10
 #define EMU_TUNE_BAND 11
+#define EMU_TUNE_CRT_ENGINE 12
 emu_status_t emu_set_tuning(int key, int value);
 int emu_get_tuning(int key);
 int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, int key);

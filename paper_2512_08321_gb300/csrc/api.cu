@@ -302,16 +302,21 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     return k > 0 ? static_cast<const void*>(static_cast<const char*>(B) + static_cast<size_t>(j0) * rsb * in_esz)
                  : B;
   };
+  // beside_products: the CRT runs on the library's stream next to residue products, which hold all
+  // of an SM's TMEM, so it takes the CUDA-core kernel (the tensor-core one would wait for TMEM)
   auto crt_on = [&](cudaStream_t cs, int64_t mi, int64_t nj, const int8_t* r, const int16_t* xi,
-                    const int16_t* yj, void* Ci) {
-    return cuda_status(g_crt_mode == 1
-                           ? launch_crt_fp(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
-                                           dt.real)
-                           : launch_crt(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
-                                        tn.crt_rows, dt.real, accurate));
+                    const int16_t* yj, void* Ci, bool beside_products) {
+    if (g_crt_mode == 1)
+      return cuda_status(launch_crt_fp(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
+                                       dt.real));
+    if (tn.crt_engine == 1 && !beside_products)
+      return cuda_status(launch_crt_tc(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
+                                       dt.real, accurate, ds->status));
+    return cuda_status(launch_crt(dt.single, mi, nj, *pl, r, L.ldr, xi, yj, ar, ai, br, bi, Ci, ldc, cs,
+                                  tn.crt_rows, dt.real, accurate));
   };
   auto crt = [&](int64_t mi, int64_t nj, const int8_t* r, const int16_t* xi, const int16_t* yj, void* Ci) {
-    return crt_on(st, mi, nj, r, xi, yj, Ci);
+    return crt_on(st, mi, nj, r, xi, yj, Ci, false);
   };
   cudaError_t e;
   phase(0, st);
@@ -342,7 +347,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
       if (cudaStreamWaitEvent(ax, ds->ev_gemm[b & 1], 0) != cudaSuccess) return EMU_ERR_CUDA;
       const int64_t j0 = b * nb;
       void* Cj = static_cast<char*>(C) + static_cast<size_t>(j0) * ldc * in_esz;
-      const emu_status_t r = crt_on(ax, m, width(b), rbuf(b), x, y + j0, Cj);
+      const emu_status_t r = crt_on(ax, m, width(b), rbuf(b), x, y + j0, Cj, true);
       if (r != EMU_OK) return r;
       return cuda_status(cudaEventRecord(ds->ev_crt[b & 1], ax));
     };
@@ -718,11 +723,14 @@ emu_status_t emu_stage_crt(int is_single, int64_t m, int64_t n, int num_moduli, 
     ar = a[0]; ai = a[1]; br = b[0]; bi = b[1];
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return emu::cuda_status(emu::g_crt_mode == 1
-                              ? emu::launch_crt_fp(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
-                                                   ldc, st)
-                              : emu::launch_crt(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
-                                                ldc, st));
+  if (emu::g_crt_mode == 1)
+    return emu::cuda_status(emu::launch_crt_fp(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
+                                               ldc, st));
+  if (emu_get_tuning(EMU_TUNE_CRT_ENGINE) == 1)
+    return emu::cuda_status(emu::launch_crt_tc(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
+                                               ldc, st, false, false, ds->status));
+  return emu::cuda_status(emu::launch_crt(is_single != 0, m, n, *pl, residues, ldr, x, y, ar, ai, br, bi, C,
+                                          ldc, st));
 }
 
 emu_status_t emu_set_scaling(int mode) {

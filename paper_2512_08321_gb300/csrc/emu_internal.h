@@ -20,6 +20,7 @@ constexpr int kAccuPreBits = 5;     // accurate mode: pre-scaling 2^(5 - e), mag
 constexpr int16_t kExpNonfinite = EMU_EXP_NONFINITE;
 // moduli-selection network
 constexpr int kMlpIn = 39, kMlpHidden = 64, kMlpOut = 21, kMlpNmin = 4;
+constexpr int kTcDigits = 30;       // tensor-core CRT: digit slots per part (the largest layout)
 constexpr int kMlpParams = kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden +
                            kMlpOut * kMlpHidden + kMlpOut;
 
@@ -48,6 +49,15 @@ struct Plan {
   int nchunk_accu;                        // the same for accurate-mode exponents
   float w13[kMaxModuli][kMaxChunks];      // 2^(13 t) mod p_l, symmetric, as float
   float inv_p[kMaxModuli];                // 1 / p_l rounded to float
+  // tensor-core CRT (k_crt_tc.cu): the sum over moduli as an exact fp16 product of
+  // the residues with balanced digits of the weights, w_l = sum_c dig[c] 2^(b c),
+  // |dig| <= 2^(b-1); [0]: b = 10, [1]: b = 9
+  int16_t tcdig[2][kMaxModuli][kTcDigits];
+  uint16_t tcest[kMaxModuli][2];          // fp16 bits of hi, lo with hi + lo ~= w_l / P
+  uint32_t tcmul[2][kTcDigits];           // 2^((b c) mod 32): digit c's shift inside its limb
+  // R0 P - (bits of 1.5 * 2^23) * sum_c 2^(b c) over the digit slots of a layout
+  // (mod 2^(32L)): [0] complex 14 slots b = 10, [1] complex 30 slots b = 9, [2] real 30 slots b = 10
+  uint32_t tcK[3][kMaxLimbs];
   // the paper's floating-point CRT (Section II, eq. CRTaccumulation)
   double s1[kMaxModuli];                  // upper bits of w_l on the common grid 2^g
   double s2[kMaxModuli];                  // RN(w_l - s1_l)
@@ -107,7 +117,8 @@ struct Tune {
   int group = 16;        // residue products: tile rasterisation group
   int chunk_k = 960;     // residue products: k between in-TMEM reductions (64..960; 960 the largest
                          // exact one: 960 products of at most 2^14 plus a residue stay below 2^24)
-  int crt_rows = 4;      // CRT: rows per thread (1, 2, 4)
+  int crt_rows = 4;      // CRT: rows per thread (1, 2, 4) of the CUDA-core kernel
+  int crt_engine = 1;    // CRT: 1 the sum over moduli on the tensor cores, 0 on the CUDA cores
   int split_elems = 4;   // split: entries per thread (2, 4)
   int nblock = 0;        // output columns per block (0: automatic, by workspace size)
   int overlap = -1;      // split and CRT of neighbouring column blocks beside the residue products:
@@ -141,6 +152,13 @@ cudaError_t launch_crt(bool single, int64_t m, int64_t n, const Plan& pl,
                        double ar, double ai, double br, double bi,
                        void* C, int64_t ldc, cudaStream_t st, int rows_per_thread = 4, bool real = false,
                        bool robust = false);
+
+// The same CRT with its sum over moduli on the tensor cores (k_crt_tc.cu): bit-identical
+// results.  Each block holds TMEM for its whole run, so it must not run beside the residue
+// products (which take all of an SM's TMEM); status receives EMU_ERR_TIMEOUT if a wait expires.
+cudaError_t launch_crt_tc(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
+                          const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
+                          int64_t ldc, cudaStream_t st, bool real, bool robust, unsigned int* status);
 
 cudaError_t launch_crt_fp(bool single, int64_t m, int64_t n, const Plan& pl, const int8_t* res, int64_t ldr,
                           const int16_t* x, const int16_t* y, double ar, double ai, double br, double bi, void* C,
@@ -186,6 +204,7 @@ struct CrtProb {
   double ar, ai, br, bi;
   long long block_begin;
   int iblocks;
+  int flags;                // alpha/beta case (crt_common.cuh: kCrtPlain, kCrtBeta), set by crt_prob_blocks
 };
 // block counts of one segment/problem in the grouped launches
 long long exp_seg_blocks(ExpSeg& s);       // sets hchunks, rows_contig; returns blocks
@@ -198,6 +217,10 @@ cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_de
                                  const Plan& pl, cudaStream_t st);
 cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob, long long blocks, const Plan& pl,
                                cudaStream_t st);
+// the grouped CRT on the tensor cores (k_crt_tc.cu): items of 128 rows
+long long crt_tc_prob_items(CrtProb& c);   // sets iblocks (128-row blocks) and flags; returns items
+cudaError_t launch_crt_tc_grouped(bool single, const CrtProb* probs_dev, int nprob, long long items, const Plan& pl,
+                                  unsigned int* status, cudaStream_t st, bool prepare_only = false);
 size_t group_problem_bytes();
 bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, const void* planesA,
                         const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,

@@ -40,6 +40,9 @@ struct emu_grouped_s {
   emu::CrtProb* d_crt = nullptr;
   int ncrt = 0;
   long long crt_blocks = 0;
+  emu::CrtProb* d_crt_tc = nullptr;   // the same problems in 128-row items (tensor-core CRT)
+  long long crt_tc_items = 0;
+  int crt_engine = 1;               // EMU_TUNE_CRT_ENGINE at plan creation
   unsigned int* status = nullptr;
   int kernels = 0;                // kernel launches in one replay
   cudaGraph_t graph = nullptr;
@@ -125,6 +128,14 @@ emu_status_t upload_gemm_descs(emu_grouped_s* g, int tile_n, void* d_dst, long l
   return EMU_OK;
 }
 
+// Phase 4: the CRT of every problem, on the tensor cores or the CUDA cores (the engine the
+// process default named when the plan was created).
+cudaError_t crt_phase(emu_grouped_s* g, cudaStream_t st) {
+  if (g->crt_engine == 1)
+    return launch_crt_tc_grouped(g->single, g->d_crt_tc, g->ncrt, g->crt_tc_items, *g->pl, g->status, st);
+  return launch_crt_grouped(g->single, g->d_crt, g->ncrt, g->crt_blocks, *g->pl, st);
+}
+
 // Phases 1-2 (exponents, split) and 4 (CRT) around a given residue-product launch.
 cudaError_t enqueue(emu_grouped_s* g, cudaStream_t st, bool with_gemm) {
   cudaError_t e = cudaMemsetAsync(g->mem + g->scratch_off, 0, g->scratch_bytes, st);
@@ -138,7 +149,7 @@ cudaError_t enqueue(emu_grouped_s* g, cudaStream_t st, bool with_gemm) {
   if ((e = launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->tile_n, g->status, st)) !=
       cudaSuccess)
     return e;
-  return launch_crt_grouped(g->single, g->d_crt, g->ncrt, g->crt_blocks, *g->pl, st);
+  return crt_phase(g, st);
 }
 
 // Time the residue-product launch for each tile width on this problem set.
@@ -257,6 +268,7 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
   const size_t off_split = o;   o += al(sizeof(SplitSeg) * 2 * nl + 1);
   const size_t off_gp = o;      o += al((group_problem_bytes() + sizeof(long long)) * nl + 1);
   const size_t off_crt = o;     o += al(sizeof(CrtProb) * nl + 1);
+  const size_t off_crt_tc = o;  o += al(sizeof(CrtProb) * nl + 1);
   g->mem_bytes = o;
   if (cudaMalloc(&g->mem, o) != cudaSuccess) {
     cudaGetLastError();
@@ -267,8 +279,8 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
   std::vector<ExpSeg> es;
   std::vector<long long> rowb;
   std::vector<SplitSeg> ss;
-  std::vector<CrtProb> cp;
-  long long eb = 0, sb = 0, cb = 0, rows = 0;
+  std::vector<CrtProb> cp, cpt;
+  long long eb = 0, sb = 0, cb = 0, ct = 0, rows = 0;
   for (int i : live) {
     const Off& f = off[i];
     int16_t* x = reinterpret_cast<int16_t*>(M + f.x);
@@ -321,9 +333,13 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
     c.ai = alpha[2 * i + 1];
     c.br = beta[2 * i];
     c.bi = beta[2 * i + 1];
+    CrtProb t = c;
     c.block_begin = cb;
     cb += crt_prob_blocks(c);
     cp.push_back(c);
+    t.block_begin = ct;
+    ct += crt_tc_prob_items(t);
+    cpt.push_back(t);
     g->probs.push_back({m[i], n[i], f.kpad, f.ldr, M + f.pa, M + f.pb, reinterpret_cast<int8_t*>(M + f.res)});
   }
   rowb.push_back(rows);
@@ -332,6 +348,9 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
   g->d_split = reinterpret_cast<SplitSeg*>(M + off_split);
   g->d_gp = M + off_gp;
   g->d_crt = reinterpret_cast<CrtProb*>(M + off_crt);
+  g->d_crt_tc = reinterpret_cast<CrtProb*>(M + off_crt_tc);
+  g->crt_tc_items = ct;
+  g->crt_engine = emu_get_tuning(EMU_TUNE_CRT_ENGINE) == 1 ? 1 : 0;
   g->nexp = g->nsplit = static_cast<int>(es.size());
   g->ngp = g->ncrt = static_cast<int>(cp.size());
   g->exp_blocks = eb;
@@ -344,10 +363,13 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
     ok &= cudaMemcpy(g->d_rowbeg, rowb.data(), sizeof(long long) * rowb.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(g->d_split, ss.data(), sizeof(SplitSeg) * ss.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(g->d_crt, cp.data(), sizeof(CrtProb) * cp.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(g->d_crt_tc, cpt.data(), sizeof(CrtProb) * cpt.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   }
   cudaStream_t st = nullptr;
   ok &= cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
   ok &= prepare_gemm_f16() == cudaSuccess;
+  if (g->crt_engine == 1)
+    ok &= launch_crt_tc_grouped(g->single, nullptr, 0, 0, *g->pl, nullptr, nullptr, true) == cudaSuccess;
   if (ok && !cp.empty()) {
     int tn = tile_n;
     if (tn == 0) {
@@ -412,7 +434,7 @@ emu_status_t emu_grouped_phase_times(emu_grouped_t g, float* ms, void* stream) {
   ok = ok && launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->tile_n, g->status, st) ==
                  cudaSuccess;
   ok = ok && cudaEventRecord(ev[3], st) == cudaSuccess;
-  ok = ok && launch_crt_grouped(g->single, g->d_crt, g->ncrt, g->crt_blocks, *g->pl, st) == cudaSuccess;
+  ok = ok && crt_phase(g, st) == cudaSuccess;
   ok = ok && cudaEventRecord(ev[4], st) == cudaSuccess;
   ok = ok && cudaEventSynchronize(ev[4]) == cudaSuccess;
   for (int i = 0; ok && i < 4; ++i) ok = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) == cudaSuccess;

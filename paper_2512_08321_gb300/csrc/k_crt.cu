@@ -28,7 +28,7 @@
 // those rows are one 32-bit word per job.
 #include <algorithm>
 
-#include "emu_internal.h"
+#include "crt_common.cuh"
 
 namespace emu {
 namespace {
@@ -41,112 +41,6 @@ __device__ __forceinline__ int sym_small(int v, int p) {   // |v| <= 3 p / 2 + 1
   if (2 * v < -p) v += p;
   if (2 * v < -p) v += p;
   return v;
-}
-
-// Round the L-limb two's-complement integer c (exact c') times 2^e2 to the
-// nearest binary64 (ties to even), by integer operations only: the magnitude's
-// leading 64 bits (a window of the top nonzero limb and the two below it,
-// shifted up to the leading one) give the 53 kept bits and the round bit, and
-// everything below them only the sticky bit.
-template <int L>
-__device__ __forceinline__ double round_limbs(uint32_t (&c)[L], int e2) {
-  const bool neg = (c[L - 1] >> 31) != 0;
-  if (neg) {   // two's-complement negate
-    uint32_t carry = 1;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const uint64_t v = static_cast<uint64_t>(~c[t]) + carry;
-      c[t] = static_cast<uint32_t>(v);
-      carry = static_cast<uint32_t>(v >> 32);
-    }
-  }
-  // top nonzero limb and the two below it (no dynamic indexing)
-  int top = -1;
-  uint32_t w0 = 0, w1 = 0, w2 = 0;
-#pragma unroll
-  for (int t = 0; t < L; ++t)
-    if (c[t]) {
-      top = t;
-      w0 = c[t];
-      w1 = t >= 1 ? c[t >= 1 ? t - 1 : 0] : 0u;
-      w2 = t >= 2 ? c[t >= 2 ? t - 2 : 0] : 0u;
-    }
-  if (top < 0) return 0.0;
-  bool sticky = false;
-#pragma unroll
-  for (int t = 0; t + 3 < L; ++t) sticky |= (t + 3 <= top) && c[t] != 0u;
-  const int lz = __clz(w0);
-  uint64_t W = (static_cast<uint64_t>(w0) << 32) | w1;    // leading one moved to bit 63 below
-  if (lz) {
-    W = (W << lz) | (w2 >> (32 - lz));
-    sticky |= (w2 << lz) != 0u;
-  } else {
-    sticky |= w2 != 0u;
-  }
-  const int lead = 32 * top + 31 - lz + e2;                // exponent of the leading bit
-  const int lsb = max(lead - 52, -1074);                   // exponent of the result's LSB
-  const int drop = 63 - (lead - lsb);                      // bits of W below it: >= 11
-  uint64_t q;
-  bool half;
-  if (drop >= 65) {            // below half the smallest subnormal
-    q = 0;
-    half = false;
-  } else if (drop == 64) {     // in [2^(lsb-1), 2^lsb): the round bit is the leading one
-    q = 0;
-    half = true;
-    sticky |= (W << 1) != 0ull;
-  } else {
-    q = W >> drop;
-    half = ((W >> (drop - 1)) & 1ull) != 0ull;
-    sticky |= (W & ((1ull << (drop - 1)) - 1ull)) != 0ull;
-  }
-  if (half && (sticky || (q & 1ull))) ++q;
-  uint64_t bits = (static_cast<uint64_t>(lsb + 1074) << 52) + q;
-  if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
-  if (neg) bits |= 0x8000000000000000ull;
-  return __longlong_as_double(static_cast<long long>(bits));
-}
-
-// Accurate-mode range fix: |c'| <= (P-1)/2 there, so the float quotient can be
-// one off near the ends of the range and c holds c' - P or c' + P.  With H =
-// (P-1)/2: c > H (H - c < 0) means c -= P; c < -H (c + H < 0) means c += P.
-// The limbs hold these values without wrapping (2^(32L-1) > 2P).
-template <int L>
-__device__ __forceinline__ void fix_range(uint32_t (&c)[L], const Plan& pl) {
-  uint32_t d[L];
-  int64_t b = 0;
-#pragma unroll
-  for (int t = 0; t < L; ++t) {        // d = H - c
-    const int64_t v = static_cast<int64_t>(pl.H[t]) - static_cast<int64_t>(c[t]) + b;
-    d[t] = static_cast<uint32_t>(v);
-    b = v >> 32;
-  }
-  if (d[L - 1] >> 31) {                // c > H: c -= P
-    b = 0;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const int64_t v = static_cast<int64_t>(c[t]) - static_cast<int64_t>(pl.Pw[t]) + b;
-      c[t] = static_cast<uint32_t>(v);
-      b = v >> 32;
-    }
-    return;
-  }
-  uint64_t cy = 0;
-#pragma unroll
-  for (int t = 0; t < L; ++t) {        // d = c + H
-    const uint64_t v = static_cast<uint64_t>(c[t]) + pl.H[t] + cy;
-    d[t] = static_cast<uint32_t>(v);
-    cy = v >> 32;
-  }
-  if (d[L - 1] >> 31) {                // c < -H: c += P
-    cy = 0;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-      const uint64_t v = static_cast<uint64_t>(c[t]) + pl.Pw[t] + cy;
-      c[t] = static_cast<uint32_t>(v);
-      cy = v >> 32;
-    }
-  }
 }
 
 // Finish one part.  acc holds sum_l u_l w_l limb by limb (unnormalised), u_l
@@ -172,14 +66,7 @@ __device__ __forceinline__ double finish(const uint64_t (&acc)[L], const uint32_
     carry = v >> 32;
   }
   if constexpr (ROBUST) fix_range<L>(c, pl);
-  return round_limbs<L>(c, e2);
-}
-
-// a * b + c with a 32 x 32 -> 64-bit product
-__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
-  uint64_t r;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
-  return r;
+  return round_exact<L>(c, e2);
 }
 
 // Residues of the block's rows for every job, staged in shared memory with
@@ -215,8 +102,8 @@ __device__ __forceinline__ uint32_t smem_word(const int8_t* smem, int job, int r
 template <int L, bool SINGLE, int kRowsPerThread, bool ROBUST = false>
 __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
                                           int64_t ldr, const int16_t* __restrict__ x, const int16_t* __restrict__ y,
-                                          double ar, double ai, double br, double bi, void* __restrict__ Cv,
-                                          int64_t ldc, int64_t j, int64_t iblock) {
+                                          double ar, double ai, double br, double bi, int flags,
+                                          void* __restrict__ Cv, int64_t ldc, int64_t j, int64_t iblock) {
   const int64_t i0 = (iblock * kThreads + threadIdx.x) * kRowsPerThread;
   const int N = pl.N;
   const int64_t job_stride = n * ldr;
@@ -284,8 +171,8 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
     }
   }
   __syncthreads();
-  const bool plain = (ar == 1.0 && ai == 0.0 && br == 0.0 && bi == 0.0);
-  const bool use_beta = !(br == 0.0 && bi == 0.0);
+  const bool plain = (flags & kCrtPlain) != 0;
+  const bool use_beta = (flags & kCrtBeta) != 0;
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
     const int r = q * kThreads + threadIdx.x;
@@ -326,7 +213,7 @@ __device__ __forceinline__ void crt_block(int64_t m, int64_t n, const Plan& pl, 
 template <int L, bool SINGLE, int kRowsPerThread, bool ROBUST>
 __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan& pl, const int8_t* __restrict__ res,
                                                int64_t ldr, const int16_t* __restrict__ x,
-                                               const int16_t* __restrict__ y, double ar, double br,
+                                               const int16_t* __restrict__ y, double ar, double br, int flags,
                                                void* __restrict__ Cv, int64_t ldc, int64_t j, int64_t iblock) {
   const int64_t i0 = (iblock * kThreads + threadIdx.x) * kRowsPerThread;
   const int N = pl.N;
@@ -371,7 +258,7 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
     }
   }
   __syncthreads();
-  const bool plain = (ar == 1.0 && br == 0.0);
+  const bool plain = (flags & kCrtPlain) != 0;
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
     const int r = q * kThreads + threadIdx.x;
@@ -381,7 +268,7 @@ __device__ __forceinline__ void crt_block_real(int64_t m, int64_t n, const Plan&
     const int64_t ci = j * ldc + i;
     if (!plain) {
       double t = __dmul_rn(ar, o);
-      if (br != 0.0) t = __fma_rn(br, SINGLE ? static_cast<double>(static_cast<const float*>(Cv)[ci])
+      if (flags & kCrtBeta) t = __fma_rn(br, SINGLE ? static_cast<double>(static_cast<const float*>(Cv)[ci])
                                              : static_cast<const double*>(Cv)[ci], t);
       o = t;
     }
@@ -395,8 +282,8 @@ __global__ void __launch_bounds__(kThreads) crt_real_kernel(int64_t m, int64_t n
                                                             const int8_t* __restrict__ res, int64_t ldr,
                                                             const int16_t* __restrict__ x,
                                                             const int16_t* __restrict__ y, double ar, double br,
-                                                            void* __restrict__ Cv, int64_t ldc) {
-  crt_block_real<L, SINGLE, R, ROBUST>(m, n, pl, res, ldr, x, y, ar, br, Cv, ldc, blockIdx.x, blockIdx.y);
+                                                            int flags, void* __restrict__ Cv, int64_t ldc) {
+  crt_block_real<L, SINGLE, R, ROBUST>(m, n, pl, res, ldr, x, y, ar, br, flags, Cv, ldc, blockIdx.x, blockIdx.y);
 }
 
 template <int L, bool SINGLE, int R, bool ROBUST>
@@ -405,9 +292,10 @@ __global__ void __launch_bounds__(kThreads) crt_kernel(int64_t m, int64_t n,
                                                        const int8_t* __restrict__ res, int64_t ldr,
                                                        const int16_t* __restrict__ x,
                                                        const int16_t* __restrict__ y, double ar,
-                                                       double ai, double br, double bi,
+                                                       double ai, double br, double bi, int flags,
                                                        void* __restrict__ Cv, int64_t ldc) {
-  crt_block<L, SINGLE, R, ROBUST>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, Cv, ldc, blockIdx.x, blockIdx.y);
+  crt_block<L, SINGLE, R, ROBUST>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, flags, Cv, ldc, blockIdx.x,
+                                  blockIdx.y);
 }
 
 // one launch over every problem of a grouped call: blocks are (column, row block) of each problem.
@@ -426,8 +314,8 @@ __global__ void __launch_bounds__(kThreads) crt_grouped(const CrtProb* __restric
   }
   const CrtProb& c = probs[lo];
   const long long local = b - c.block_begin;
-  crt_block<L, SINGLE, kGroupedCrtRows>(c.m, c.n, pl, c.res, c.ldr, c.x, c.y, c.ar, c.ai, c.br, c.bi, c.C, c.ldc,
-                                        local / c.iblocks, local % c.iblocks);
+  crt_block<L, SINGLE, kGroupedCrtRows>(c.m, c.n, pl, c.res, c.ldr, c.x, c.y, c.ar, c.ai, c.br, c.bi, c.flags, c.C,
+                                        c.ldc, local / c.iblocks, local % c.iblocks);
 }
 
 template <int L, int R, bool ROBUST>
@@ -437,15 +325,18 @@ void launch_lrr(bool single, bool real, dim3 grid, int64_t m, int64_t n, const P
   // staged residues, then the unscaled outputs (16 or 8 bytes a row)
   const size_t sm = std::max(static_cast<size_t>(real ? 1 : 3) * pl.N * kThreads * R,
                              static_cast<size_t>(real ? 8 : 16) * kThreads * R);
+  const int fl = crt_flags(ar, real ? 0.0 : ai, br, real ? 0.0 : bi);
   if (real) {
-    if (single) crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
-    else crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, C, ldc);
+    if (single)
+      crt_real_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, fl, C, ldc);
+    else
+      crt_real_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, br, fl, C, ldc);
   } else if (single) {
     max_shared_carveout(crt_kernel<L, true, R, ROBUST>);
-    crt_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+    crt_kernel<L, true, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, fl, C, ldc);
   } else {
     max_shared_carveout(crt_kernel<L, false, R, ROBUST>);
-    crt_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, C, ldc);
+    crt_kernel<L, false, R, ROBUST><<<grid, kThreads, sm, st>>>(m, n, pl, res, ldr, x, y, ar, ai, br, bi, fl, C, ldc);
   }
 }
 
@@ -648,6 +539,7 @@ cudaError_t launch_grouped_l(bool single, const CrtProb* probs, int nprob, long 
 long long crt_prob_blocks(CrtProb& c) {
   const int64_t per_block = static_cast<int64_t>(kThreads) * kGroupedCrtRows;
   c.iblocks = static_cast<int>((c.m + per_block - 1) / per_block);
+  c.flags = crt_flags(c.ar, c.ai, c.br, c.bi);
   return static_cast<long long>(c.n) * c.iblocks;
 }
 

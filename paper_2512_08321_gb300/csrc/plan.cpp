@@ -136,6 +136,31 @@ double big_minus_double(const Big& a, double d) {
   return a_ge ? r : -r;
 }
 
+// IEEE binary16 bits of x rounded to nearest (ties to even), |x| < 65504, and back.
+uint16_t half_bits(double x) {
+  const uint16_t sign = x < 0 ? 0x8000u : 0u;
+  x = std::fabs(x);
+  if (x == 0.0) return sign;
+  int e;
+  std::frexp(x, &e);                               // x = f 2^e, 0.5 <= f < 1: leading bit 2^(e-1)
+  int lsb = (e - 1) - 10;                          // exponent of the last kept bit
+  if (lsb < -24) lsb = -24;                        // subnormal range
+  double mant = std::nearbyint(std::ldexp(x, -lsb));
+  if (mant >= 2048.0) {                            // rounding carried into the next binade
+    mant /= 2.0;
+    ++lsb;
+  }
+  if (mant < 1024.0) return static_cast<uint16_t>(sign | static_cast<uint16_t>(mant));   // subnormal
+  return static_cast<uint16_t>(sign | ((lsb + 25) << 10) | (static_cast<uint16_t>(mant) - 1024u));
+}
+
+double half_value(uint16_t h) {
+  const int ex = (h >> 10) & 0x1F;
+  const double mant = ex ? (1024 + (h & 0x3FF)) : (h & 0x3FF);
+  const double v = std::ldexp(mant, ex ? ex - 25 : -24);
+  return (h & 0x8000u) ? -v : v;
+}
+
 int gcd_int(int a, int b) {
   while (b) {
     int t = a % b;
@@ -168,6 +193,7 @@ void build(int N, Plan& pl) {
   // Step II and the CRT weights
   Big sumw;
   double sum_qp = 0.0;                         // sum_l q_l / p_l = sum_l w_l / P
+  uint32_t qs[kMaxModuli] = {};
   for (int l = 0; l < N; ++l) {
     const uint32_t p = static_cast<uint32_t>(pl.p[l]);
     Big M = P;
@@ -180,6 +206,7 @@ void build(int N, Plan& pl) {
         q = t;
         break;
       }
+    qs[l] = q;
     Big w = M;
     mul_small(w, q);
     for (int t = 0; t < kMaxLimbs; ++t) pl.w[l][t] = t < pl.L ? w.v[t] : 0u;
@@ -265,6 +292,54 @@ void build(int N, Plan& pl) {
     pl.KI[t] = t < pl.L ? KI.v[t] : 0u;
     pl.Pw[t] = t < pl.L ? P.v[t] : 0u;
     pl.H[t] = t < pl.L ? H.v[t] : 0u;
+  }
+  // tensor-core CRT constants
+  {
+    Big mask;                                  // 2^(32L) - 1
+    for (int t = 0; t < pl.L; ++t) mask.v[t] = 0xFFFFFFFFu;
+    for (int v = 0; v < 2; ++v) {
+      const int b = v == 0 ? 10 : 9;
+      for (int c = 0; c < kTcDigits; ++c) pl.tcmul[v][c] = 1u << ((b * c) & 31);
+      for (int l = 0; l < N; ++l) {
+        // balanced base-2^b digits of w_l (w_l < P: a few digits more than bitlen(P) / b at most)
+        Big w;
+        for (int t = 0; t < kMaxLimbs; ++t) w.v[t] = pl.w[l][t];
+        int64_t carry = 0;
+        for (int c = 0; c < kTcDigits; ++c) {
+          // digit = (w >> bc) mod 2^b + carry, balanced into [-2^(b-1), 2^(b-1))
+          int64_t d = static_cast<int64_t>(extract64(w, b * c) & ((1ull << b) - 1)) + carry;
+          carry = 0;
+          if (d >= (int64_t(1) << (b - 1))) {
+            d -= int64_t(1) << b;
+            carry = 1;
+          }
+          pl.tcdig[v][l][c] = static_cast<int16_t>(d);
+        }
+      }
+    }
+    // w_l / P = q_l / p_l as hi + lo in fp16 (the quotient estimate's columns)
+    for (int l = 0; l < N; ++l) {
+      const double g = static_cast<double>(qs[l]) / static_cast<double>(pl.p[l]);
+      const uint16_t hi = half_bits(g);
+      pl.tcest[l][0] = hi;
+      pl.tcest[l][1] = half_bits(g - half_value(hi));
+    }
+    // K for each layout: R0 P - magic * sum over its digit slots that land below 2^(32L)
+    const int slots[3] = {14, 30, 30}, bases[3] = {10, 9, 10};
+    for (int v = 0; v < 3; ++v) {
+      Big bias;
+      for (int c = 0; c < slots[v]; ++c) {
+        const int bit = bases[v] * c;
+        if (bit >= 32 * pl.L) continue;
+        Big term(0x4B400000ull);
+        shl(term, bit);
+        add(bias, term);
+      }
+      Big Kc = P;
+      mul_small(Kc, static_cast<uint32_t>(pl.R0));
+      sub(Kc, bias);
+      for (int t = 0; t < kMaxLimbs; ++t) pl.tcK[v][t] = t < pl.L ? Kc.v[t] : 0u;
+    }
   }
   // X = (P - 1) 2^27 for the fast-mode exponent rule
   Big X = P;

@@ -26,7 +26,7 @@ namespace {
 using Key = std::tuple<int, int, int, int, int>;
 
 // cache lines: tag, dtype, N, the three log2 buckets, then tile_n group chunk_k
-// crt_rows split_elems order pairing kdir band
+// crt_rows split_elems order pairing kdir band crt_engine
 constexpr const char* kCacheTag = "gemm2";
 
 std::mutex g_mu;
@@ -57,6 +57,7 @@ bool valid(int key, int v) {
     case EMU_TUNE_PAIRING: return v >= 0 && v <= 2;
     case EMU_TUNE_KDIR: return v == 0 || v == 1;
     case EMU_TUNE_BAND: return v >= 128 && v <= 65536 && v % 128 == 0;
+    case EMU_TUNE_CRT_ENGINE: return v == 0 || v == 1;
     default: return false;
   }
 }
@@ -78,14 +79,15 @@ void load_locked() {
       }
       continue;
     }
-    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n, &t.group,
+    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n, &t.group,
                     &t.chunk_k, &t.crt_rows, &t.split_elems, &t.sched.order, &t.sched.pairing, &t.sched.kalt,
-                    &t.sched.band_cols) != 14)
+                    &t.sched.band_cols, &t.crt_engine) != 15)
       break;
     // a stale or hand-edited entry with a value the launchers would refuse is skipped,
     // so the defaults stay in force for its bucket
     if (valid(EMU_TUNE_TILE_N, t.tile_n) && valid(EMU_TUNE_GROUP, t.group) && valid(EMU_TUNE_CHUNK_K, t.chunk_k) &&
-        valid(EMU_TUNE_CRT_ROWS, t.crt_rows) && valid(EMU_TUNE_SPLIT_ELEMS, t.split_elems) && t.sched.valid())
+        valid(EMU_TUNE_CRT_ROWS, t.crt_rows) && valid(EMU_TUNE_SPLIT_ELEMS, t.split_elems) && t.sched.valid() &&
+        valid(EMU_TUNE_CRT_ENGINE, t.crt_engine))
       g_table[Key(s, N, bm, bn, bk)] = t;
     else
       std::fprintf(stderr, "ozaki2emu: ignoring invalid autotune cache entry for dtype %d, N %d\n", s, N);
@@ -110,9 +112,9 @@ void save_locked() {
   for (const auto& kv : g_table) {
     const Key& k = kv.first;
     const Tune& t = kv.second;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", kCacheTag, std::get<0>(k), std::get<1>(k),
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", kCacheTag, std::get<0>(k), std::get<1>(k),
                  std::get<2>(k), std::get<3>(k), std::get<4>(k), t.tile_n, t.group, t.chunk_k, t.crt_rows,
-                 t.split_elems, t.sched.order, t.sched.pairing, t.sched.kalt, t.sched.band_cols);
+                 t.split_elems, t.sched.order, t.sched.pairing, t.sched.kalt, t.sched.band_cols, t.crt_engine);
   }
   std::fclose(f);
 }
@@ -130,6 +132,7 @@ void set(Tune& t, int key, int v) {
     case EMU_TUNE_PAIRING: t.sched.pairing = v; break;
     case EMU_TUNE_KDIR: t.sched.kalt = v; break;
     case EMU_TUNE_BAND: t.sched.band_cols = v; break;
+    case EMU_TUNE_CRT_ENGINE: t.crt_engine = v; break;
     default: break;
   }
 }
@@ -221,6 +224,7 @@ int emu_get_tuning(int key) {
     case EMU_TUNE_PAIRING: return t.sched.pairing;
     case EMU_TUNE_KDIR: return t.sched.kalt;
     case EMU_TUNE_BAND: return t.sched.band_cols;
+    case EMU_TUNE_CRT_ENGINE: return t.crt_engine;
     default: return -1;
   }
 }
@@ -239,6 +243,7 @@ int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, 
     case EMU_TUNE_PAIRING: return t.sched.pairing;
     case EMU_TUNE_KDIR: return t.sched.kalt;
     case EMU_TUNE_BAND: return t.sched.band_cols;
+    case EMU_TUNE_CRT_ENGINE: return t.crt_engine;
     default: return -1;
   }
 }
@@ -386,8 +391,12 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
       }
     }
     t.sched = sc;
-    // CRT: rows per thread
-    bt = 1e30f;
+    // CRT: the tensor-core kernel, then the CUDA-core kernel's rows per thread
+    bt = time_min(st, a, b, reps, [&] {
+      launch_crt_tc(single, m, n, *pl, reinterpret_cast<int8_t*>(M + ores), ldr, x, y, 1.0, 0.0, 0.0, 0.0, M + oC, m,
+                    st, real, false, status);
+    });
+    t.crt_engine = 1;
     for (int r : {4, 2, 1}) {
       const float ms = time_min(st, a, b, reps, [&] {
         launch_crt(single, m, n, *pl, reinterpret_cast<int8_t*>(M + ores), ldr, x, y, 1.0, 0.0, 0.0, 0.0, M + oC, m,
@@ -396,6 +405,7 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
       if (ms < kKeep * bt) {
         bt = ms;
         t.crt_rows = r;
+        t.crt_engine = 0;
       }
     }
     ok = cudaStreamSynchronize(st) == cudaSuccess;

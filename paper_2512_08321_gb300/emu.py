@@ -381,6 +381,7 @@ EMU_TUNE_TILE_N, EMU_TUNE_GROUP, EMU_TUNE_CHUNK_K, EMU_TUNE_CRT_ROWS, EMU_TUNE_S
 EMU_TUNE_NBLOCK = 6
 EMU_TUNE_OVERLAP = 7
 EMU_TUNE_ORDER, EMU_TUNE_PAIRING, EMU_TUNE_KDIR, EMU_TUNE_BAND = 8, 9, 10, 11
+EMU_TUNE_CRT_ENGINE = 12
 SCHEDULE_KNOBS = {"order": EMU_TUNE_ORDER, "pairing": EMU_TUNE_PAIRING, "kdir": EMU_TUNE_KDIR,
                   "band": EMU_TUNE_BAND}
 

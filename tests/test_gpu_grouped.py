@@ -134,3 +134,31 @@ def test_grouped_argument_errors():
     assert emu.emu_grouped_create(False, args, 0)[0] == emu.EMU_ERR_MODULI_RANGE
     args = _args(d, 14)
     assert emu.emu_grouped_create(False, args, 96)[0] == emu.EMU_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("engine,N,single", [(0, 14, False), (1, 14, False), (1, 20, False), (1, 8, True),
+                                             (0, 8, True)])
+def test_grouped_crt_engines(engine, N, single):
+    """The grouped CRT phase on the tensor cores (128-row items, every limb
+    layout) and on the CUDA cores: each problem bit-exact against the oracle."""
+    saved = emu.emu_get_tuning(emu.EMU_TUNE_CRT_ENGINE)
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_CRT_ENGINE, engine), "crt engine")
+    try:
+        probs = _problems(12, 1, 300, 17 + N, single)
+        dprobs = _device(probs)
+        st, plan = emu.emu_grouped_create(single, _args(dprobs, N), 128)
+        emu.check(st, "emu_grouped_create")
+        try:
+            emu.check(emu.emu_grouped_run(plan), "emu_grouped_run")
+            torch.cuda.synchronize()
+            assert emu.emu_stream_status() == emu.EMU_OK
+            for i, p in enumerate(dprobs):
+                if p["m"] == 0 or p["n"] == 0:
+                    continue
+                got = host(p["dC"], p["m"])
+                want = _oracle(p, N, single)
+                assert same_bits(got, want), (i, p["m"], p["n"], p["k"], mismatch_report(got, want))
+        finally:
+            emu.emu_grouped_destroy(plan)
+    finally:
+        emu.emu_set_tuning(emu.EMU_TUNE_CRT_ENGINE, saved)

@@ -30,7 +30,7 @@ KNOBS = [(emu.EMU_TUNE_TILE_N, v) for v in (64, 128, 256)] + \
 
 @pytest.fixture(autouse=True)
 def _defaults():
-    saved = {k: emu.emu_get_tuning(k) for k in list(range(1, 6)) + list(range(8, 12))}
+    saved = {k: emu.emu_get_tuning(k) for k in list(range(1, 6)) + list(range(8, 13))}
     yield
     for k, v in saved.items():
         emu.emu_set_tuning(k, v)
@@ -92,7 +92,7 @@ def test_autotune_cache_file_round_trip(tmp_path):
     assert st == 0
     lines = [l.split() for l in cache.read_text().splitlines() if l.startswith("gemm2 ")]
     assert len(lines) == 1 and list(map(int, lines[0][6:11])) == best
-    assert len(lines[0]) == 15
+    assert len(lines[0]) == 16
 
 
 # modulus-loop schedules of the residue products: (order, pairing, kdir, band columns, chunk_k)
@@ -175,7 +175,7 @@ def test_autotune_cache_skips_invalid_entries(tmp_path):
     of that bucket runs with the defaults and succeeds."""
     cache = tmp_path / "tune.txt"
     # dtype 0 (Z), N 12, buckets of m = 300, n = 200, k = 500 -> 9, 8, 9; chunk_k 1000 is invalid
-    cache.write_text("gemm2 0 12 9 8 9 256 16 1000 4 4 0 0 0 8192\n"
+    cache.write_text("gemm2 0 12 9 8 9 256 16 1000 4 4 0 0 0 8192 1\n"
                      "gemm 0 12 9 8 9 256 16 960 4 4\n")
     code = ("import sys; sys.path.insert(0, %r)\n"
             "import numpy as np, torch\n"
