@@ -152,15 +152,27 @@ def test_accurate_with_paper_fp_crt():
 
 
 def test_accuracy_gain_over_fast_at_same_N():
+    """Accurate scaling keeps more bits where its exponents exceed the fast ones.
+    Over all entries the largest error sits on entries whose two total shifts
+    x_i + y_j coincide, so the test compares the mean error over all entries and
+    the maximum error over the entries where the accurate shift is larger (the
+    exponents are the oracle's, which the GPU's equal bit for bit)."""
     A, B = _cplx(200, 180, 2000, "N", "N", 2.0, 96, False)
     exact = Emulation(A, B, 24, keep_residue_planes=False).out            # reference, far below the errors
     bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    shift = {}
+    for mode, name in ((emu.EMU_SCALING_FAST, "fast"), (emu.EMU_SCALING_ACCURATE, "accurate")):
+        em = Emulation(A, B, 10, keep_residue_planes=False, scaling=name)
+        shift[mode] = em.x[:, None] + em.y[None, :]
     errs = {}
     for mode in (emu.EMU_SCALING_FAST, emu.EMU_SCALING_ACCURATE):
         emu.check(emu.emu_set_scaling(mode), "scaling")
         got = run_gemm(A, B, 10)
-        d = np.maximum(np.abs(got.real - exact.real), np.abs(got.imag - exact.imag))
-        errs[mode] = float(np.mean(d / bound))
-    # the tighter bound keeps about half a bit more on average here (k = 2000, phi = 2); the
-    # maximum error can come from a row whose two exponents coincide
-    assert errs[emu.EMU_SCALING_ACCURATE] < errs[emu.EMU_SCALING_FAST] / 1.2, errs
+        errs[mode] = np.maximum(np.abs(got.real - exact.real), np.abs(got.imag - exact.imag)) / bound
+    fast, accu = errs[emu.EMU_SCALING_FAST], errs[emu.EMU_SCALING_ACCURATE]
+    more = shift[emu.EMU_SCALING_ACCURATE] > shift[emu.EMU_SCALING_FAST]
+    assert np.all(shift[emu.EMU_SCALING_ACCURATE] >= shift[emu.EMU_SCALING_FAST])
+    assert more.sum() > more.size // 2
+    # the tighter bound keeps about half a bit more on average here (k = 2000, phi = 2)
+    assert accu.mean() < fast.mean() / 1.2, (accu.mean(), fast.mean())
+    assert accu[more].max() < fast[more].max(), (accu[more].max(), fast[more].max())

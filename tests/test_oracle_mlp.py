@@ -78,3 +78,36 @@ def test_features_closed_forms():
     # A row: t = 1, 0.5, 0.25 -> ceil(t 2^15)^2 sums to 2^30 (1 + 1/4 + 1/16)
     La = 0.5 * math.log2(1 + 0.25 + 0.0625)
     assert math.isclose(f[32], La) and math.isclose(f[33], La)
+
+
+def test_forward_closed_form():
+    """Hand-set weights whose logits follow by hand: hidden unit 0 copies
+    feature 3, hidden unit 1 copies -feature 5 (so the ReLU passes one sign
+    only), layer 2 sums them with weights 2 and -3 into unit 7, and output t
+    reads unit 7 with weight t and bias -t."""
+    W1 = np.zeros((64, 39))
+    b1 = np.zeros(64)
+    W2 = np.zeros((64, 64))
+    b2 = np.zeros(64)
+    W3 = np.zeros((21, 64))
+    b3 = np.zeros(21)
+    W1[0, 3] = 1.0
+    W1[1, 5] = -1.0
+    b1[2] = -1.0                          # a unit the ReLU always zeroes
+    W2[7, 0], W2[7, 1], W2[7, 2] = 2.0, -3.0, 100.0
+    b2[7] = 0.5
+    for t in range(21):
+        W3[t, 7] = float(t)
+        b3[t] = -float(t)
+    theta = mlp.pack([W1, b1, W2, b2, W3, b3])
+    X = np.zeros((4, 39))
+    X[0, 3], X[0, 5] = 1.5, -2.0          # h1 = (1.5, 2.0): a2 = 3 - 6 + 0.5 = -2.5 -> 0
+    X[1, 3], X[1, 5] = 4.0, 1.0           # h1 = (4, 0): a2 = 8.5
+    X[2, 3], X[2, 5] = -1.0, -0.25        # h1 = (0, 0.25): a2 = -0.75 + 0.5 = -0.25 -> 0
+    X[3, 3], X[3, 5] = 0.25, 0.0          # h1 = (0.25, 0): a2 = 1.0
+    z, (Xc, a1, h1, a2, h2) = mlp.forward(theta, X)
+    h7 = np.array([0.0, 8.5, 0.0, 1.0])
+    assert np.array_equal(h2[:, 7], h7)
+    assert np.count_nonzero(h2[:, :7]) == 0 and np.count_nonzero(h2[:, 8:]) == 0
+    t = np.arange(21, dtype=float)
+    assert np.array_equal(z, h7[:, None] * t[None, :] - t[None, :])
