@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the unfused cuBLAS-INT8 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the compact cgemm8192 and grouped512 records added to the default workload's line")
     ap.add_argument("--overlap", choices=["auto", "on", "off"], default="auto",
                     help="EMU_TUNE_OVERLAP: split and CRT of neighbouring column blocks beside the products "
                          "(auto: the library's default, on for the real GEMMs)")
@@ -477,6 +479,19 @@ def main():
         out["plain_emulation"] = plain_emulation(emu, torch, A, B, wl, C_fused)
         del C_fused
 
+    # the other workloads of the hot path, measured in the same run (rank 0, default workload only)
+    if rank == 0 and args.workload == "zgemm16384" and not args.no_extra:
+        extra = {"cgemm8192": extra_single(emu, torch, "cgemm8192")}
+        plan, g = grouped_measure(emu, torch, WORKLOADS["grouped512"], rank, 5, 3, with_loop=True)
+        emu.emu_grouped_destroy(plan)
+        pk2, _ = peaks()
+        g["roofline_residue_gemm"] = {
+            "achieved_tflops": g["gemm_flops"] / (g["phases_ms"]["residue_gemm"] * 1e-3) * 1e-12,
+            "peak": float(pk2.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))}
+        g["roofline_residue_gemm"]["frac"] = g["roofline_residue_gemm"]["achieved_tflops"] / \
+            g["roofline_residue_gemm"]["peak"]
+        extra["grouped512"] = g
+        out["extra_workloads"] = extra
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -733,6 +748,118 @@ def run_grouped(args, wl, world, rank, local):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def extra_single(emu, torch, name, steps=5, warmup=3):
+    """A compact record of another single-GEMM workload (cgemm8192) measured in the
+    same run: autotuned, W warm-up calls, then the median of K device-timed calls
+    (CUDA events on the launching stream), with the phase times of one more call."""
+    from paper_2512_08321_gb300.workloads import paper_matrix_device
+    wl = WORKLOADS[name]
+    m, n, k, N, single = wl["m"], wl["n"], wl["k"], wl["N"], wl["single"]
+    cdt = torch.complex64 if single else torch.complex128
+    f = emu.emu_cgemm if single else emu.emu_zgemm
+    code = emu.EMU_DTYPE_C if single else emu.EMU_DTYPE_Z
+    A = paper_matrix_device(m, k, wl["phi"], wl["seed"], cdt)
+    B = paper_matrix_device(k, n, wl["phi"], wl["seed"] + 1, cdt)
+    C = torch.zeros((n, m), dtype=cdt, device="cuda")
+    st = torch.cuda.current_stream()
+    st_t, tuned = emu.emu_autotune_gemm(code, m, n, k, N)
+    emu.check(st_t, "emu_autotune_gemm")
+
+    def call():
+        emu.check(f("N", "N", m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 0.0, C.data_ptr(), m, N, st), name)
+
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        call()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    emu.check(emu.emu_set_phase_events(pev), "phase events")
+    call()
+    emu.emu_set_phase_events(None)
+    torch.cuda.synchronize()
+    ms = statistics.median(times)
+    flops = 8.0 * m * n * k
+    return {"workload": name, "m": m, "n": n, "k": k, "num_moduli": N, "phi": wl["phi"], "io": str(cdt)[6:],
+            "tflops": flops / (ms * 1e-3) * 1e-12, "ms_median": ms, "steps": steps, "warmup": warmup,
+            "phases_ms": {nm: pev[i].elapsed_time(pev[i + 1])
+                          for i, nm in enumerate(["exponents", "split", "residue_gemm", "crt"])},
+            "tuning": tuning_record(emu, code, N, m, n, k, tuned),
+            "status": emu.STATUS_NAMES.get(emu.emu_stream_status(st), "?")}
+
+
+def grouped_measure(emu, torch, wl, rank, steps, warmup, with_loop, seed_offset=0):
+    """The grouped workload: a plan over every problem (autotuned tile width), W warm-up
+    replays of its CUDA graph, then K timed replays (CUDA events, median and mean), the
+    phase times of the same plan outside the graph, and optionally the plain loop of
+    per-problem emu_zgemm calls on the same data."""
+    from paper_2512_08321_gb300.workloads import log_uniform_shapes, paper_matrix_device
+    N = wl["N"]
+    shapes = log_uniform_shapes(wl["count"], wl["lo"], wl["hi"], wl["seed"])
+    probs, tensors = [], []
+    flops = 0.0
+    for i, (m, n, k) in enumerate(shapes):
+        m, n, k = int(m), int(n), int(k)
+        s = wl["seed"] + 7919 * i + 1000003 * rank + seed_offset
+        A = paper_matrix_device(m, k, wl["phi"], s, torch.complex128)
+        B = paper_matrix_device(k, n, wl["phi"], s + 1, torch.complex128)
+        C = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+        tensors.append((A, B, C))
+        probs.append(dict(transa="N", transb="N", m=m, n=n, k=k, A=A.data_ptr(), lda=m, B=B.data_ptr(), ldb=k,
+                          C=C.data_ptr(), ldc=m))
+        flops += 8.0 * m * n * k
+    st, plan = emu.emu_grouped_create(False, emu.GroupedArgs(probs, N), 0)
+    emu.check(st, "emu_grouped_create")
+    stream = torch.cuda.current_stream()
+    try:
+        for _ in range(warmup):
+            emu.check(emu.emu_grouped_run(plan, stream), "run")
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record()
+            emu.check(emu.emu_grouped_run(plan, stream), "run")
+            b.record()
+        torch.cuda.synchronize()
+        times = [a.elapsed_time(b) for a, b in evs]
+        phase_runs = [emu.emu_grouped_phase_times(plan, stream)[1] for _ in range(3)]
+        phases = {nm: statistics.mean(r[i] for r in phase_runs)
+                  for i, nm in enumerate(["exponents", "split", "residue_gemm", "crt"])}
+        rec = {"problems": wl["count"], "mnk_range": [wl["lo"], wl["hi"]], "num_moduli": N, "phi": wl["phi"],
+               "flops": flops, "replay_ms_median": statistics.median(times), "replay_ms_mean": statistics.mean(times),
+               "tflops": flops / (statistics.median(times) * 1e-3) * 1e-12, "phases_ms": phases,
+               "gemm_flops": 6.0 * N * sum(float(m) * n * k for m, n, k in shapes),
+               "tile_n": emu.emu_grouped_tile(plan), "graph_kernels_per_replay": emu.emu_grouped_kernels(plan),
+               "status": emu.STATUS_NAMES.get(emu.emu_stream_status(stream), "?")}
+        if with_loop:
+            def loop():
+                for (m, n, k), (A, B, C) in zip(shapes, tensors):
+                    s2 = emu.emu_zgemm("N", "N", int(m), int(n), int(k), 1.0, A.data_ptr(), int(m), B.data_ptr(),
+                                       int(k), 0.0, C.data_ptr(), int(m), N, stream)
+                    if s2 != emu.EMU_OK:
+                        raise emu.EmuError(s2, "emu_zgemm")
+            loop()
+            torch.cuda.synchronize()
+            la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            la.record()
+            loop()
+            lb.record()
+            torch.cuda.synchronize()
+            lms = la.elapsed_time(lb)
+            rec["plain_loop"] = {"ms": lms, "tflops": flops / (lms * 1e-3) * 1e-12,
+                                 "speedup_of_grouped": lms / rec["replay_ms_median"], "launches": 10 * len(shapes)}
+        return plan, rec
+    except Exception:
+        emu.emu_grouped_destroy(plan)
+        raise
 
 
 def plain_emulation(emu, torch, A, B, wl, C_ref):
