@@ -42,6 +42,9 @@ WORKLOADS = {
     # 512 uneven problems, m, n, k log-uniform in [64, 2048]: one grouped plan replayed from a CUDA graph
     "grouped512": dict(single=False, grouped=True, count=512, lo=64, hi=2048, phi=1.0, N=16, seed=20251212,
                        m=0, n=0, k=0),
+    # 64 problems of the same distribution: a case small enough for profiler captures
+    "grouped64": dict(single=False, grouped=True, count=64, lo=64, hi=2048, phi=1.0, N=16, seed=20251213,
+                      m=0, n=0, k=0),
     # held-out inputs for the learned moduli selector (not in its training set), three targets
     "learned": dict(single=False, learned=True, shapes=[(8192, 8192, 8192), (16384, 1024, 16384)],
                     phis=[0.5, 3.0], targets=[1e-6, 1e-10, 1e-15], seed=20251214, N=0, m=0, n=0, k=0, phi=0.0),

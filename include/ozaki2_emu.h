@@ -194,11 +194,15 @@ typedef struct emu_grouped_s* emu_grouped_t;
 
 /* Build a grouped plan: workspace (cudaMalloc, owned by the plan), device
  * descriptor tables and the CUDA graph.  tile_n: rows of op(A) per tile of the
- * residue-product launch (64, 128 or 256), or 0 to let the autotuner time the
- * three on this problem set (the choice is remembered per problem-set
- * signature, and kept in the file named by EMU_AUTOTUNE_CACHE if set).
+ * residue-product launch (64, 128 or 256 for every problem), or
+ * EMU_GROUPED_TILE_PER_PROBLEM for each problem's own width from its row
+ * count (the one launch mixes them), or 0 to let the autotuner time these four
+ * choices on this problem set (the choice is remembered per problem-set
+ * signature, and kept in the file named by EMU_AUTOTUNE_CACHE if set).  The
+ * CRT phase uses the engine EMU_TUNE_CRT_ENGINE names at creation.
  * Synchronous; returns EMU_ERR_INVALID_ARG / EMU_ERR_K_TOO_LARGE /
  * EMU_ERR_MODULI_RANGE as emu_zgemm would for any problem. */
+#define EMU_GROUPED_TILE_PER_PROBLEM (-1)
 emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa, const emu_op_t* transb,
                                 const int64_t* m, const int64_t* n, const int64_t* k, const double* alpha,
                                 const void* const* A, const int64_t* lda, const void* const* B,
@@ -207,7 +211,8 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
 /* Replay the plan's graph on `stream` (asynchronous).  The matrices are read
  * and written at the addresses given at creation. */
 emu_status_t emu_grouped_run(emu_grouped_t plan, void* stream);
-/* Tile width the plan uses, and the number of kernels one replay launches. */
+/* Tile width the plan uses (EMU_GROUPED_TILE_PER_PROBLEM for per-problem
+ * widths), and the number of kernels one replay launches. */
 int emu_grouped_tile(emu_grouped_t plan);
 int emu_grouped_kernels(emu_grouped_t plan);
 /* Diagnostic: run the plan's four phases once on `stream` outside the graph,

@@ -226,7 +226,7 @@ bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, c
                         const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,
                         long long* unit_begin, const GemmSchedule& sched = GemmSchedule());
 cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long total_units, const Plan& pl,
-                                    int tile_n, unsigned int* status, cudaStream_t st);
+                                    unsigned int* status, cudaStream_t st);
 cudaError_t prepare_gemm_f16();
 // moduli-selection network (mlp.cu) and its features (k_scale.cu)
 cudaError_t launch_mlp_forward(const float* th, const float* X, int batch, float* Z, cudaStream_t st);

@@ -109,8 +109,25 @@ std::string signature(bool single, int N, const std::vector<emu_grouped_s::Prob>
   return buf;
 }
 
+// Tile width of one problem under the per-problem rule: the width (64, 128,
+// 256) with the fewest padded rows counting 64 rows of fixed cost per tile
+// (its epilogue and pipeline fill), ties to the wider tile.
+int problem_tile(int64_t m) {
+  int best = 256;
+  int64_t best_cost = -1;
+  for (int tn : {256, 128, 64}) {
+    const int64_t cost = (m + tn - 1) / tn * (tn + 64);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = tn;
+    }
+  }
+  return best;
+}
+
 // Descriptors, then the first unit of every problem as a compact array the
-// residue-product kernel scans (long long per problem).
+// residue-product kernel scans (long long per problem).  tile_n: 64, 128 or
+// 256 for every problem, EMU_GROUPED_TILE_PER_PROBLEM for problem_tile(m).
 emu_status_t upload_gemm_descs(emu_grouped_s* g, int tile_n, void* d_dst, long long* total_units) {
   const size_t np = g->probs.size();
   std::vector<unsigned char> host(group_problem_bytes() * np + sizeof(long long) * np);
@@ -119,8 +136,9 @@ emu_status_t upload_gemm_descs(emu_grouped_s* g, int tile_n, void* d_dst, long l
   for (size_t i = 0; i < np; ++i) {
     const auto& p = g->probs[i];
     ubeg[i] = units;
+    const int tn = tile_n == EMU_GROUPED_TILE_PER_PROBLEM ? problem_tile(p.m) : tile_n;
     if (!fill_group_problem(host.data() + i * group_problem_bytes(), p.m, p.n, p.kpad, g->N, p.pa, p.pb, p.res, p.ldr,
-                            g->chunk_k, g_f16_group, tile_n, &units))
+                            g->chunk_k, g_f16_group, tn, &units))
       return EMU_ERR_CUDA;
   }
   if (cudaMemcpy(d_dst, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) return EMU_ERR_CUDA;
@@ -146,16 +164,17 @@ cudaError_t enqueue(emu_grouped_s* g, cudaStream_t st, bool with_gemm) {
   if ((e = launch_split_grouped(g->single, true, g->d_split, g->nsplit, g->split_blocks, *g->pl, st)) != cudaSuccess)
     return e;
   if (!with_gemm) return cudaSuccess;
-  if ((e = launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->tile_n, g->status, st)) !=
+  if ((e = launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->status, st)) !=
       cudaSuccess)
     return e;
   return crt_phase(g, st);
 }
 
-// Time the residue-product launch for each tile width on this problem set.
+// Time the residue-product launch for the per-problem widths and each uniform
+// tile width on this problem set.
 int autotune(emu_grouped_s* g, cudaStream_t st) {
-  const int cands[3] = {256, 128, 64};
-  int best = 256;
+  const int cands[4] = {EMU_GROUPED_TILE_PER_PROBLEM, 256, 128, 64};
+  int best = EMU_GROUPED_TILE_PER_PROBLEM;
   float best_ms = 1e30f;
   if (enqueue(g, st, false) != cudaSuccess) return best;      // planes for the timing runs
   cudaEvent_t a, b;
@@ -167,7 +186,7 @@ int autotune(emu_grouped_s* g, cudaStream_t st) {
     float ms_min = 1e30f;
     for (int rep = 0; rep < 4; ++rep) {
       cudaEventRecord(a, st);
-      launch_gemm_f16_grouped(g->d_gp, g->ngp, units, *g->pl, tn, g->status, st);
+      launch_gemm_f16_grouped(g->d_gp, g->ngp, units, *g->pl, g->status, st);
       cudaEventRecord(b, st);
       if (cudaEventSynchronize(b) != cudaSuccess) break;
       float ms = 0;
@@ -200,7 +219,8 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
   *out = nullptr;
   if (count < 0) return EMU_ERR_INVALID_ARG;
   if (num_moduli < EMU_MIN_MODULI || num_moduli > EMU_MAX_MODULI) return EMU_ERR_MODULI_RANGE;
-  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256) return EMU_ERR_INVALID_ARG;
+  if (tile_n != 0 && tile_n != EMU_GROUPED_TILE_PER_PROBLEM && tile_n != 64 && tile_n != 128 && tile_n != 256)
+    return EMU_ERR_INVALID_ARG;
   if (count > 0 && (!transa || !transb || !m || !n || !k || !alpha || !A || !lda || !B || !ldb || !beta || !C || !ldc))
     return EMU_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
@@ -431,7 +451,7 @@ emu_status_t emu_grouped_phase_times(emu_grouped_t g, float* ms, void* stream) {
   ok = ok && cudaEventRecord(ev[1], st) == cudaSuccess;
   ok = ok && launch_split_grouped(g->single, true, g->d_split, g->nsplit, g->split_blocks, *g->pl, st) == cudaSuccess;
   ok = ok && cudaEventRecord(ev[2], st) == cudaSuccess;
-  ok = ok && launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->tile_n, g->status, st) ==
+  ok = ok && launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->status, st) ==
                  cudaSuccess;
   ok = ok && cudaEventRecord(ev[3], st) == cudaSuccess;
   ok = ok && crt_phase(g, st) == cudaSuccess;

@@ -53,6 +53,7 @@ namespace {
 // (jb < 0 when the job count is odd and this is the last pair).
 struct Unit {
   int ja, jb, tj, ti;
+  int bn;                           // output rows of this tile (MMA N): the kernel's BN, or less (grouped)
   bool desc;                        // k chunks in descending order
   int ppm;                          // planes (jobs) per modulus: 3 complex, 1 real
   int nkb, ck, nch;                 // k-blocks, k-blocks per chunk, chunks
@@ -118,13 +119,19 @@ __device__ __forceinline__ void pair_jobs(int p, int J, int ppm, int pairing, in
   }
 }
 
+// The epilogue's rounding stays on rintf and float-to-int conversion (the XU
+// pipe, idle otherwise): the same steps on the FMA pipe with a magic constant
+// were measured to slow the residue products beside them by 5-6 % (ZGEMM
+// 16384^3: 246 against 233 ms, alternating builds on one GPU).
+
 // descending k chunks on the odd units a CTA processes (its units are
 // blockIdx.x, blockIdx.x + gridDim.x, ...)
 __device__ __forceinline__ bool unit_desc(long long u, int kalt) {
   return kalt && (((u - blockIdx.x) / gridDim.x) & 1);
 }
 
-// one GEMM: tensor maps are kernel parameters
+// one GEMM: tensor maps are kernel parameters; the tile width is the kernel's BN
+template <int BN>
 struct SingleWork {
   const CUtensorMap* mapA;
   const CUtensorMap* mapB;
@@ -138,6 +145,7 @@ struct SingleWork {
     unit_coords(u, s.pairs, s.tiles, s.TJ, s.TI, s.group, s.order, s.band, pair, w.tj, w.ti);
     pair_jobs(pair, s.J, s.ppm, s.pairing, w.ja, w.jb);
     w.desc = unit_desc(u, s.kalt);
+    w.bn = BN;
     w.ppm = s.ppm;
     w.nkb = s.nkb;
     w.ck = s.ck;
@@ -161,6 +169,7 @@ struct GroupProblem {  // CUtensorMap members give it 64-byte alignment
   long long unit_begin;             // first unit of this problem
   int TJ, TI, tiles, group, nkb, ck, nch, J, ppm;
   int order, pairing, kalt, band;   // schedule, as in Sched
+  int bn;                           // this problem's tile width: 64, 128 or 256 (at most the kernel's BN)
 };
 
 struct GroupWork {
@@ -183,6 +192,7 @@ struct GroupWork {
     unit_coords(v, (P.J + 1) / 2, P.tiles, P.TJ, P.TI, P.group, P.order, P.band, pair, w.tj, w.ti);
     pair_jobs(pair, P.J, P.ppm, P.pairing, w.ja, w.jb);
     w.desc = unit_desc(u, P.kalt);
+    w.bn = P.bn;
     w.ppm = P.ppm;
     w.nkb = P.nkb;
     w.ck = P.ck;
@@ -197,9 +207,14 @@ struct GroupWork {
   }
 };
 
-template <int BN, class Work>
+// BN: the largest tile width (shared-memory stages, TMEM slots); EPI: epilogue
+// warps (8 or 16), EPI / 4 of them on each quarter of the TMEM lanes, each
+// taking 4 / EPI of a tile's columns (at least 32: with 64-wide tiles and 16
+// warps, half of them only wait and arrive).
+template <int BN, int EPI, class Work>
 __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigned int* status, bool fence_maps) {
   using C = Cfg<BN>;
+  constexpr int kParts = EPI / 4;                 // column parts of a tile
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;                 // 1024-aligned operand stages
@@ -226,7 +241,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(tfull(i), 1);
-      mbar_init(tempty(i), 32 * kEpiWarps);
+      mbar_init(tempty(i), 32 * EPI);
     }
     mbar_init(done, 1);
     *abort_s = 0;
@@ -268,9 +283,9 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
               const uint32_t sa = base + st * C::kStageBytes;
-              mbar_expect_tx(full(st), C::kStageBytes);
+              mbar_expect_tx(full(st), static_cast<uint32_t>(kStageA + U.bn * BK * 2));
               tma_load_3d(sa, U.mapA, full(st), kb * BK, U.tj * BM, job);
-              tma_load_3d(sa + kStageA, U.mapB, full(st), kb * BK, U.ti * BN, job);
+              tma_load_3d(sa + kStageA, U.mapB, full(st), kb * BK, U.ti * U.bn, job);
             }
           }
         }
@@ -289,7 +304,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       long long it = 0;
-      int used[2] = {0, 0};
+      uint32_t used = 0u;                           // bit s: parity of slot s's uses so far
       bool ok = true;
       int hint = 0;
       for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
@@ -299,9 +314,10 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
             const int job = which ? U.jb : U.ja;
             if (job < 0) continue;
             const int slot = which;
-            if (!mbar_wait(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u, ctl)) { ok = false; break; }
+            if (!mbar_wait(tempty(slot), ((used >> slot) & 1u) ^ 1u, ctl)) { ok = false; break; }
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
+            const uint32_t idesc = C::kIdescNoN | (static_cast<uint32_t>(U.bn >> 3) << 17);
             const int a = U.desc ? U.nch - 1 - c : c;
             const int kb0 = a * U.ck, kb1 = min(U.nkb, (a + 1) * U.ck);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -315,13 +331,13 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
               for (int kk = 0; kk < BK / UK; ++kk) {
                 // advance the start address by 32 bytes per 16 fp16 of k
                 const uint64_t off = static_cast<uint64_t>((kk * UK * 2) >> 4);
-                mma_f16(td, da + off, db + off, C::kIdesc, !(c == 0 && kb == kb0 && kk == 0));
+                mma_f16(td, da + off, db + off, idesc, !(c == 0 && kb == kb0 && kk == 0));
               }
               mma_commit(empty(st));
             }
             if (!ok) break;
             mma_commit(tfull(slot));
-            ++used[slot];
+            used ^= 1u << slot;
           }
         }
       }
@@ -333,17 +349,19 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    constexpr int kHalf = BN / 2;                   // columns of a slot per epilogue warp
     const int ew = warp - 2;
     const int quad = warp & 3;                      // TMEM lanes 32*quad .. 32*quad+31
-    const int half = ew >> 2;                       // columns [kHalf*half, kHalf*half + kHalf) of a slot
+    const int part = ew >> 2;                       // column part of a tile
     const int row_in_tile = quad * 32 + lane;       // output column within the tile
-    int used[2] = {0, 0};
+    uint32_t used = 0u;                             // bit s: parity of slot s's uses so far
     bool ok = true;
     int hint = 0;
     for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
       const Unit U = W.get(u, hint);
       const int64_t col = static_cast<int64_t>(U.tj) * BM + row_in_tile;
+      // columns of this warp: [part * pw, part * pw + pw), pw >= 32; parts past the tile only wait
+      const int pw = (U.bn / kParts) < 32 ? 32 : (U.bn / kParts);
+      const bool mine = part * pw < U.bn;
       for (int c = 0; ok && c < U.nch; ++c) {
         const bool last = (c == U.nch - 1);
         for (int which = 0; ok && which < 2; ++which) {
@@ -354,22 +372,24 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
           const float p = static_cast<float>(pl.p[l]);
           const float inv_p = 1.0f / p;
           const int pi = pl.p[l];
-          if (!mbar_wait(tfull(slot), static_cast<uint32_t>(used[slot] & 1), ctl)) { ok = false; break; }
+          if (!mbar_wait(tfull(slot), (used >> slot) & 1u, ctl)) { ok = false; break; }
           tc_fence_after();
           const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) +
-                              static_cast<uint32_t>(slot * BN + half * kHalf);
-          if (!last) {
+                              static_cast<uint32_t>(slot * BN + part * pw);
+          if (!mine) {
+            tc_fence_before();
+            mbar_arrive(tempty(slot));
+          } else if (!last) {
             // in-place reduction: keeps every later partial sum below 2^24
 #pragma unroll 1
-            for (int cc = 0; cc < kHalf; cc += 32) {
+            for (int cc = 0; cc < pw; cc += 32) {
               uint32_t v[32];
               tmem_ld32(ta + cc, v);
               tmem_wait_ld();
 #pragma unroll
               for (int q = 0; q < 32; ++q) {
                 const float x = __uint_as_float(v[q]);
-                const float r = fmaf(-rintf(x * inv_p), p, x);
-                v[q] = __float_as_uint(r);
+                v[q] = __float_as_uint(fmaf(-rintf(x * inv_p), p, x));
               }
               tmem_st32(ta + cc, v);
             }
@@ -378,14 +398,14 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
             mbar_arrive(tempty(slot));
           } else {
             // final: exact symmetric residue, int8, row-contiguous
-            const int64_t row0 = static_cast<int64_t>(U.ti) * BN + half * kHalf;
+            const int64_t row0 = static_cast<int64_t>(U.ti) * U.bn + part * pw;
             int8_t* out = U.res + static_cast<int64_t>(job) * U.n * U.ldr + col * U.ldr + row0;
 #pragma unroll 1
-            for (int cc = 0; cc < kHalf; cc += 32) {
+            for (int cc = 0; cc < pw; cc += 32) {
               uint32_t v[32];
               tmem_ld32(ta + cc, v);
               tmem_wait_ld();
-              if (cc == kHalf - 32) {
+              if (cc == pw - 32) {
                 tc_fence_before();
                 mbar_arrive(tempty(slot));          // TMEM slot may be refilled
               }
@@ -414,7 +434,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
               }
             }
           }
-          ++used[slot];
+          used ^= 1u << slot;
         }
       }
     }
@@ -434,16 +454,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const __grid_constant__ CUtensorMap mapB,   // A planes: MMA operand B
                     const __grid_constant__ Plan pl, const Sched s, int8_t* __restrict__ res, int64_t ldr,
                     int64_t n, int64_t rcap, unsigned int* status) {
-  const SingleWork W{&mapA, &mapB, s, res, ldr, n, rcap};
-  gemm_body<BN>(W, pl, status, false);
+  const SingleWork<BN> W{&mapA, &mapB, s, res, ldr, n, rcap};
+  gemm_body<BN, kEpiWarps>(W, pl, status, false);
 }
 
-template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+// Grouped launches: 256-row stages with each problem's own tile width, and 16
+// epilogue warps (short-k units are bound by their epilogue, not their MMAs).
+constexpr int kGroupedEpi = 16;
+constexpr int kGroupedThreads = 32 * (2 + kGroupedEpi);
+
+__global__ void __launch_bounds__(kGroupedThreads, 1)
     gemm_f16_grouped_kernel(const GroupProblem* __restrict__ probs, int count, long long total,
                             const __grid_constant__ Plan pl, unsigned int* status) {
   const GroupWork W{probs, reinterpret_cast<const long long*>(probs + count), count, total};
-  gemm_body<BN>(W, pl, status, true);
+  gemm_body<256, kGroupedEpi>(W, pl, status, true);
 }
 
 // The largest shared-memory carveout: an SM holding one block of this kernel
@@ -455,13 +479,19 @@ cudaError_t set_smem_attrs() {
     cudaError_t e = cudaFuncSetAttribute(gemm_f16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg<BN>::kSmemBytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_f16_grouped_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               Cfg<BN>::kSmemBytes);
-    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gemm_f16_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                static_cast<int>(cudaSharedmemCarveoutMaxShared));
+    return e;
+  }();
+  return err;
+}
+
+cudaError_t set_grouped_attrs() {
+  static cudaError_t err = [] {
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<256>::kSmemBytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_f16_grouped_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+      e = cudaFuncSetAttribute(gemm_f16_grouped_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                static_cast<int>(cudaSharedmemCarveoutMaxShared));
     return e;
   }();
@@ -547,6 +577,7 @@ cudaError_t prepare_gemm_f16() {
   cudaError_t e = set_smem_attrs<64>();
   if (e == cudaSuccess) e = set_smem_attrs<128>();
   if (e == cudaSuccess) e = set_smem_attrs<256>();
+  if (e == cudaSuccess) e = set_grouped_attrs();
   return e;
 }
 
@@ -556,7 +587,7 @@ cudaError_t prepare_gemm_f16() {
 bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, const void* planesA,
                         const void* planesB, int8_t* res, int64_t ldr, int chunk_k, int group, int tile_n,
                         long long* unit_begin, const GemmSchedule& sc) {
-  if (!get_encoder() || !sc.valid()) return false;
+  if (!get_encoder() || !sc.valid() || (tile_n != 64 && tile_n != 128 && tile_n != 256)) return false;
   GroupProblem& P = *static_cast<GroupProblem*>(desc);
   std::memset(&P, 0, sizeof(P));
   const int J = 3 * N;
@@ -578,34 +609,22 @@ bool fill_group_problem(void* desc, int64_t m, int64_t n, int64_t kpad, int N, c
   P.pairing = sc.pairing;
   P.kalt = sc.kalt;
   P.band = sc.band_cols / BM;
+  P.bn = tile_n;
   P.unit_begin = *unit_begin;
   *unit_begin += static_cast<long long>((J + 1) / 2) * P.tiles;
   return true;
 }
 
 cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long total_units, const Plan& pl,
-                                    int tile_n, unsigned int* status, cudaStream_t st) {
+                                    unsigned int* status, cudaStream_t st) {
   if (count <= 0 || total_units <= 0) return cudaSuccess;
   if (!get_encoder()) return cudaErrorNotSupported;
   const GroupProblem* P = static_cast<const GroupProblem*>(probs_dev);
   const long long grid = total_units < g_sms ? total_units : g_sms;
-  cudaError_t e;
-  switch (tile_n) {
-    case 64:
-      if ((e = set_smem_attrs<64>()) != cudaSuccess) return e;
-      gemm_f16_grouped_kernel<64><<<static_cast<unsigned int>(grid), kThreads, Cfg<64>::kSmemBytes, st>>>(
-          P, count, total_units, pl, status);
-      break;
-    case 128:
-      if ((e = set_smem_attrs<128>()) != cudaSuccess) return e;
-      gemm_f16_grouped_kernel<128><<<static_cast<unsigned int>(grid), kThreads, Cfg<128>::kSmemBytes, st>>>(
-          P, count, total_units, pl, status);
-      break;
-    default:
-      if ((e = set_smem_attrs<256>()) != cudaSuccess) return e;
-      gemm_f16_grouped_kernel<256><<<static_cast<unsigned int>(grid), kThreads, Cfg<256>::kSmemBytes, st>>>(
-          P, count, total_units, pl, status);
-  }
+  const cudaError_t e = set_grouped_attrs();
+  if (e != cudaSuccess) return e;
+  gemm_f16_grouped_kernel<<<static_cast<unsigned int>(grid), kGroupedThreads, Cfg<256>::kSmemBytes, st>>>(
+      P, count, total_units, pl, status);
   count_launches(1);
   return cudaGetLastError();
 }

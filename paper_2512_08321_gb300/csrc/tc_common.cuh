@@ -35,6 +35,8 @@ struct Cfg {
   static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) |
                                      (static_cast<uint32_t>(BN >> 3) << 17) |
                                      (static_cast<uint32_t>(BM >> 4) << 24);
+  // the same without N (bits 17-22), for a tile width chosen at run time
+  static constexpr uint32_t kIdescNoN = kIdesc & ~(0x3Fu << 17);
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
 };
 

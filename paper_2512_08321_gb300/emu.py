@@ -274,6 +274,9 @@ def emu_grouped_create(is_single, args, tile_n=0):
     return st, h
 
 
+EMU_GROUPED_TILE_PER_PROBLEM = -1
+
+
 def emu_grouped_run(plan, stream=None):
     return lib().emu_grouped_run(plan, _stream(stream))
 

@@ -61,7 +61,7 @@ def _oracle(p, N, single):
                    out_fmt=fp.BINARY32 if single else fp.BINARY64, **ab).out
 
 
-@pytest.mark.parametrize("tile", [64, 128, 256, 0])
+@pytest.mark.parametrize("tile", [64, 128, 256, -1, 0])
 def test_grouped_bitexact(tile):
     N, single = 14, False
     probs = _problems(14, 1, 200, 11, single)
@@ -70,7 +70,7 @@ def test_grouped_bitexact(tile):
     st, plan = emu.emu_grouped_create(single, args, tile)
     emu.check(st, "emu_grouped_create")
     try:
-        assert emu.emu_grouped_tile(plan) in (64, 128, 256)
+        assert emu.emu_grouped_tile(plan) in (64, 128, 256, emu.EMU_GROUPED_TILE_PER_PROBLEM)
         if tile:
             assert emu.emu_grouped_tile(plan) == tile
         assert emu.emu_grouped_kernels(plan) >= 6
