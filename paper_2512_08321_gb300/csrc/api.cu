@@ -433,10 +433,12 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
                                      tn.split_elems, dt.real)) != cudaSuccess)
       return EMU_ERR_CUDA;
   }
-  for (int64_t j0 = 0; j0 < n; j0 += nb) {
-    const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
+  for (int64_t j0 = 0, nj = 0; j0 < n; j0 += nj) {
+    const int64_t w = (hooks && j0 == 0 && hooks->nb0 > 0 && hooks->nb0 < nb) ? hooks->nb0 : nb;
+    nj = (n - j0) < w ? (n - j0) : w;
     const void* Bj = block_ptr(j0);
-    void* Cj = static_cast<char*>(C) + static_cast<size_t>(j0) * ldc * in_esz;
+    void* Cbase = (hooks && hooks->c_dev && j0 < hooks->c_dev_end) ? hooks->c_dev : C;
+    void* Cj = static_cast<char*>(Cbase) + static_cast<size_t>(j0) * ldc * in_esz;
     int16_t* yj = y + j0;
     if (hooks && (s = hooks->wait_inputs(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
     if (k == 0) {

@@ -250,7 +250,8 @@ cudaError_t launch_features(bool single, const void* A, int64_t m, int64_t rsa, 
 extern int g_f16_group;
 
 // Block hooks of a host-buffer call (host.cu).  The output columns are
-// processed in blocks of at most `nb` (0: the library's choice); before a
+// processed in blocks of at most `nb` (0: the library's choice), the first of
+// `nb0` (when nonzero); before a
 // block's columns of B (and of C, when beta != 0) are touched the caller's
 // stream is made to wait for them (`wait_inputs`); once the block's CRT is
 // enqueued `output_done` is told its columns of C are final, and
@@ -262,6 +263,9 @@ extern int g_f16_group;
 // otherwise all of A is waited for first.
 struct BlockHooks {
   int64_t nb, mb;
+  int64_t nb0;              // width of the first column block (0: nb)
+  void* c_dev;              // columns below c_dev_end are written here (same ldc) instead of into C
+  int64_t c_dev_end;
   void* ctx;
   emu_status_t (*wait_inputs)(void* ctx, int64_t j0, int64_t nj, cudaStream_t st);
   emu_status_t (*wait_rows)(void* ctx, int64_t i0, int64_t mi, cudaStream_t st);

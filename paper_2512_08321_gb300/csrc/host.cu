@@ -133,7 +133,8 @@ cudaError_t transfer(bool to_host, void* dev, size_t dpitch, const void* host, c
                  : cudaMemcpy2DAsync(dev, dpitch, host, hpitch, width, rows, cudaMemcpyHostToDevice, st);
 }
 
-constexpr int kMaxHostBlocks = 8;
+constexpr int kMaxHostBlocks = 16;           // events of column blocks (at most 9 are used) and row blocks
+constexpr int kTargetBlocks = 8;
 constexpr int64_t kHostBlockMin = 2048;
 
 // Columns of C (rows of op(A)) per block of a host-buffer call: about eight
@@ -142,8 +143,19 @@ constexpr int64_t kHostBlockMin = 2048;
 // 8192^3 from pinned buffers ran at 165 TFLOPS with 1024, 182 with 2048).
 int64_t host_block(int64_t len) {
   if (len <= kHostBlockMin) return len;
-  int64_t cb = round_up((len + kMaxHostBlocks - 1) / kMaxHostBlocks, 256);
+  int64_t cb = round_up((len + kTargetBlocks - 1) / kTargetBlocks, 256);
   return cb < kHostBlockMin ? kHostBlockMin : cb;
+}
+
+// Width of the first column block when there are several: half a block
+// (a multiple of 256).  While A arrives block of rows by block of rows, the
+// first column block's products are all the GPU can do, and the copy of A
+// slows them; a narrower first block keeps that work close to the pace A
+// arrives at, and the wider blocks after it run at full speed.
+int64_t first_block(int64_t n, int64_t cb) {
+  if (n <= cb) return n;
+  const int64_t h = round_up(cb / 2, 256);
+  return h < cb ? h : cb;
 }
 
 // Per-device side stream and events.  Host-buffer calls on one device are
@@ -213,20 +225,29 @@ void trace_reset() {
   g_trace.n = 0;
 }
 
-// State of one host-buffer call, seen by the block hooks.
+// State of one host-buffer call, seen by the block hooks.  Column block 0
+// covers [0, nb0), block c > 0 covers [nb0 + (c - 1) cb, ...).
 struct HostCall {
   Side* sd;
   int64_t n;
-  int64_t cb, mb;             // columns per column block, rows per row block
+  int64_t cb, mb;             // columns per column block (after the first), rows per row block
+  int64_t nb0;                // columns of the first column block
   char* dC;                   // device copy of C (leading dimension ldc)
   void* C;                    // caller's C
   const void* Cv;             // its device view, or nullptr (pageable)
   size_t pitch, width;        // ldc and m in bytes
+  int64_t c_dev_end;          // pinned C: columns below this go through dC and back by DMA
+  int64_t block_of(int64_t j) const { return j < nb0 ? 0 : 1 + (j - nb0) / cb; }
+  int64_t block_begin(int64_t c) const { return c == 0 ? 0 : nb0 + (c - 1) * cb; }
+  int64_t block_cols(int64_t c) const {
+    const int64_t b = block_begin(c), w = c == 0 ? nb0 : cb;
+    return std::min(w, n - b);
+  }
 };
 
 emu_status_t wait_inputs(void* ctx, int64_t j0, int64_t nj, cudaStream_t st) {
   const HostCall* hc = static_cast<const HostCall*>(ctx);
-  for (int64_t c = j0 / hc->cb; c <= (j0 + nj - 1) / hc->cb; ++c)
+  for (int64_t c = hc->block_of(j0); c <= hc->block_of(j0 + nj - 1); ++c)
     if (cudaStreamWaitEvent(st, hc->sd->in[c], 0) != cudaSuccess) return EMU_ERR_CUDA;
   trace(EMU_TRACE_BLOCK_START, st);
   return EMU_OK;
@@ -239,11 +260,24 @@ emu_status_t wait_rows(void* ctx, int64_t i0, int64_t mi, cudaStream_t st) {
   return EMU_OK;
 }
 
-// A column block of C is final once its CRT is done.  Pinned C: the CRT wrote it
-// straight into host memory.  Pageable C: it goes back in one piece after the
-// last block (a copy into pageable memory holds the calling thread).
-emu_status_t output_done(void* /*ctx*/, int64_t /*j0*/, int64_t /*nj*/, cudaStream_t st) {
+// A column block of C is final once its CRT is done.  Pinned C, last block (or
+// beta != 0): the CRT wrote it straight into host memory.  Pinned C, earlier
+// blocks: the CRT wrote the device copy, and the DMA engines bring it back on
+// the side stream while the next block computes (stores from SMs into host
+// memory slowed the residue products beside them; the DMA engines do not).
+// Pageable C: it goes back in one piece after the last block (a copy into
+// pageable memory holds the calling thread).
+emu_status_t output_done(void* ctx, int64_t j0, int64_t nj, cudaStream_t st) {
+  const HostCall* hc = static_cast<const HostCall*>(ctx);
   trace(EMU_TRACE_BLOCK_CRT, st);
+  if (hc->Cv && j0 < hc->c_dev_end) {
+    const size_t off = static_cast<size_t>(j0) * hc->pitch;
+    if (cudaEventRecord(hc->sd->out, st) != cudaSuccess || cudaStreamWaitEvent(hc->sd->s, hc->sd->out, 0) != cudaSuccess ||
+        cudaMemcpy2DAsync(static_cast<char*>(hc->C) + off, hc->pitch, hc->dC + off, hc->pitch, hc->width,
+                          static_cast<size_t>(nj), cudaMemcpyDeviceToHost, hc->sd->s) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    trace(EMU_TRACE_C_OUT, hc->sd->s);
+  }
   return EMU_OK;
 }
 
@@ -269,14 +303,21 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
   std::lock_guard<std::mutex> lk(sd->mu);
   char* stg = nullptr;
   const void* Cv = device_view(C);
-  s = get_staging(al(bA) + al(bB) + (Cv ? 0 : al(bC)), &stg);   // pinned C is written in place
+  const int64_t cb_all = host_block(n);
+  const int64_t nb0 = first_block(n, cb_all);
+  const int64_t cb = n > nb0 ? host_block(n - nb0) : n;
+  const int64_t nblk = n > nb0 ? 1 + (n - nb0 + cb - 1) / cb : 1;
+  // pinned C with beta = 0 and several blocks: all but the last block through the device copy
+  const int64_t c_dev_end = (Cv && !use_beta && nblk > 1) ? nb0 + (nblk - 2) * cb : 0;
+  s = get_staging(al(bA) + al(bB) + ((!Cv || c_dev_end > 0) ? al(bC) : 0), &stg);
   if (s != EMU_OK) return s;
   char* dA = stg;
   char* dB = stg + al(bA);
   char* dC = dB + al(bB);
-  HostCall hc{sd, n, host_block(n), host_block(m), dC, C, Cv, static_cast<size_t>(ldc) * esz,
-              static_cast<size_t>(m) * esz};
-  const int64_t nblk = (n + hc.cb - 1) / hc.cb, mblk = (m + hc.mb - 1) / hc.mb;
+  HostCall hc{sd, n, cb, host_block(m), nb0, dC, C, Cv, static_cast<size_t>(ldc) * esz,
+              static_cast<size_t>(m) * esz, c_dev_end};
+  const int64_t mblk = (m + hc.mb - 1) / hc.mb;
+  if (nblk > kMaxHostBlocks || mblk > kMaxHostBlocks) return EMU_ERR_UNSUPPORTED;
   const size_t lda_b = static_cast<size_t>(lda) * esz, ldb_b = static_cast<size_t>(ldb) * esz;
   const void* Av = device_view(A);
   const void* Bv = device_view(B);
@@ -297,7 +338,7 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
                     contiguous || !view ? Shape::kDma : Shape::kNarrow, sd->s);
   };
   auto bring_cols = [&](int64_t c) -> cudaError_t {   // columns c0.. of op(B) (and of C)
-    const int64_t c0 = c * hc.cb, cn = std::min(hc.cb, n - c0);
+    const int64_t c0 = hc.block_begin(c), cn = hc.block_cols(c);
     cudaError_t e = cudaSuccess;
     if (bB)   // columns c0.. of the stored k x n matrix, or rows c0.. of the stored n x k matrix
       e = tb == EMU_OP_N ? bring(dB, B, Bv, c0 * ldb_b, ldb_b, static_cast<size_t>(k) * esz, static_cast<size_t>(cn))
@@ -325,7 +366,8 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
   for (int64_t c = 1; c < nblk && res == EMU_OK; ++c)
     if (bring_cols(c) != cudaSuccess) res = EMU_ERR_CUDA;
   if (res == EMU_OK) {
-    const BlockHooks hooks{hc.cb, hc.mb, &hc, wait_inputs, wait_rows, output_done, products_start};
+    const BlockHooks hooks{hc.cb, hc.mb, hc.nb0, c_dev_end > 0 ? static_cast<void*>(dC) : nullptr, c_dev_end, &hc,
+                           wait_inputs, wait_rows, output_done, products_start};
     res = run_gemm(single, real, ta, tb, m, n, k, ar, ai, bA ? dA : nullptr, lda, bB ? dB : nullptr, ldb, br, bi,
                    Cv ? const_cast<void*>(Cv) : static_cast<void*>(dC),
                    ldc, N, stream, &hooks);

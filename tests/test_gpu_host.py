@@ -171,11 +171,14 @@ def test_host_calls_on_two_streams():
 
 
 def test_host_trace_records_the_pipeline():
-    m, n, k, N = 2304, 2048 + 1101, 32, 6            # two blocks of rows of A, two column blocks
+    # two blocks of rows of A; three column blocks: a first block of half the
+    # width (1024), then [1024, 3072) and the ragged [3072, 3149)
+    m, n, k, N = 2304, 2048 + 1101, 32, 6
     A, B, _ = _mats("z", m, n, k, "N", "N", 350)
     hA, pa, _ = _stored(A, m, True)
     hB, pb, _ = _stored(B, k, True)
-    hC, pc, _ = _stored(np.zeros((m, n), np.complex128), m, True)
+    hC, pc, view = _stored(np.zeros((m, n), np.complex128), m, True)
+    ref = _device_ref("z", A, B, np.zeros((m, n), np.complex128), m, n, k, "N", "N", 1.0, 0.0, N)
     emu.check(emu.emu_host_trace_enable(1), "trace on")
     try:
         emu.check(emu.emu_zgemm_host("N", "N", m, n, k, 1.0, pa, m, pb, k, 0.0, pc, m, N), "host call")
@@ -183,23 +186,27 @@ def test_host_trace_records_the_pipeline():
         tr = emu.emu_host_trace_read()
     finally:
         emu.emu_host_trace_enable(0)
+    assert same_bits(np.ascontiguousarray(view()), np.ascontiguousarray(ref))
     names = [t[0] for t in tr]
     ms = {}
     for nm, t in tr:
         ms.setdefault(nm, []).append(t)
-    # side stream: the first column block, A's two blocks of rows, the other column block
+    # side stream: the first column block, A's two blocks of rows, the other column blocks
     side_in = [nm for nm in names if nm in ("a_in", "b_in")]
-    assert side_in == ["b_in", "a_in", "a_in", "b_in"]
+    assert side_in == ["b_in", "a_in", "a_in", "b_in", "b_in"]
     assert names[0] == "start" and names[-1] == "end"
-    # pinned C is written in place by each block's CRT: no separate copy back
-    assert [len(ms.get(nm, [])) for nm in ("block_start", "block_crt", "c_out")] == [2, 2, 0]
+    # pinned C (beta = 0): every block but the last goes through the device copy and back by DMA,
+    # the last block's CRT writes host memory in place
+    assert [len(ms.get(nm, [])) for nm in ("block_start", "block_crt", "c_out")] == [3, 3, 2]
     assert ms["start"] == [0.0] and min(t for _, t in tr) >= 0.0
     assert ms["end"][0] >= max(t for _, t in tr)             # the call ends after every step
     assert ms["block_crt"][0] >= ms["a_in"][-1]               # the first block used all of A
-    for b in range(2):
+    for b in range(3):
         s, c = ms["block_start"][b], ms["block_crt"][b]
         assert s <= c                                        # block start, its CRT
         assert s >= ms["b_in"][b]                            # after its columns of B arrived
+    for b in range(2):
+        assert ms["c_out"][b] >= ms["block_crt"][b]           # copied back after its CRT
 
 
 @pytest.mark.parametrize("kind,opA,scaling", [("z", "N", "fast"), ("s", "T", "fast"), ("c", "C", "fast"),
