@@ -141,31 +141,37 @@ struct TcSingle {
 };
 
 // Many problems (a grouped call): CrtProb descriptors whose block_begin is the
-// first item and iblocks the 128-row blocks of each problem; an item's problem
-// is found by binary search.
+// first item and iblocks the 128-row blocks of each problem.  A block's items
+// only move forward, so the cursor keeps its problem and steps past the
+// problems it has left (binary search only for the first item).
 struct TcGrouped {
   const CrtProb* probs;
   int nprob;
   int total;
   struct Cursor {
-    int it;
+    int it, p;
   };
-  __device__ Cursor begin(int first) const { return Cursor{first}; }
+  __device__ Cursor begin(int first) const {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].block_begin <= first) lo = mid; else hi = mid - 1;
+    }
+    return Cursor{first, lo};
+  }
   __device__ void steps(int stride, int& dj, int& dib) const {
     dj = stride;
     dib = 0;
   }
-  __device__ void advance(Cursor& c, int dj, int) const { c.it += dj; }
+  __device__ void advance(Cursor& c, int dj, int) const {
+    c.it += dj;
+    while (c.p + 1 < nprob && probs[c.p + 1].block_begin <= c.it) ++c.p;
+  }
   __device__ TcPos pos(const Cursor& cur) const {
     if (cur.it >= total) return TcPos{0, -1, 0};
-    int lo = 0, hi = nprob - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (probs[mid].block_begin <= cur.it) lo = mid; else hi = mid - 1;
-    }
-    const unsigned local = static_cast<unsigned>(cur.it - probs[lo].block_begin);
-    const unsigned ib = static_cast<unsigned>(probs[lo].iblocks);
-    return TcPos{lo, static_cast<int>(local / ib), static_cast<int>(local % ib) * 128};
+    const unsigned local = static_cast<unsigned>(cur.it - probs[cur.p].block_begin);
+    const unsigned ib = static_cast<unsigned>(probs[cur.p].iblocks);
+    return TcPos{cur.p, static_cast<int>(local / ib), static_cast<int>(local % ib) * 128};
   }
   __device__ const CrtProb& prob(int p) const { return probs[p]; }
 };

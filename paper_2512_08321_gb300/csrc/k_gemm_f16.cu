@@ -264,8 +264,12 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       bool ok = true;
       const CUtensorMap* fenced = nullptr;
       int hint = 0;
+      // the next unit's descriptor is fetched while this one's loads are issued
+      Unit nxt;
+      if (blockIdx.x < nunits) nxt = W.get(blockIdx.x, hint);
       for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Unit U = W.get(u, hint);
+        const Unit U = nxt;
+        if (u + gridDim.x < nunits) nxt = W.get(u + gridDim.x, hint);
         if (fence_maps && U.mapA != fenced) {
           // descriptors written by the host into global memory: acquire them for the TMA unit
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(U.mapA) : "memory");
@@ -307,8 +311,12 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       uint32_t used = 0u;                           // bit s: parity of slot s's uses so far
       bool ok = true;
       int hint = 0;
+      // the next unit's descriptor is fetched while this one's MMAs are issued
+      Unit nxt;
+      if (blockIdx.x < nunits) nxt = W.get(blockIdx.x, hint);
       for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Unit U = W.get(u, hint);
+        const Unit U = nxt;
+        if (u + gridDim.x < nunits) nxt = W.get(u + gridDim.x, hint);
         for (int c = 0; ok && c < U.nch; ++c) {
           for (int which = 0; ok && which < 2; ++which) {
             const int job = which ? U.jb : U.ja;
