@@ -440,12 +440,25 @@ def main():
         eb.record()
         barrier()
         e_ms = max_over_ranks(ea.elapsed_time(eb) / args.steps, dist)
+        # one more call with the library's trace: when A, B arrived and each column block finished
+        emu.emu_host_trace_enable(True)
+        e2e_step()
+        torch.cuda.synchronize()
+        tr = emu.emu_host_trace_read()
+        emu.emu_host_trace_enable(False)
         step()                                 # the device call once more (C last held the FP64-CRT result)
         torch.cuda.synchronize()
+        ev = {}
+        for nm, t in tr:
+            ev.setdefault(nm, []).append(round(t, 2))
+        trace_summary = {"a_in_done_ms": max(ev.get("a_in", [0.0])), "b_in_done_ms": max(ev.get("b_in", [0.0])),
+                         "block_crt_ms": ev.get("block_crt", []), "c_out_ms": ev.get("c_out", []),
+                         "end_ms": max(ev.get("end", [0.0]))}
         out["e2e"] = {"value": world * flops / (e_ms * 1e-3) * 1e-12, "unit": "TFLOPS",
                       "h2d_bytes_per_step": esz * (m * k + k * n), "d2h_bytes_per_step": esz * m * n,
                       "ms_per_step": e_ms, "call": fh.__name__ + " (pinned host A, B, C)",
-                      "bitexact_vs_device_call": bool(torch.equal(Ch, C.cpu()))}
+                      "bitexact_vs_device_call": bool(torch.equal(Ch, C.cpu())),
+                      "trace_of_one_more_call": trace_summary}
         del Ah, Bh, Ch
 
     # ---- comparators on the same GPU (rank 0)

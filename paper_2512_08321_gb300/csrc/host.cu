@@ -260,11 +260,11 @@ emu_status_t wait_rows(void* ctx, int64_t i0, int64_t mi, cudaStream_t st) {
   return EMU_OK;
 }
 
-// A column block of C is final once its CRT is done.  Pinned C, last block (or
-// beta != 0): the CRT wrote it straight into host memory.  Pinned C, earlier
-// blocks: the CRT wrote the device copy, and the DMA engines bring it back on
-// the side stream while the next block computes (stores from SMs into host
-// memory slowed the residue products beside them; the DMA engines do not).
+// A column block of C is final once its CRT is done.  Pinned C, last two
+// blocks (or beta != 0): the CRT wrote it straight into host memory.  Pinned C,
+// earlier blocks: the CRT wrote the device copy, and the DMA engines bring it
+// back on the side stream while the next blocks compute (stores from SMs into
+// host memory slowed the residue products beside them; the DMA engines do not).
 // Pageable C: it goes back in one piece after the last block (a copy into
 // pageable memory holds the calling thread).
 emu_status_t output_done(void* ctx, int64_t j0, int64_t nj, cudaStream_t st) {
@@ -307,8 +307,11 @@ emu_status_t gemm_host(bool single, bool real, emu_op_t ta, emu_op_t tb, int64_t
   const int64_t nb0 = first_block(n, cb_all);
   const int64_t cb = n > nb0 ? host_block(n - nb0) : n;
   const int64_t nblk = n > nb0 ? 1 + (n - nb0 + cb - 1) / cb : 1;
-  // pinned C with beta = 0 and several blocks: all but the last block through the device copy
-  const int64_t c_dev_end = (Cv && !use_beta && nblk > 1) ? nb0 + (nblk - 2) * cb : 0;
+  // pinned C with beta = 0: the blocks before the last two go through the device copy and back by
+  // DMA, each copy hidden behind at least two blocks of computation (beside the residue products
+  // those copies ran at 12-190 GB/s, too slow to hide behind the last block alone); the last two
+  // blocks' CRTs write host memory in place
+  const int64_t c_dev_end = (Cv && !use_beta && nblk > 2) ? nb0 + (nblk - 3) * cb : 0;
   s = get_staging(al(bA) + al(bB) + ((!Cv || c_dev_end > 0) ? al(bC) : 0), &stg);
   if (s != EMU_OK) return s;
   char* dA = stg;

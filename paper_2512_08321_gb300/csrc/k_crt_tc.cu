@@ -474,22 +474,24 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kNC));
 }
 
-// Registers per thread: 64 lets 8 blocks share an SM (as many as its TMEM
-// holds); the variants that would spill at 64 (one limb; two or three real limbs)
-// and the 64-column ones (whose shared memory allows fewer blocks) get more.
+// Minimum resident blocks (which caps registers per thread): 8 blocks of 64
+// registers fill an SM (as many as its TMEM holds).  Four complex limbs mean
+// N >= 13, three K tiles and 6 blocks by shared memory, so those variants may
+// use 80 registers, as may the ones that would spill at 64 (one limb; two or
+// three real limbs); the 64-column ones (fewer blocks still) about 100.
 template <bool REAL, bool WIDE, int L>
-constexpr int tc_regs() {
-  return WIDE ? 96 : ((L == 1 || (REAL && (L == 2 || L == 3))) ? 80 : 64);
+constexpr int tc_min_blocks() {
+  return WIDE ? 5 : ((L == 1 || (REAL && (L == 2 || L == 3)) || (!REAL && L == 4)) ? 6 : 8);
 }
 
 template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST>
-__global__ void __maxnreg__((tc_regs<REAL, WIDE, L>())) crt_tc_kernel(const TcSingle W, const __grid_constant__ Plan pl,
+__global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<REAL, WIDE, L>())) crt_tc_kernel(const TcSingle W, const __grid_constant__ Plan pl,
                                                             unsigned int* status) {
   crt_tc_body<SINGLE, REAL, WIDE, L, ROBUST>(W, pl, status);
 }
 
 template <bool SINGLE, bool WIDE, int L>
-__global__ void __maxnreg__((tc_regs<false, WIDE, L>())) crt_tc_grouped_kernel(const TcGrouped W, const __grid_constant__ Plan pl,
+__global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<false, WIDE, L>())) crt_tc_grouped_kernel(const TcGrouped W, const __grid_constant__ Plan pl,
                                                                     unsigned int* status) {
   crt_tc_body<SINGLE, false, WIDE, L, false>(W, pl, status);
 }

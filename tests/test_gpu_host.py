@@ -195,9 +195,9 @@ def test_host_trace_records_the_pipeline():
     side_in = [nm for nm in names if nm in ("a_in", "b_in")]
     assert side_in == ["b_in", "a_in", "a_in", "b_in", "b_in"]
     assert names[0] == "start" and names[-1] == "end"
-    # pinned C (beta = 0): every block but the last goes through the device copy and back by DMA,
-    # the last block's CRT writes host memory in place
-    assert [len(ms.get(nm, [])) for nm in ("block_start", "block_crt", "c_out")] == [3, 3, 2]
+    # pinned C (beta = 0): the blocks before the last two go through the device copy and back by
+    # DMA, the last two blocks' CRTs write host memory in place
+    assert [len(ms.get(nm, [])) for nm in ("block_start", "block_crt", "c_out")] == [3, 3, 1]
     assert ms["start"] == [0.0] and min(t for _, t in tr) >= 0.0
     assert ms["end"][0] >= max(t for _, t in tr)             # the call ends after every step
     assert ms["block_crt"][0] >= ms["a_in"][-1]               # the first block used all of A
@@ -205,8 +205,7 @@ def test_host_trace_records_the_pipeline():
         s, c = ms["block_start"][b], ms["block_crt"][b]
         assert s <= c                                        # block start, its CRT
         assert s >= ms["b_in"][b]                            # after its columns of B arrived
-    for b in range(2):
-        assert ms["c_out"][b] >= ms["block_crt"][b]           # copied back after its CRT
+    assert ms["c_out"][0] >= ms["block_crt"][0]               # copied back after its CRT
 
 
 @pytest.mark.parametrize("kind,opA,scaling", [("z", "N", "fast"), ("s", "T", "fast"), ("c", "C", "fast"),
