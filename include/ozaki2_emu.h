@@ -347,6 +347,13 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *                        cores, 0 limb products on the CUDA cores (also used,
  *                        whatever the setting, for a CRT running beside residue
  *                        products on the library's second stream)
+ *   EMU_TUNE_CTA_PAIR    residue products: 1 tiles of 256 output columns x 256
+ *                        rows on pairs of SMs (a cluster of two CTAs sharing
+ *                        each MMA, cta_group::2; EMU_TUNE_TILE_N then has no
+ *                        effect), 0 (default) 128-column tiles on one SM; a
+ *                        device without cluster launch support refuses 1 at
+ *                        call time (EMU_ERR_CUDA).  Grouped calls always use
+ *                        one-SM tiles
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
  * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
@@ -358,8 +365,8 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  * value that a call of the given dtype, N and shape will use (the autotuned
  * entry of its bucket, else the process default; -1 for an unknown key).
  * The autotuner searches the tile width, group and chunk, then the schedule
- * knobs 8-11 one at a time, then the CRT engine (and the CUDA-core kernel's
- * rows) and the split entries. */
+ * knobs 8-11 and 13 one at a time, then the CRT engine (and the CUDA-core
+ * kernel's rows) and the split entries. */
 #define EMU_TUNE_TILE_N 1
 #define EMU_TUNE_GROUP 2
 #define EMU_TUNE_CHUNK_K 3
@@ -372,6 +379,7 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 #define EMU_TUNE_KDIR 10
 #define EMU_TUNE_BAND 11
 #define EMU_TUNE_CRT_ENGINE 12
+#define EMU_TUNE_CTA_PAIR 13
 emu_status_t emu_set_tuning(int key, int value);
 int emu_get_tuning(int key);
 int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, int key);

@@ -105,9 +105,10 @@ struct GemmSchedule {
   int pairing = 0;        // 0 adjacent jobs, 1 halves (p, p + ceil(J/2)), 2 component-major (all D, E, F)
   int kalt = 0;           // 1: a CTA's odd units run their k chunks in descending order
   int band_cols = 8192;   // columns per band for order 2 (the paper's n-block), a multiple of 128
+  int cta_pair = 0;       // 1: 256 x 256 tiles on SM pairs (cta_group::2); 0: 128 x tile_n tiles on one SM
   bool valid() const {
     return order >= 0 && order <= 2 && pairing >= 0 && pairing <= 2 && (kalt == 0 || kalt == 1) &&
-           band_cols >= 128 && band_cols <= 65536 && band_cols % 128 == 0;
+           band_cols >= 128 && band_cols <= 65536 && band_cols % 128 == 0 && (cta_pair == 0 || cta_pair == 1);
   }
 };
 
@@ -140,6 +141,9 @@ cudaError_t launch_split(bool single, bool conj, const void* X, int64_t rows, in
 cudaError_t launch_gemm_i8(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                            const int8_t* planesA, const int8_t* planesB, int8_t* res,
                            int64_t ldr, cudaStream_t st, int ppm = 3);
+
+// true when the SM-pair residue-product kernel (GemmSchedule::cta_pair) can run on this device
+bool gemm_pair_supported();
 
 cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl,
                             const void* planesA, const void* planesB, int8_t* res,

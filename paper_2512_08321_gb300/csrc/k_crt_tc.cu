@@ -334,11 +334,13 @@ __device__ __forceinline__ void tc_epilogue(const Q& q, const TcPos& t, uint32_t
   }
 }
 
-// The block's items are pipelined two deep: item n is converted into A
-// buffer n & 1 and its MMA issued into accumulator slot n & 1, then item
-// n - 1's outputs are finished from the other slot while that MMA runs; item
-// n + 1's bytes are copied in meanwhile (each thread stages and converts the
-// same chunks, so one staging buffer suffices).
+// The block's items are pipelined two deep: item n is converted into operand
+// A (once item n - 1's MMA has read it) and its MMA issued into accumulator
+// slot n & 1, then item n - 1's outputs are finished from the other slot while
+// that MMA runs; item n + 1's bytes are copied in meanwhile (each thread
+// stages and converts the same chunks, so one staging buffer suffices).  One
+// A buffer keeps a block's shared memory small enough for as many blocks per
+// SM as the TMEM columns allow.
 template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST, class Work>
 __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsigned int* status) {
   using LY = TcLayout<REAL, WIDE>;
@@ -348,8 +350,8 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
   const int a_bytes = KT * 4096;
   extern __shared__ __align__(128) uint8_t tc_smem[];
   uint8_t* sB = tc_smem;                                  // KT x kBTileBytes
-  uint8_t* sA = sB + KT * LY::kBTileBytes;                // 2 x KT x 4096
-  uint8_t* sS = sA + 2 * a_bytes;                         // J x kStageRow
+  uint8_t* sA = sB + KT * LY::kBTileBytes;                // KT x 4096
+  uint8_t* sS = sA + a_bytes;                             // J x kStageRow
   const int stage_bytes = (J * kStageRow + 127) / 128 * 128;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sS + stage_bytes);   // MMA done, per slot
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -386,10 +388,10 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
     }
     *reinterpret_cast<__half*>(sB + b_off<kNC>(n, k)) = __float2half_rn(val);
   }
-  // A's columns past the jobs, in both buffers: 2048 in the bias entry, zeros after it
-  for (int e = threadIdx.x; e < 2 * 128 * (KT * 16 - J); e += kTcThreads) {
-    const int m = e & 127, k = J + ((e >> 7) >> 1), b = (e >> 7) & 1;
-    *reinterpret_cast<__half*>(sA + b * a_bytes + a_off(m, k)) = __float2half_rn(k == J ? 2048.0f : 0.0f);
+  // A's columns past the jobs: 2048 in the bias entry, zeros after it
+  for (int e = threadIdx.x; e < 128 * (KT * 16 - J); e += kTcThreads) {
+    const int m = e & 127, k = J + (e >> 7);
+    *reinterpret_cast<__half*>(sA + a_off(m, k)) = __float2half_rn(k == J ? 2048.0f : 0.0f);
   }
   tc_fence_before();
   __syncthreads();
@@ -409,14 +411,24 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
   uint32_t ph = 0u;                                       // bit s: parity of slot s's next completion
   uint32_t pending = 0u;                                  // bit s: a commit of slot s not yet waited for
   TcPos prev{0, -1, 0};
-  // one pipeline step with accumulator slot and A buffer SLOT for `cur` (and
-  // SLOT ^ 1 for `prev`); false when the block is done
+  // one pipeline step with accumulator slot SLOT for `cur` (SLOT ^ 1 for
+  // `prev`); false when the block is done
   auto step = [&](auto slot_c) -> bool {
     constexpr int SLOT = decltype(slot_c)::value;
+    constexpr int PS = SLOT ^ 1;
     TcPos next{0, -1, 0};
+    if (prev.j >= 0) {
+      // prev's MMA is done with operand A before A is overwritten (it was issued a whole
+      // epilogue ago, so this seldom waits).  An expired wait sets the abort flag (seen by
+      // every thread after the barrier below); the status word then reports the timeout.
+      if (mbar_wait(bar0 + 8 * PS, (ph >> PS) & 1u, ctl)) {
+        pending &= ~(1u << PS);
+        ph ^= 1u << PS;
+      }
+    }
     if (cur.j >= 0) {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      convert_item(U, sS, sA + SLOT * a_bytes);
+      convert_item(U, sS, sA);
       // the next item's bytes: this thread's chunks only, which it has just converted
       W.advance(cursor, dj, dib);
       next = W.pos(cursor);
@@ -431,23 +443,14 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
     if (*abort_s) return false;                           // read after the barrier: the same in every thread
     if (cur.j >= 0) {
       if (threadIdx.x == 0) {
-        const uint32_t as = a0 + SLOT * a_bytes;
         for (int kt = 0; kt < KT; ++kt)
-          mma_f16(tmem + SLOT * kNC, plain_desc(as + kt * 4096, 128, 256),
+          mma_f16(tmem + SLOT * kNC, plain_desc(a0 + kt * 4096, 128, 256),
                   plain_desc(b0 + kt * LY::kBTileBytes, 128, 256), LY::kIdesc, kt > 0);
         mma_commit(bar0 + 8 * SLOT);
       }
       pending |= 1u << SLOT;
     }
     if (prev.j >= 0) {
-      constexpr int PS = SLOT ^ 1;
-      // an expired wait sets the abort flag (seen by every thread after the next barrier);
-      // this item's outputs are then not trusted: the status word reports the timeout
-      if (mbar_wait(bar0 + 8 * PS, (ph >> PS) & 1u, ctl)) {
-        pending &= ~(1u << PS);
-        ph ^= 1u << PS;
-      }
-      tc_fence_after();
       tc_epilogue<SINGLE, REAL, WIDE, L, ROBUST>(W.prob(prev.p), prev, tmem + PS * kNC, pl);
       tc_fence_before();
     }
@@ -475,13 +478,13 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
 }
 
 // Minimum resident blocks (which caps registers per thread): 8 blocks of 64
-// registers fill an SM (as many as its TMEM holds).  Four complex limbs mean
-// N >= 13, three K tiles and 6 blocks by shared memory, so those variants may
-// use 80 registers, as may the ones that would spill at 64 (one limb; two or
-// three real limbs); the 64-column ones (fewer blocks still) about 100.
+// registers fill an SM (as many as its TMEM holds, and shared memory allows up
+// to N = 16).  The variants that would spill at 64 (one limb; two or three
+// real limbs) may use 80 registers; the 64-column ones (fewer blocks by TMEM)
+// about 100.
 template <bool REAL, bool WIDE, int L>
 constexpr int tc_min_blocks() {
-  return WIDE ? 5 : ((L == 1 || (REAL && (L == 2 || L == 3)) || (!REAL && L == 4)) ? 6 : 8);
+  return WIDE ? 5 : ((L == 1 || (REAL && (L == 2 || L == 3))) ? 6 : 8);
 }
 
 template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST>
@@ -496,21 +499,31 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<false, WIDE, L>()))
   crt_tc_body<SINGLE, false, WIDE, L, false>(W, pl, status);
 }
 
-// Shared memory of one block: operand B, two A buffers, the staging buffer,
-// barriers; raised so that no more blocks fit on an SM than its 512 TMEM
-// columns hold (2 x 32 or 2 x 64 columns a block).  GB300: 228 KB per SM,
-// 1 KB of it reserved per resident block.
+// Shared memory of one block: operand B, operand A, the staging buffer,
+// barriers; raised so that no more blocks fit on an SM than tc_blocks (at most
+// as many as its 512 TMEM columns hold: 2 x 32 or 2 x 64 columns a block).
+// GB300: 228 KB per SM, 1 KB of it reserved per resident block.
 constexpr int kSmemPerSM = 228 * 1024;
 
 int tc_max_blocks(bool real, bool wide) { return 512 / (2 * ((!real && wide) ? 64 : 32)); }
 
-size_t tc_smem_bytes(bool real, bool wide, int N) {
+// Blocks per SM: as many as TMEM holds, except single complex launches of
+// three or more K tiles (N >= 11), which keep 6: ZGEMM 16384^3 with N = 15
+// took 5.61 ms at 6 blocks and 5.70 at 8, while the grouped launch (N = 16,
+// problems of 64 to 2048 rows) went from 4.24 ms at 5 blocks to 3.90 at 8.
+int tc_blocks(bool real, bool wide, int N, bool grouped) {
+  const int tm = tc_max_blocks(real, wide);
+  const int KT = ((real ? 1 : 3) * N + 1 + 15) / 16;
+  return (!grouped && !real && KT >= 3 && tm > 6) ? 6 : tm;
+}
+
+size_t tc_smem_bytes(bool real, bool wide, int N, bool grouped) {
   const int J = (real ? 1 : 3) * N;
   const int KT = (J + 1 + 15) / 16;
   const int nc = (!real && wide) ? 64 : 32;
   const size_t stage = static_cast<size_t>((J * kStageRow + 127) / 128 * 128);
-  size_t need = static_cast<size_t>(KT) * (nc * 32 + 2 * 4096) + stage + 64;
-  const int maxb = tc_max_blocks(real, wide);
+  size_t need = static_cast<size_t>(KT) * (nc * 32 + 4096) + stage + 64;
+  const int maxb = tc_blocks(real, wide, N, grouped);
   const size_t floor_bytes = static_cast<size_t>(kSmemPerSM / (maxb + 1) - 1024 + 128);   // maxb + 1 blocks do not fit
   if (need < floor_bytes) need = floor_bytes;
   return (need + 127) / 128 * 128;
@@ -538,7 +551,7 @@ int tc_grid(long long items, size_t smem) {
 
 template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST>
 cudaError_t launch_tc_v(const TcSingle& W, long long items, const Plan& pl, unsigned int* status, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(REAL, WIDE, pl.N);
+  const size_t smem = tc_smem_bytes(REAL, WIDE, pl.N, false);
   cudaError_t e = prep(crt_tc_kernel<SINGLE, REAL, WIDE, L, ROBUST>, smem);
   if (e != cudaSuccess) return e;
   const int grid = tc_grid(items, smem);
@@ -569,7 +582,7 @@ template <bool SINGLE, int L>
 cudaError_t launch_tc_grouped_l(const TcGrouped& W, const Plan& pl, unsigned int* status, cudaStream_t st,
                                 bool prepare_only) {
   constexpr bool kWide = L >= 5;
-  const size_t smem = tc_smem_bytes(false, kWide, pl.N);
+  const size_t smem = tc_smem_bytes(false, kWide, pl.N, true);
   cudaError_t e = prep(crt_tc_grouped_kernel<SINGLE, kWide, L>, smem);
   if (e != cudaSuccess || prepare_only) return e;
   const int grid = tc_grid(W.total, smem);

@@ -466,6 +466,288 @@ __global__ void __launch_bounds__(kThreads, 1)
   gemm_body<BN, kEpiWarps>(W, pl, status, false);
 }
 
+// ------------------------------------------------------------------ SM pairs
+// cta_group::2: the two CTAs of a cluster share one 256 x 256 tile.  MMA M =
+// 256 output columns, 128 in each CTA's TMEM lanes (CTA r holds the tile's
+// columns 128 r .. 128 r + 127, from its own stage of B-plane rows); MMA N =
+// 256 output rows, whose A-plane rows each CTA loads half of (rows 128 r ..).
+// The even CTA issues the MMAs for both; its commits arrive on the barriers of
+// both CTAs (multicast), and both CTAs' TMA loads count on its full barriers.
+// Each SM stages 32 KB per k-block instead of the 48 KB of a 128 x 256 tile on
+// one SM, for the same MMA work per SM.  The epilogue is the one-SM kernel's,
+// each CTA on its own TMEM; its arrivals on `tempty` go to the even CTA.
+// Measured at ZGEMM 16384^3, N = 15: 7 % fewer SM cycles than one-SM tiles,
+// but the GPU then sits lower under its power cap (1515-1575 against
+// 1826-1852 MHz), so the products took 255 ms against 231: an autotuner
+// candidate, not the default.
+constexpr int kPairStages = 6;
+constexpr int kPairRows = 128;                                   // A-plane rows per CTA per stage
+constexpr int kPairStageBytes = kStageA + kPairRows * BK * 2;    // 32 KB
+constexpr int kPairBN = 256;                                     // MMA N: output rows per tile
+constexpr int kPairBM = 2 * BM;                                  // output columns per tile
+constexpr int kPairSmem = kPairStages * kPairStageBytes + 1024 + 256;
+constexpr uint32_t kPairIdesc = (1u << 4) | (static_cast<uint32_t>(kPairBN >> 3) << 17) |
+                                (static_cast<uint32_t>(kPairBM >> 4) << 24);
+
+__device__ __forceinline__ void pair_body(const SingleWork<kPairBN>& W, const Plan& pl, unsigned int* status) {
+  constexpr int EPI = kEpiWarps;
+  constexpr int kParts = EPI / 4;
+  constexpr int S = kPairStages;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;                 // the same offset in both CTAs
+  uint8_t* gbase = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + S * kPairStageBytes);
+  // barrier layout: full[S], empty[S], tfull[2], tempty[2], done
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (S + i); };
+  auto tfull = [&](int i) { return bar0 + 8u * (2 * S + i); };
+  auto tempty = [&](int i) { return bar0 + 8u * (2 * S + 2 + i); };
+  const uint32_t done = bar0 + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  Ctl ctl{status, abort_s};
+  const long long nunits = W.units();
+  const long long pid = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int kalt = W.s.kalt;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull(i), 1);
+      mbar_init(tempty(i), 2 * 32 * EPI);
+    }
+    mbar_init(done, 1);
+    *abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {   // one warp of each CTA: the same 512 columns in both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * kPairBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n");
+  }
+  tc_fence_before();
+  cluster_sync();                    // both CTAs' barriers initialised and TMEM allocated
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t full_c0 = map_to_rank(full(0), 0);           // the even CTA's full barriers
+  const uint32_t tempty_c0 = map_to_rank(tempty(0), 0);       // and tempty barriers
+
+  auto get = [&](long long u, int& hint) {
+    Unit U = W.get(u, hint);
+    U.desc = kalt && ((((u - pid) / npairs) & 1) != 0);        // the same in both CTAs
+    return U;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer (both CTAs)
+    if (lane == 0) {
+      long long it = 0;
+      bool ok = true;
+      int hint = 0;
+      Unit nxt;
+      if (pid < nunits) nxt = get(pid, hint);
+      for (long long u = pid; ok && u < nunits; u += npairs) {
+        const Unit U = nxt;
+        if (u + npairs < nunits) nxt = get(u + npairs, hint);
+        for (int c = 0; ok && c < U.nch; ++c) {
+          const int a = U.desc ? U.nch - 1 - c : c;
+          for (int which = 0; ok && which < 2; ++which) {
+            const int job = which ? U.jb : U.ja;
+            if (job < 0) continue;
+            const int kb1 = min(U.nkb, (a + 1) * U.ck);
+            for (int kb = a * U.ck; kb < kb1; ++kb, ++it) {
+              const int st = static_cast<int>(it % S);
+              const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+              if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
+              // the even CTA's full barrier counts the bytes of both CTAs' loads
+              if (leader) mbar_expect_tx(full(st), static_cast<uint32_t>(2 * kPairStageBytes));
+              const uint32_t sa = base + st * kPairStageBytes;
+              const uint32_t fb = full_c0 + 8u * st;
+              tma_load_3d_pair(sa, U.mapA, fb, kb * BK, U.tj * kPairBM + static_cast<int>(rank) * BM, job);
+              tma_load_3d_pair(sa + kStageA, U.mapB, fb, kb * BK, U.ti * kPairBN + static_cast<int>(rank) * kPairRows,
+                               job);
+            }
+          }
+        }
+      }
+      // drain: every load issued has landed (the even CTA's barriers count both CTAs' bytes)
+      if (leader) {
+        for (int st = 0; st < S; ++st) {
+          if (it <= st) continue;
+          const long long last = st + ((it - 1 - st) / S) * S;
+          const uint32_t ph = static_cast<uint32_t>((last / S) & 1);
+          const long long t0 = clock64();
+          while (!mbar_try_cluster(full(st), ph) && clock64() - t0 < kWaitLimit) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer (the even CTA)
+    if (lane == 0 && leader) {
+      long long it = 0;
+      uint32_t used = 0u;
+      bool ok = true;
+      int hint = 0;
+      Unit nxt;
+      if (pid < nunits) nxt = get(pid, hint);
+      for (long long u = pid; ok && u < nunits; u += npairs) {
+        const Unit U = nxt;
+        if (u + npairs < nunits) nxt = get(u + npairs, hint);
+        for (int c = 0; ok && c < U.nch; ++c) {
+          for (int which = 0; ok && which < 2; ++which) {
+            const int job = which ? U.jb : U.ja;
+            if (job < 0) continue;
+            const int slot = which;
+            // both CTAs' epilogues have emptied this slot
+            if (!mbar_wait_cluster(tempty(slot), ((used >> slot) & 1u) ^ 1u, ctl)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t td = tmem + static_cast<uint32_t>(slot * kPairBN);
+            const int a = U.desc ? U.nch - 1 - c : c;
+            const int kb0 = a * U.ck, kb1 = min(U.nkb, (a + 1) * U.ck);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+              const int st = static_cast<int>(it % S);
+              const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+              if (!mbar_wait_cluster(full(st), ph, ctl)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t sa = base + st * kPairStageBytes;
+              const uint64_t da = smem_desc(sa), db = smem_desc(sa + kStageA);
+#pragma unroll
+              for (int kk = 0; kk < BK / UK; ++kk) {
+                const uint64_t off = static_cast<uint64_t>((kk * UK * 2) >> 4);
+                mma_f16_pair(td, da + off, db + off, kPairIdesc, !(c == 0 && kb == kb0 && kk == 0));
+              }
+              mma_commit_pair(empty(st));             // the stage is free in both CTAs
+            }
+            if (!ok) break;
+            mma_commit_pair(tfull(slot));
+            used ^= 1u << slot;
+          }
+        }
+      }
+      mma_commit_pair(done);
+      const long long t0 = clock64();
+      while (!mbar_try(done, 0u) && clock64() - t0 < kWaitLimit) {
+      }
+    } else if (lane == 0) {
+      // the odd CTA: the even CTA's last commit also arrives here once every MMA that
+      // reads this CTA's shared memory or writes its TMEM is done
+      const long long t0 = clock64();
+      while (!mbar_try(done, 0u) && clock64() - t0 < kWaitLimit) {
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (both CTAs)
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int part = ew >> 2;
+    const int row_in_tile = quad * 32 + lane;
+    constexpr int pw = kPairBN / kParts;
+    uint32_t used = 0u;
+    bool ok = true;
+    int hint = 0;
+    for (long long u = pid; ok && u < nunits; u += npairs) {
+      const Unit U = get(u, hint);
+      const int64_t col = static_cast<int64_t>(U.tj) * kPairBM + static_cast<int64_t>(rank) * BM + row_in_tile;
+      for (int c = 0; ok && c < U.nch; ++c) {
+        const bool last = (c == U.nch - 1);
+        for (int which = 0; ok && which < 2; ++which) {
+          const int job = which ? U.jb : U.ja;
+          if (job < 0) continue;
+          const int slot = which;
+          const int l = job / U.ppm;
+          const float p = static_cast<float>(pl.p[l]);
+          const float inv_p = 1.0f / p;
+          const int pi = pl.p[l];
+          if (!mbar_wait(tfull(slot), (used >> slot) & 1u, ctl)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) +
+                              static_cast<uint32_t>(slot * kPairBN + part * pw);
+          if (!last) {
+#pragma unroll 1
+            for (int cc = 0; cc < pw; cc += 32) {
+              uint32_t v[32];
+              tmem_ld32(ta + cc, v);
+              tmem_wait_ld();
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                const float x = __uint_as_float(v[q]);
+                v[q] = __float_as_uint(fmaf(-rintf(x * inv_p), p, x));
+              }
+              tmem_st32(ta + cc, v);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive_cluster(tempty_c0 + 8u * slot);
+          } else {
+            const int64_t row0 = static_cast<int64_t>(U.ti) * kPairBN + part * pw;
+            int8_t* out = U.res + static_cast<int64_t>(job) * U.n * U.ldr + col * U.ldr + row0;
+#pragma unroll 1
+            for (int cc = 0; cc < pw; cc += 32) {
+              uint32_t v[32];
+              tmem_ld32(ta + cc, v);
+              tmem_wait_ld();
+              if (cc == pw - 32) {
+                tc_fence_before();
+                mbar_arrive_cluster(tempty_c0 + 8u * slot);
+              }
+              uint32_t w[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                uint32_t packed = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  const float x = __uint_as_float(v[4 * q + b]);
+                  int r = static_cast<int>(fmaf(-rintf(x * inv_p), p, x));
+                  if (2 * r >= pi) r -= pi;
+                  if (2 * r < -pi) r += pi;
+                  packed |= (static_cast<uint32_t>(r) & 0xFFu) << (8 * b);
+                }
+                w[q] = packed;
+              }
+              if (col < U.n) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                  const int64_t r0 = row0 + cc + 16 * q;
+                  if (r0 < U.rcap)
+                    *reinterpret_cast<uint4*>(out + cc + 16 * q) =
+                        make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+                }
+              }
+            }
+          }
+          used ^= 1u << slot;
+        }
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ teardown
+  tc_fence_before();
+  cluster_sync();                    // no CTA leaves while the pair's MMAs or loads may touch it
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kPairBN));
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    gemm_f16_pair_kernel(const __grid_constant__ CUtensorMap mapA,   // B planes: MMA operand A
+                         const __grid_constant__ CUtensorMap mapB,   // A planes: MMA operand B
+                         const __grid_constant__ Plan pl, const Sched s, int8_t* __restrict__ res, int64_t ldr,
+                         int64_t n, int64_t rcap, unsigned int* status) {
+  const SingleWork<kPairBN> W{&mapA, &mapB, s, res, ldr, n, rcap};
+  pair_body(W, pl, status);
+}
+
 // Grouped launches: 256-row stages with each problem's own tile width, and 16
 // epilogue warps (short-k units are bound by their epilogue, not their MMAs).
 constexpr int kGroupedEpi = 16;
@@ -540,9 +822,74 @@ cudaError_t launch_single(int64_t m, int64_t n, int64_t kpad, const Plan& pl, co
   return cudaGetLastError();
 }
 
+cudaError_t set_pair_attrs() {
+  static cudaError_t err = [] {
+    cudaError_t e = cudaFuncSetAttribute(gemm_f16_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_f16_pair_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               static_cast<int>(cudaSharedmemCarveoutMaxShared));
+    return e;
+  }();
+  return err;
+}
+
+// SM pairs that can hold a CTA pair of the kernel at once (0 if none or on error)
+int pair_clusters() {
+  static int n = [] {
+    if (set_pair_attrs() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 1024);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kPairSmem;
+    int v = 0;
+    if (cudaOccupancyMaxActiveClusters(&v, gemm_f16_pair_kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    return v;
+  }();
+  return n;
+}
+
+cudaError_t launch_pair(int64_t m, int64_t n, int64_t kpad, const Plan& pl, const void* planesA, const void* planesB,
+                        int8_t* res, int64_t ldr, int chunk_k, int group, unsigned int* status, cudaStream_t st,
+                        int ppm, int64_t a_plane_rows, int64_t rcap, const GemmSchedule& sc) {
+  cudaError_t e = set_pair_attrs();
+  if (e != cudaSuccess) return e;
+  const int clusters = pair_clusters();
+  if (clusters <= 0) return cudaErrorNotSupported;
+  const int J = ppm * pl.N;
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, planesB, n, kpad, J, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, planesA, m, kpad, J, kPairRows, a_plane_rows)) return cudaErrorInvalidValue;
+  Sched s;
+  s.J = J;
+  s.ppm = ppm;
+  s.pairs = (J + 1) / 2;
+  s.TJ = static_cast<int>((n + kPairBM - 1) / kPairBM);
+  s.TI = static_cast<int>((m + kPairBN - 1) / kPairBN);
+  s.tiles = s.TJ * s.TI;
+  s.group = group > 0 ? group : 16;
+  s.nkb = static_cast<int>(kpad / BK);
+  s.ck = chunk_k / BK;
+  s.nch = (s.nkb + s.ck - 1) / s.ck;
+  s.units = static_cast<long long>(s.pairs) * s.tiles;
+  s.order = sc.order;
+  s.pairing = sc.pairing;
+  s.kalt = sc.kalt;
+  s.band = sc.band_cols / kPairBM > 0 ? sc.band_cols / kPairBM : 1;
+  const long long pairs = s.units < clusters ? s.units : clusters;
+  gemm_f16_pair_kernel<<<static_cast<unsigned int>(2 * pairs), kThreads, kPairSmem, st>>>(mapA, mapB, pl, s, res,
+                                                                                          ldr, n, rcap, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int g_f16_group = 16;   // tile rasterisation group of grouped launches
+
+bool gemm_pair_supported() { return get_encoder() && pair_clusters() > 0; }
 
 // a_plane_rows: rows between consecutive planes of planesA (0: m), so that a
 // block of rows of a larger plane set can be passed; rcap: residue rows stored
@@ -562,6 +909,9 @@ cudaError_t launch_gemm_f16(int64_t m, int64_t n, int64_t kpad, const Plan& pl, 
   if ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u)
     return cudaErrorInvalidValue;
   if (!get_encoder()) return cudaErrorNotSupported;
+  if (sc.cta_pair)
+    return launch_pair(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm, a_plane_rows,
+                       rcap, sc);
   switch (tile_n) {
     case 64:
       return launch_single<64>(m, n, kpad, pl, planesA, planesB, res, ldr, chunk_k, group, status, st, ppm,

@@ -26,8 +26,8 @@ namespace {
 using Key = std::tuple<int, int, int, int, int>;
 
 // cache lines: tag, dtype, N, the three log2 buckets, then tile_n group chunk_k
-// crt_rows split_elems order pairing kdir band crt_engine
-constexpr const char* kCacheTag = "gemm2";
+// crt_rows split_elems order pairing kdir band crt_engine cta_pair
+constexpr const char* kCacheTag = "gemm3";
 
 std::mutex g_mu;
 Tune g_default;
@@ -58,6 +58,7 @@ bool valid(int key, int v) {
     case EMU_TUNE_KDIR: return v == 0 || v == 1;
     case EMU_TUNE_BAND: return v >= 128 && v <= 65536 && v % 128 == 0;
     case EMU_TUNE_CRT_ENGINE: return v == 0 || v == 1;
+    case EMU_TUNE_CTA_PAIR: return v == 0 || v == 1;
     default: return false;
   }
 }
@@ -79,9 +80,9 @@ void load_locked() {
       }
       continue;
     }
-    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n, &t.group,
-                    &t.chunk_k, &t.crt_rows, &t.split_elems, &t.sched.order, &t.sched.pairing, &t.sched.kalt,
-                    &t.sched.band_cols, &t.crt_engine) != 15)
+    if (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", &s, &N, &bm, &bn, &bk, &t.tile_n,
+                    &t.group, &t.chunk_k, &t.crt_rows, &t.split_elems, &t.sched.order, &t.sched.pairing,
+                    &t.sched.kalt, &t.sched.band_cols, &t.crt_engine, &t.sched.cta_pair) != 16)
       break;
     // a stale or hand-edited entry with a value the launchers would refuse is skipped,
     // so the defaults stay in force for its bucket
@@ -112,9 +113,10 @@ void save_locked() {
   for (const auto& kv : g_table) {
     const Key& k = kv.first;
     const Tune& t = kv.second;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", kCacheTag, std::get<0>(k), std::get<1>(k),
-                 std::get<2>(k), std::get<3>(k), std::get<4>(k), t.tile_n, t.group, t.chunk_k, t.crt_rows,
-                 t.split_elems, t.sched.order, t.sched.pairing, t.sched.kalt, t.sched.band_cols, t.crt_engine);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", kCacheTag, std::get<0>(k),
+                 std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), t.tile_n, t.group, t.chunk_k,
+                 t.crt_rows, t.split_elems, t.sched.order, t.sched.pairing, t.sched.kalt, t.sched.band_cols,
+                 t.crt_engine, t.sched.cta_pair);
   }
   std::fclose(f);
 }
@@ -133,6 +135,7 @@ void set(Tune& t, int key, int v) {
     case EMU_TUNE_KDIR: t.sched.kalt = v; break;
     case EMU_TUNE_BAND: t.sched.band_cols = v; break;
     case EMU_TUNE_CRT_ENGINE: t.crt_engine = v; break;
+    case EMU_TUNE_CTA_PAIR: t.sched.cta_pair = v; break;
     default: break;
   }
 }
@@ -225,6 +228,7 @@ int emu_get_tuning(int key) {
     case EMU_TUNE_KDIR: return t.sched.kalt;
     case EMU_TUNE_BAND: return t.sched.band_cols;
     case EMU_TUNE_CRT_ENGINE: return t.crt_engine;
+    case EMU_TUNE_CTA_PAIR: return t.sched.cta_pair;
     default: return -1;
   }
 }
@@ -244,6 +248,7 @@ int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, 
     case EMU_TUNE_KDIR: return t.sched.kalt;
     case EMU_TUNE_BAND: return t.sched.band_cols;
     case EMU_TUNE_CRT_ENGINE: return t.crt_engine;
+    case EMU_TUNE_CTA_PAIR: return t.sched.cta_pair;
     default: return -1;
   }
 }
@@ -343,7 +348,7 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
         }
     // modulus-loop schedule of the residue products, one knob at a time from the best so far:
     // unit order (modulus outer; tile outer; column bands of the paper's 8192 columns and of 2048),
-    // then alternating k direction, then job pairing
+    // then alternating k direction, then job pairing, then SM-pair tiles
     GemmSchedule sc;
     auto time_sched = [&](const GemmSchedule& cand) {
       return time_min(st, a, b, reps, [&] {
@@ -384,6 +389,15 @@ emu_status_t emu_autotune_gemm(int dtype, int64_t m, int64_t n, int64_t k, int n
       if (real && pr == 2) continue;           // one job per modulus: the same as adjacent
       GemmSchedule c = sc;
       c.pairing = pr;
+      const float ms = time_sched(c);
+      if (ms < kKeep * bt) {
+        bt = ms;
+        sc = c;
+      }
+    }
+    if (ok && gemm_pair_supported()) {          // 256 x 256 tiles on SM pairs
+      GemmSchedule c = sc;
+      c.cta_pair = 1;
       const float ms = time_sched(c);
       if (ms < kKeep * bt) {
         bt = ms;

@@ -30,7 +30,7 @@ KNOBS = [(emu.EMU_TUNE_TILE_N, v) for v in (64, 128, 256)] + \
 
 @pytest.fixture(autouse=True)
 def _defaults():
-    saved = {k: emu.emu_get_tuning(k) for k in list(range(1, 6)) + list(range(8, 13))}
+    saved = {k: emu.emu_get_tuning(k) for k in list(range(1, 6)) + list(range(8, 14))}
     yield
     for k, v in saved.items():
         emu.emu_set_tuning(k, v)
@@ -90,9 +90,9 @@ def test_autotune_cache_file_round_trip(tmp_path):
     assert r.returncode == 0, r.stderr[-2000:]
     st, *best = map(int, r.stdout.split())
     assert st == 0
-    lines = [l.split() for l in cache.read_text().splitlines() if l.startswith("gemm2 ")]
+    lines = [l.split() for l in cache.read_text().splitlines() if l.startswith("gemm3 ")]
     assert len(lines) == 1 and list(map(int, lines[0][6:11])) == best
-    assert len(lines[0]) == 16
+    assert len(lines[0]) == 17
 
 
 # modulus-loop schedules of the residue products: (order, pairing, kdir, band columns, chunk_k)
@@ -147,7 +147,8 @@ def test_schedule_bitexact_real_and_single(order, pairing, kdir):
 
 def test_invalid_schedule_knobs_rejected():
     for key, value in ((emu.EMU_TUNE_ORDER, 3), (emu.EMU_TUNE_PAIRING, -1), (emu.EMU_TUNE_KDIR, 2),
-                       (emu.EMU_TUNE_BAND, 100), (emu.EMU_TUNE_BAND, 0)):
+                       (emu.EMU_TUNE_BAND, 100), (emu.EMU_TUNE_BAND, 0), (emu.EMU_TUNE_CTA_PAIR, 2),
+                       (emu.EMU_TUNE_CTA_PAIR, -1)):
         assert emu.emu_set_tuning(key, value) == emu.EMU_ERR_INVALID_ARG
 
 
@@ -158,7 +159,7 @@ def test_autotuned_schedule_valid_reported_and_used():
     got_sched = {nm: emu.emu_tuned_value(emu.EMU_DTYPE_Z, N, m, n, k, key)
                  for nm, key in emu.SCHEDULE_KNOBS.items()}
     assert got_sched["order"] in (0, 1, 2) and got_sched["pairing"] in (0, 1, 2) and got_sched["kdir"] in (0, 1)
-    assert got_sched["band"] % 128 == 0
+    assert got_sched["band"] % 128 == 0 and got_sched["cta_pair"] in (0, 1)
     assert emu.emu_tuned_value(emu.EMU_DTYPE_Z, N, m, n, k, emu.EMU_TUNE_TILE_N) == best[0]
     assert emu.emu_tuned_value(emu.EMU_DTYPE_Z, N, m, n, k, 99) == -1
     A = paper_matrix(m, k, 1.0, 47)
@@ -175,8 +176,8 @@ def test_autotune_cache_skips_invalid_entries(tmp_path):
     of that bucket runs with the defaults and succeeds."""
     cache = tmp_path / "tune.txt"
     # dtype 0 (Z), N 12, buckets of m = 300, n = 200, k = 500 -> 9, 8, 9; chunk_k 1000 is invalid
-    cache.write_text("gemm2 0 12 9 8 9 256 16 1000 4 4 0 0 0 8192 1\n"
-                     "gemm 0 12 9 8 9 256 16 960 4 4\n")
+    cache.write_text("gemm3 0 12 9 8 9 256 16 1000 4 4 0 0 0 8192 1 0\n"
+                     "gemm2 0 12 9 8 9 256 16 960 4 4 0 0 0 8192 1\n")
     code = ("import sys; sys.path.insert(0, %r)\n"
             "import numpy as np, torch\n"
             "from paper_2512_08321_gb300 import emu\n"
@@ -193,3 +194,47 @@ def test_autotune_cache_skips_invalid_entries(tmp_path):
     same, chunk = map(int, r.stdout.split())
     assert same == 1 and chunk == 960
     assert "ignoring invalid autotune cache entry" in r.stderr
+
+
+# SM-pair tiles (256 x 256 on a cluster of two CTAs): the schedules above, then
+# shapes whose second CTA of a pair holds only padding (m or n <= 128)
+PAIR_SCHEDULES = [(0, 0, 0, 8192, 960), (1, 1, 1, 8192, 64), (2, 2, 1, 384, 960), (0, 2, 0, 8192, 512)]
+
+
+@pytest.mark.parametrize("order,pairing,kdir,band,chunk", PAIR_SCHEDULES)
+def test_pair_schedule_bitexact(order, pairing, kdir, band, chunk):
+    A, B, N, ref = _schedule_case()
+    _set_schedule(order, pairing, kdir, band, chunk)
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_CTA_PAIR, 1), "cta pair")
+    got = run_gemm(A, B, N, opB="T")
+    assert same_bits(got, ref), mismatch_report(got, ref)
+
+
+@pytest.mark.parametrize("m,n,k", [(100, 300, 200), (300, 90, 130), (257, 129, 64), (1, 1, 1)])
+def test_pair_edges_bitexact(m, n, k):
+    N = 14
+    A = paper_matrix(m, k, 1.0, 50 + m)
+    B = paper_matrix(k, n, 1.0, 51 + n)
+    ref = emulate(A, B, N, keep_residue_planes=False)
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_CTA_PAIR, 1), "cta pair")
+    got = run_gemm(A, B, N)
+    assert same_bits(got, ref.out), mismatch_report(got, ref.out)
+
+
+def test_pair_real_and_single_bitexact():
+    from oracle.emulate_real import emulate_real
+    from paper_2512_08321_gb300.workloads import paper_matrix_real
+    from .helpers import run_real
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_CTA_PAIR, 1), "cta pair")
+    m, n, k, N = 530, 610, 1000, 15
+    A = paper_matrix_real(m, k, 1.0, 53)
+    B = paper_matrix_real(k, n, 1.0, 54)
+    ref = emulate_real(A, B, N)
+    got = run_real(A, B, N)
+    assert same_bits(got, ref.out), mismatch_report(got, ref.out)
+    Ac = paper_matrix(m, k, 0.5, 55, np.complex64)
+    Bc = paper_matrix(k, n, 0.5, 56, np.complex64)
+    refc = emulate(Ac.astype(np.complex128), Bc.astype(np.complex128), 8, out_fmt=fp.BINARY32,
+                   keep_residue_planes=False)
+    assert same_bits(run_gemm(Ac, Bc, 8, single=True), refc.out)
+    assert emu.emu_stream_status() == emu.EMU_OK
