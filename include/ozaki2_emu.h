@@ -354,6 +354,11 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *                        device without cluster launch support refuses 1 at
  *                        call time (EMU_ERR_CUDA).  Grouped calls always use
  *                        one-SM tiles
+ *   EMU_TUNE_BOUND_PAIR  accurate-mode bound products: 1 (default) tiles of 256
+ *                        output columns x 128 rows on pairs of SMs
+ *                        (cta_group::2; one-SM tiles on a device that cannot
+ *                        run them), 0 128 x 128 tiles on one SM; a process
+ *                        setting only, never autotuned
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
  * separately), and later calls whose (dtype, N, ceil(log2) of m, n, k) match
@@ -380,6 +385,7 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
 #define EMU_TUNE_BAND 11
 #define EMU_TUNE_CRT_ENGINE 12
 #define EMU_TUNE_CTA_PAIR 13
+#define EMU_TUNE_BOUND_PAIR 14
 emu_status_t emu_set_tuning(int key, int value);
 int emu_get_tuning(int key);
 int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, int key);

@@ -414,7 +414,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
           launch_bound_split(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, L.kpad, pb, st) !=
               cudaSuccess)
         return EMU_ERR_CUDA;
-      e = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ds->status, st);
+      e = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ds->status, st, tn.bound_pair == 1);
       if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
       if (e != cudaSuccess) return EMU_ERR_CUDA;
     }

@@ -93,7 +93,7 @@ cudaError_t launch_bound_split(bool single, bool real, const void* X, int64_t ro
                                cudaStream_t st);
 cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, const void* planesA,
                               const void* planesB, unsigned int* Mrow, unsigned int* Ncol, unsigned int* status,
-                              cudaStream_t st);
+                              cudaStream_t st, bool pair = false);
 cudaError_t launch_accu_finalize(int64_t rows, const int* emax, const unsigned int* flag, const unsigned int* Mb,
                                  const Plan& pl, int16_t* xout, cudaStream_t st);
 
@@ -125,6 +125,8 @@ struct Tune {
   int overlap = -1;      // split and CRT of neighbouring column blocks beside the residue products:
                          // 1 on, 0 off, -1 (default) on for the real GEMMs only
   GemmSchedule sched;    // residue products: modulus-loop schedule
+  int bound_pair = 1;    // accurate-mode bound products: 1 on SM pairs (cta_group::2) where the device
+                         // can run them, 0 on one SM
 };
 
 // Tuning of a call of this shape: the autotuned entry of its (dtype, N, shape

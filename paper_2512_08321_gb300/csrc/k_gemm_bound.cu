@@ -23,11 +23,26 @@ namespace {
 // across the warp) and the column maxima over rows of max(C-bar_R, C-bar_I) go
 // to global memory by atomicMax.  Rows/columns beyond m/n read TMA's zero
 // fill, so they add nothing.
-constexpr int kBoundBN = 128;
+constexpr int kBoundBN = 128;          // output rows per tile (MMA N)
 constexpr int kBoundChunk = 32;
-constexpr int kBoundStages = 6;        // 32 KB stages
-constexpr int kBoundSmem = kBoundStages * Cfg<kBoundBN>::kStageBytes + 1024 + 256;
 constexpr int kBoundTmemCols = 512;    // 2 slots x (128 FP32 + 128 int32) columns
+
+// One-SM tiles: 128 output columns x 128 rows, 6 stages of 32 KB.  SM pairs
+// (cta_group::2, a cluster of two CTAs): 256 columns x 128 rows, each CTA
+// holding 128 of the columns in its TMEM and loading 64 of the A-bar rows, so
+// a stage is 24 KB and 8 of them fit; the even CTA issues the MMAs (M = 256).
+// Measured at ZGEMM 16384^3, N = 15 in accurate mode: the exponent phase took
+// 26.8-27.3 ms on pairs against 27.7-28.2 on one SM, so pairs are the default.
+template <bool PAIR>
+struct BoundCfg {
+  static constexpr int kRowsB = PAIR ? kBoundBN / 2 : kBoundBN;      // A-bar rows per CTA and stage
+  static constexpr int kStageBytes = kStageA + kRowsB * BK * 2;
+  static constexpr int kStages = PAIR ? 8 : 6;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr int kTileCols = PAIR ? 2 * BM : BM;
+  static constexpr uint32_t kIdesc = (1u << 4) | (static_cast<uint32_t>(kBoundBN >> 3) << 17) |
+                                     (static_cast<uint32_t>(kTileCols >> 4) << 24);
+};
 
 struct BoundSched {
   int TJ, TI, tiles, group, nkb, real;
@@ -41,25 +56,25 @@ __device__ __forceinline__ void bound_src(int slot, int kb, int nkb, bool real, 
   else { pa = 1; pb = 0; kc = kb - nkb; }           // B-bar_I x A-bar_R
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_bound_kernel(const __grid_constant__ CUtensorMap mapA,   // B-bar planes: MMA operand A
-                      const __grid_constant__ CUtensorMap mapB,   // A-bar planes: MMA operand B
-                      const BoundSched s, unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
-                      int64_t m, int64_t n, unsigned int* status) {
+template <bool PAIR>
+__device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtensorMap* mapB, const BoundSched& s,
+                                           unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
+                                           int64_t m, int64_t n, unsigned int* status) {
+  using BC = BoundCfg<PAIR>;
   constexpr int BN = kBoundBN;
-  using C = Cfg<BN>;
+  constexpr int S = BC::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kBoundStages * C::kStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + S * BC::kStageBytes);
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int i) { return bar0 + 8u * i; };
-  auto empty = [&](int i) { return bar0 + 8u * (kBoundStages + i); };
-  auto tfull = [&](int i) { return bar0 + 8u * (2 * kBoundStages + i); };
-  auto tempty = [&](int i) { return bar0 + 8u * (2 * kBoundStages + 2 + i); };
-  const uint32_t done = bar0 + 8u * (2 * kBoundStages + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kBoundStages + 5);
+  auto empty = [&](int i) { return bar0 + 8u * (S + i); };
+  auto tfull = [&](int i) { return bar0 + 8u * (2 * S + i); };
+  auto tempty = [&](int i) { return bar0 + 8u * (2 * S + 2 + i); };
+  const uint32_t done = bar0 + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -68,36 +83,52 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int len0 = real ? s.nkb : 2 * s.nkb, len1 = real ? 0 : s.nkb;
   const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk;   // len1 <= len0: slot 1 has no more chunks
   const long long nunits = s.tiles;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const long long first = PAIR ? (blockIdx.x >> 1) : blockIdx.x;
+  const long long step = PAIR ? (gridDim.x >> 1) : gridDim.x;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kBoundStages; ++i) {
+    for (int i = 0; i < S; ++i) {
       mbar_init(full(i), 1);
       mbar_init(empty(i), 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(tfull(i), 1);
-      mbar_init(tempty(i), 32 * kEpiWarps);
+      mbar_init(tempty(i), (PAIR ? 2 : 1) * 32 * kEpiWarps);
     }
     mbar_init(done, 1);
     *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kBoundTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                   "r"(kBoundTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                   "r"(kBoundTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) cluster_sync(); else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // the even CTA's barriers (the pair's loads count on its full barriers, both epilogues free its slots)
+  const uint32_t full_c0 = PAIR ? map_to_rank(full(0), 0) : full(0);
+  const uint32_t tempty_c0 = PAIR ? map_to_rank(tempty(0), 0) : tempty(0);
+  auto wait_x = [&](uint32_t bar, uint32_t parity) {     // waits on barriers the other CTA arrives on
+    return PAIR ? mbar_wait_cluster(bar, parity, ctl) : mbar_wait(bar, parity, ctl);
+  };
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       long long it = 0;
       bool ok = true;
-      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      for (long long u = first; ok && u < nunits; u += step) {
         int tj, ti;
         tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
         for (int c = 0; ok && c < nch0; ++c) {
@@ -106,64 +137,80 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (c * kBoundChunk >= len) continue;
             const int kb1 = min(len, (c + 1) * kBoundChunk);
             for (int kb = c * kBoundChunk; kb < kb1; ++kb, ++it) {
-              const int st = static_cast<int>(it % kBoundStages);
-              const uint32_t ph = static_cast<uint32_t>((it / kBoundStages) & 1);
+              const int st = static_cast<int>(it % S);
+              const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
               int pa, pb, kc;
               bound_src(slot, kb, s.nkb, real, pa, pb, kc);
-              const uint32_t sa = base + st * C::kStageBytes;
-              mbar_expect_tx(full(st), C::kStageBytes);
-              tma_load_3d(sa, &mapA, full(st), kc * BK, tj * BM, pa);
-              tma_load_3d(sa + kStageA, &mapB, full(st), kc * BK, ti * BN, pb);
+              const uint32_t sa = base + st * BC::kStageBytes;
+              if constexpr (PAIR) {
+                if (leader) mbar_expect_tx(full(st), static_cast<uint32_t>(2 * BC::kStageBytes));
+                const uint32_t fb = full_c0 + 8u * st;
+                tma_load_3d_pair(sa, mapA, fb, kc * BK, tj * BC::kTileCols + static_cast<int>(rank) * BM, pa);
+                tma_load_3d_pair(sa + kStageA, mapB, fb, kc * BK, ti * BN + static_cast<int>(rank) * BC::kRowsB, pb);
+              } else {
+                mbar_expect_tx(full(st), BC::kStageBytes);
+                tma_load_3d(sa, mapA, full(st), kc * BK, tj * BM, pa);
+                tma_load_3d(sa + kStageA, mapB, full(st), kc * BK, ti * BN, pb);
+              }
             }
           }
         }
       }
-      for (int st = 0; st < kBoundStages; ++st) {
-        if (it <= st) continue;
-        const long long last = st + ((it - 1 - st) / kBoundStages) * kBoundStages;
-        const uint32_t ph = static_cast<uint32_t>((last / kBoundStages) & 1);
-        const long long t0 = clock64();
-        while (!mbar_try(full(st), ph) && clock64() - t0 < kWaitLimit) {
+      // drain: every load issued has landed (for a pair, the even CTA's barriers count both CTAs' loads)
+      if (leader) {
+        for (int st = 0; st < S; ++st) {
+          if (it <= st) continue;
+          const long long last = st + ((it - 1 - st) / S) * S;
+          const uint32_t ph = static_cast<uint32_t>((last / S) & 1);
+          const long long t0 = clock64();
+          while (!(PAIR ? mbar_try_cluster(full(st), ph) : mbar_try(full(st), ph)) && clock64() - t0 < kWaitLimit) {
+          }
         }
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (for a pair: the even CTA)
+    if (lane == 0 && leader) {
       long long it = 0;
       int used[2] = {0, 0};
       bool ok = true;
-      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      for (long long u = first; ok && u < nunits; u += step) {
         for (int c = 0; ok && c < nch0; ++c) {
           for (int slot = 0; ok && slot < 2; ++slot) {
             const int len = slot ? len1 : len0;
             if (c * kBoundChunk >= len) continue;
-            if (!mbar_wait(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u, ctl)) { ok = false; break; }
+            if (!wait_x(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u)) { ok = false; break; }
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
             const int kb0 = c * kBoundChunk, kb1 = min(len, (c + 1) * kBoundChunk);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
-              const int st = static_cast<int>(it % kBoundStages);
-              const uint32_t ph = static_cast<uint32_t>((it / kBoundStages) & 1);
-              if (!mbar_wait(full(st), ph, ctl)) { ok = false; break; }
+              const int st = static_cast<int>(it % S);
+              const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+              if (!wait_x(full(st), ph)) { ok = false; break; }
               tc_fence_after();
-              const uint32_t sa = base + st * C::kStageBytes;
+              const uint32_t sa = base + st * BC::kStageBytes;
               const uint64_t da = smem_desc(sa), db = smem_desc(sa + kStageA);
 #pragma unroll
               for (int kk = 0; kk < BK / UK; ++kk) {
                 const uint64_t off = static_cast<uint64_t>((kk * UK * 2) >> 4);
-                mma_f16(td, da + off, db + off, C::kIdesc, !(kb == kb0 && kk == 0));   // fresh sum per chunk
+                if constexpr (PAIR) mma_f16_pair(td, da + off, db + off, BC::kIdesc, !(kb == kb0 && kk == 0));
+                else mma_f16(td, da + off, db + off, BC::kIdesc, !(kb == kb0 && kk == 0));   // fresh sum per chunk
               }
-              mma_commit(empty(st));
+              if constexpr (PAIR) mma_commit_pair(empty(st)); else mma_commit(empty(st));
             }
             if (!ok) break;
-            mma_commit(tfull(slot));
+            if constexpr (PAIR) mma_commit_pair(tfull(slot)); else mma_commit(tfull(slot));
             ++used[slot];
           }
         }
       }
-      mma_commit(done);
+      if constexpr (PAIR) mma_commit_pair(done); else mma_commit(done);
+      const long long t0 = clock64();
+      while (!mbar_try(done, 0u) && clock64() - t0 < kWaitLimit) {
+      }
+    } else if (PAIR && lane == 0) {
+      // the odd CTA: the even CTA's last commit arrives here once every MMA touching this CTA is done
       const long long t0 = clock64();
       while (!mbar_try(done, 0u) && clock64() - t0 < kWaitLimit) {
       }
@@ -180,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     int used[2] = {0, 0};
     bool ok = true;
-    for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+    for (long long u = first; ok && u < nunits; u += step) {
       int tj, ti;
       tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
       for (int c = 0; ok && c < nch0; ++c) {
@@ -204,13 +251,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tmem_wait_st();
           tc_fence_before();
-          mbar_arrive(tempty(slot));
+          if constexpr (PAIR) mbar_arrive_cluster(tempty_c0 + 8u * slot); else mbar_arrive(tempty(slot));
           ++used[slot];
         }
       }
       if (!ok) break;
       // max(C-bar_R, C-bar_I) per (row, this column); rows of this thread: 64 half + 32 piece + q
-      const int64_t col = static_cast<int64_t>(tj) * BM + quad * 32 + lane;
+      const int64_t col = static_cast<int64_t>(tj) * BC::kTileCols + static_cast<int64_t>(rank) * BM + quad * 32 + lane;
       unsigned int colmax = 0u;
 #pragma unroll 1
       for (int piece = 0; piece < 2; ++piece) {
@@ -245,37 +292,82 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) cluster_sync(); else __syncthreads();   // a pair: no CTA leaves while the MMAs touch it
   tc_fence_after();
-  if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBoundTmemCols));
+  if (warp == 1) {
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBoundTmemCols));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kBoundTmemCols));
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bound_kernel(const __grid_constant__ CUtensorMap mapA,   // B-bar planes: MMA operand A
+                      const __grid_constant__ CUtensorMap mapB,   // A-bar planes: MMA operand B
+                      const BoundSched s, unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
+                      int64_t m, int64_t n, unsigned int* status) {
+  bound_body<false>(&mapA, &mapB, s, Mrow, Ncol, m, n, status);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    gemm_bound_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                           const BoundSched s, unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
+                           int64_t m, int64_t n, unsigned int* status) {
+  bound_body<true>(&mapA, &mapB, s, Mrow, Ncol, m, n, status);
 }
 
 }  // namespace
 
 cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, const void* planesA,
                               const void* planesB, unsigned int* Mrow, unsigned int* Ncol, unsigned int* status,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool pair) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (kpad % BK || ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u))
     return cudaErrorInvalidValue;
   if (!get_encoder()) return cudaErrorNotSupported;
-  static cudaError_t attr =
-      cudaFuncSetAttribute(gemm_bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoundSmem);
+  static const cudaError_t attr = [] {
+    cudaError_t e = cudaFuncSetAttribute(gemm_bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BoundCfg<false>::kSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_bound_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               BoundCfg<true>::kSmem);
+    return e;
+  }();
   if (attr != cudaSuccess) return attr;
+  // SM pairs that can run a CTA pair of the pair kernel at once (0: none)
+  static const int clusters = [] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 1024);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = BoundCfg<true>::kSmem;
+    int v = 0;
+    if (cudaOccupancyMaxActiveClusters(&v, gemm_bound_pair_kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    return v;
+  }();
+  if (clusters <= 0) pair = false;          // no room for a CTA pair: one-SM tiles
   const int planes = real ? 1 : 3;
+  const int cols = pair ? BoundCfg<true>::kTileCols : BM;
   CUtensorMap mapA, mapB;
   if (!make_map(&mapA, planesB, n, kpad, planes, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&mapB, planesA, m, kpad, planes, kBoundBN)) return cudaErrorInvalidValue;
+  if (!make_map(&mapB, planesA, m, kpad, planes, pair ? BoundCfg<true>::kRowsB : kBoundBN)) return cudaErrorInvalidValue;
   BoundSched s;
-  s.TJ = static_cast<int>((n + BM - 1) / BM);
+  s.TJ = static_cast<int>((n + cols - 1) / cols);
   s.TI = static_cast<int>((m + kBoundBN - 1) / kBoundBN);
   s.tiles = s.TJ * s.TI;
-  s.group = 16;
+  s.group = pair ? 8 : 16;                 // the same column span (2048) in a raster group
   s.nkb = static_cast<int>(kpad / BK);
   s.real = real ? 1 : 0;
-  const int grid = s.tiles < g_sms ? s.tiles : g_sms;
-  gemm_bound_kernel<<<grid, kThreads, kBoundSmem, st>>>(mapA, mapB, s, Mrow, Ncol, m, n, status);
+  if (pair) {
+    const int p = s.tiles < clusters ? s.tiles : clusters;
+    gemm_bound_pair_kernel<<<2 * p, kThreads, BoundCfg<true>::kSmem, st>>>(mapA, mapB, s, Mrow, Ncol, m, n, status);
+  } else {
+    const int grid = s.tiles < g_sms ? s.tiles : g_sms;
+    gemm_bound_kernel<<<grid, kThreads, BoundCfg<false>::kSmem, st>>>(mapA, mapB, s, Mrow, Ncol, m, n, status);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

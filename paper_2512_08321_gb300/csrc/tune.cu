@@ -4,8 +4,8 @@
 // own): the residue-product tile width, rasterisation group and reduction
 // chunk, then the modulus-loop schedule of those products (unit order, among
 // them the paper's n-blocked order of Section III-A; k direction; job
-// pairing), searched one knob at a time from the best so far; the CRT rows per
-// thread; the split entries per thread.  A candidate replaces the incumbent
+// pairing; tiles on SM pairs), searched one knob at a time from the best so
+// far; the CRT engine and rows per thread; the split entries per thread.  A candidate replaces the incumbent
 // only when it is at least 0.5 % faster, so timing noise does not move the
 // choice.  The winners are kept per (dtype, N, ceil(log2) of m, n, k) and used
 // by later calls in that bucket; EMU_AUTOTUNE_CACHE names a file that keeps
@@ -59,6 +59,7 @@ bool valid(int key, int v) {
     case EMU_TUNE_BAND: return v >= 128 && v <= 65536 && v % 128 == 0;
     case EMU_TUNE_CRT_ENGINE: return v == 0 || v == 1;
     case EMU_TUNE_CTA_PAIR: return v == 0 || v == 1;
+    case EMU_TUNE_BOUND_PAIR: return v == 0 || v == 1;
     default: return false;
   }
 }
@@ -136,6 +137,7 @@ void set(Tune& t, int key, int v) {
     case EMU_TUNE_BAND: t.sched.band_cols = v; break;
     case EMU_TUNE_CRT_ENGINE: t.crt_engine = v; break;
     case EMU_TUNE_CTA_PAIR: t.sched.cta_pair = v; break;
+    case EMU_TUNE_BOUND_PAIR: t.bound_pair = v; break;
     default: break;
   }
 }
@@ -192,8 +194,9 @@ Tune tune_for(int dtype, int N, int64_t m, int64_t n, int64_t k) {
   auto it = g_table.find(key_of(dtype, N, m, n, k));
   if (it == g_table.end()) return g_default;
   Tune t = it->second;
-  t.nblock = g_default.nblock;          // column blocking and overlap are process settings, not tuned
-  t.overlap = g_default.overlap;
+  t.nblock = g_default.nblock;          // column blocking, overlap and the bound products' tiles
+  t.overlap = g_default.overlap;        // are process settings, not tuned
+  t.bound_pair = g_default.bound_pair;
   return t;
 }
 
@@ -229,6 +232,7 @@ int emu_get_tuning(int key) {
     case EMU_TUNE_BAND: return t.sched.band_cols;
     case EMU_TUNE_CRT_ENGINE: return t.crt_engine;
     case EMU_TUNE_CTA_PAIR: return t.sched.cta_pair;
+    case EMU_TUNE_BOUND_PAIR: return t.bound_pair;
     default: return -1;
   }
 }
@@ -249,6 +253,7 @@ int emu_tuned_value(int dtype, int num_moduli, int64_t m, int64_t n, int64_t k, 
     case EMU_TUNE_BAND: return t.sched.band_cols;
     case EMU_TUNE_CRT_ENGINE: return t.crt_engine;
     case EMU_TUNE_CTA_PAIR: return t.sched.cta_pair;
+    case EMU_TUNE_BOUND_PAIR: return t.bound_pair;
     default: return -1;
   }
 }

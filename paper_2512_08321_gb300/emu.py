@@ -386,6 +386,7 @@ EMU_TUNE_OVERLAP = 7
 EMU_TUNE_ORDER, EMU_TUNE_PAIRING, EMU_TUNE_KDIR, EMU_TUNE_BAND = 8, 9, 10, 11
 EMU_TUNE_CRT_ENGINE = 12
 EMU_TUNE_CTA_PAIR = 13
+EMU_TUNE_BOUND_PAIR = 14
 SCHEDULE_KNOBS = {"order": EMU_TUNE_ORDER, "pairing": EMU_TUNE_PAIRING, "kdir": EMU_TUNE_KDIR,
                   "band": EMU_TUNE_BAND, "cta_pair": EMU_TUNE_CTA_PAIR}
 

@@ -25,6 +25,7 @@ def _accurate():
     emu.emu_set_scaling(emu.EMU_SCALING_FAST)
     emu.emu_set_crt_mode(emu.EMU_CRT_EXACT)
     emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 0)
+    emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, 0)
 
 
 def _cplx(m, n, k, opA, opB, phi, seed, single):
@@ -176,3 +177,32 @@ def test_accuracy_gain_over_fast_at_same_N():
     # the tighter bound keeps about half a bit more on average here (k = 2000, phi = 2)
     assert accu.mean() < fast.mean() / 1.2, (accu.mean(), fast.mean())
     assert accu[more].max() < fast[more].max(), (accu[more].max(), fast[more].max())
+
+
+@pytest.mark.parametrize("case", ["complex", "real", "single", "chunks", "edges", "one"])
+def test_bound_products_on_sm_pairs(case):
+    """The bound products on SM pairs (256-column tiles, each CTA of a pair
+    holding 128 of them and loading half of the 128 rows): the same exponents
+    and results, including column counts that leave the odd CTA only padding."""
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, 1), "bound pair")
+    if case == "real":
+        A, B = _real(300, 520, 333, "N", "T", 2.0, 94, False)
+        ref = RealEmulation(A, apply_op_real(B, "T"), 14, scaling="accurate").out
+        got = run_real(A, B, 14, "N", "T")
+    elif case == "single":
+        A, B = _cplx(257, 300, 200, "N", "N", 1.0, 96, True)
+        ref = Emulation(A.astype(np.complex128), B.astype(np.complex128), 7, scaling="accurate",
+                        out_fmt=fp.BINARY32, keep_residue_planes=False).out
+        got = run_gemm(A, B, 7, single=True)
+    else:
+        m, n, k = {"complex": (300, 600, 333), "chunks": (70, 150, 5000), "edges": (129, 100, 64),
+                   "one": (1, 1, 1)}[case]
+        A, B = _cplx(m, n, k, "N", "N", 2.0, 98, False)
+        if case == "edges":
+            A[3] = 0.0
+            A[5, 7] = complex(np.inf, 0.0)
+            B[9, 4] = complex(0.0, np.nan)
+        ref = Emulation(A, B, 13, scaling="accurate", keep_residue_planes=False).out
+        got = run_gemm(A, B, 13)
+    assert same_bits(got, ref), mismatch_report(got, ref)
+    assert emu.emu_stream_status() == emu.EMU_OK
