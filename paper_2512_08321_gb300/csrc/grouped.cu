@@ -22,7 +22,7 @@ struct emu_grouped_s {
   int count = 0;
   const emu::Plan* pl = nullptr;
   int tile_n = 256;
-  int chunk_k = 512;
+  int chunk_k = 960;                // k between in-TMEM reductions (the largest exact one)
   char* mem = nullptr;            // workspace + descriptor tables
   size_t mem_bytes = 0;
   size_t scratch_off = 0, scratch_bytes = 0;
