@@ -334,14 +334,18 @@ __device__ __forceinline__ void tc_epilogue(const Q& q, const TcPos& t, uint32_t
   }
 }
 
-// The block's items are pipelined two deep: item n is converted into operand
-// A (once item n - 1's MMA has read it) and its MMA issued into accumulator
-// slot n & 1, then item n - 1's outputs are finished from the other slot while
-// that MMA runs; item n + 1's bytes are copied in meanwhile (each thread
-// stages and converts the same chunks, so one staging buffer suffices).  One
-// A buffer keeps a block's shared memory small enough for as many blocks per
-// SM as the TMEM columns allow.
-template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST, class Work>
+// The block's items are pipelined two deep: item n is converted into an A
+// buffer and its MMA issued into accumulator slot n & 1, then item n - 1's
+// outputs are finished from the other slot while that MMA runs; item n + 1's
+// bytes are copied in meanwhile (each thread stages and converts the same
+// chunks, so one staging buffer suffices).  NBUF = 2: A buffer n & 1, and item
+// n - 1's MMA is waited for after item n's is issued.  NBUF = 1: one A buffer,
+// written once item n - 1's MMA has read it (issued a whole epilogue earlier,
+// so this seldom waits); the smaller block fits as many blocks per SM as the
+// TMEM columns allow.  Measured: single launches (ZGEMM 4096^3, N = 14) ran
+// 5 % more instructions with one buffer at the same 6 blocks, grouped launches
+// (N = 16) gained from 5 to 8 blocks; so single launches take 2, grouped 1.
+template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST, int NBUF, class Work>
 __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsigned int* status) {
   using LY = TcLayout<REAL, WIDE>;
   constexpr int kNC = LY::kNC;
@@ -350,8 +354,8 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
   const int a_bytes = KT * 4096;
   extern __shared__ __align__(128) uint8_t tc_smem[];
   uint8_t* sB = tc_smem;                                  // KT x kBTileBytes
-  uint8_t* sA = sB + KT * LY::kBTileBytes;                // KT x 4096
-  uint8_t* sS = sA + a_bytes;                             // J x kStageRow
+  uint8_t* sA = sB + KT * LY::kBTileBytes;                // NBUF x KT x 4096
+  uint8_t* sS = sA + NBUF * a_bytes;                      // J x kStageRow
   const int stage_bytes = (J * kStageRow + 127) / 128 * 128;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sS + stage_bytes);   // MMA done, per slot
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -388,10 +392,10 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
     }
     *reinterpret_cast<__half*>(sB + b_off<kNC>(n, k)) = __float2half_rn(val);
   }
-  // A's columns past the jobs: 2048 in the bias entry, zeros after it
-  for (int e = threadIdx.x; e < 128 * (KT * 16 - J); e += kTcThreads) {
-    const int m = e & 127, k = J + (e >> 7);
-    *reinterpret_cast<__half*>(sA + a_off(m, k)) = __float2half_rn(k == J ? 2048.0f : 0.0f);
+  // A's columns past the jobs, in every buffer: 2048 in the bias entry, zeros after it
+  for (int e = threadIdx.x; e < NBUF * 128 * (KT * 16 - J); e += kTcThreads) {
+    const int m = e & 127, k = J + ((e >> 7) % (KT * 16 - J)), b = (e >> 7) / (KT * 16 - J);
+    *reinterpret_cast<__half*>(sA + b * a_bytes + a_off(m, k)) = __float2half_rn(k == J ? 2048.0f : 0.0f);
   }
   tc_fence_before();
   __syncthreads();
@@ -416,19 +420,20 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
   auto step = [&](auto slot_c) -> bool {
     constexpr int SLOT = decltype(slot_c)::value;
     constexpr int PS = SLOT ^ 1;
+    constexpr int AB = NBUF == 1 ? 0 : SLOT;             // A buffer of `cur`
     TcPos next{0, -1, 0};
-    if (prev.j >= 0) {
-      // prev's MMA is done with operand A before A is overwritten (it was issued a whole
-      // epilogue ago, so this seldom waits).  An expired wait sets the abort flag (seen by
-      // every thread after the barrier below); the status word then reports the timeout.
+    // an expired wait sets the abort flag (seen by every thread after the next barrier);
+    // the status word then reports the timeout
+    auto wait_prev = [&]() {
       if (mbar_wait(bar0 + 8 * PS, (ph >> PS) & 1u, ctl)) {
         pending &= ~(1u << PS);
         ph ^= 1u << PS;
       }
-    }
+    };
+    if (NBUF == 1 && prev.j >= 0) wait_prev();             // prev's MMA has read the one A buffer
     if (cur.j >= 0) {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      convert_item(U, sS, sA);
+      convert_item(U, sS, sA + AB * a_bytes);
       // the next item's bytes: this thread's chunks only, which it has just converted
       W.advance(cursor, dj, dib);
       next = W.pos(cursor);
@@ -444,13 +449,17 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
     if (cur.j >= 0) {
       if (threadIdx.x == 0) {
         for (int kt = 0; kt < KT; ++kt)
-          mma_f16(tmem + SLOT * kNC, plain_desc(a0 + kt * 4096, 128, 256),
+          mma_f16(tmem + SLOT * kNC, plain_desc(a0 + AB * a_bytes + kt * 4096, 128, 256),
                   plain_desc(b0 + kt * LY::kBTileBytes, 128, 256), LY::kIdesc, kt > 0);
         mma_commit(bar0 + 8 * SLOT);
       }
       pending |= 1u << SLOT;
     }
     if (prev.j >= 0) {
+      if (NBUF == 2) {
+        wait_prev();
+        tc_fence_after();
+      }
       tc_epilogue<SINGLE, REAL, WIDE, L, ROBUST>(W.prob(prev.p), prev, tmem + PS * kNC, pl);
       tc_fence_before();
     }
@@ -478,52 +487,45 @@ __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsig
 }
 
 // Minimum resident blocks (which caps registers per thread): 8 blocks of 64
-// registers fill an SM (as many as its TMEM holds, and shared memory allows up
-// to N = 16).  The variants that would spill at 64 (one limb; two or three
-// real limbs) may use 80 registers; the 64-column ones (fewer blocks by TMEM)
-// about 100.
-template <bool REAL, bool WIDE, int L>
+// registers fill an SM (as many as its TMEM holds).  Single launches of four
+// complex limbs (N >= 13: three or more K tiles, two A buffers) fit 6 blocks
+// by shared memory, so they may use 80 registers, as may the ones that would
+// spill at 64 (one limb; two or three real limbs); grouped launches of four
+// limbs (one A buffer) fit 8; the 64-column ones (fewer blocks by TMEM) about 100.
+template <bool REAL, bool WIDE, int L, bool GROUPED = false>
 constexpr int tc_min_blocks() {
-  return WIDE ? 5 : ((L == 1 || (REAL && (L == 2 || L == 3))) ? 6 : 8);
+  return WIDE ? 5 : ((L == 1 || (REAL && (L == 2 || L == 3)) || (!GROUPED && !REAL && L == 4)) ? 6 : 8);
 }
 
 template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST>
 __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<REAL, WIDE, L>())) crt_tc_kernel(const TcSingle W, const __grid_constant__ Plan pl,
                                                             unsigned int* status) {
-  crt_tc_body<SINGLE, REAL, WIDE, L, ROBUST>(W, pl, status);
+  crt_tc_body<SINGLE, REAL, WIDE, L, ROBUST, 2>(W, pl, status);
 }
 
 template <bool SINGLE, bool WIDE, int L>
-__global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<false, WIDE, L>())) crt_tc_grouped_kernel(const TcGrouped W, const __grid_constant__ Plan pl,
+__global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<false, WIDE, L, true>())) crt_tc_grouped_kernel(const TcGrouped W, const __grid_constant__ Plan pl,
                                                                     unsigned int* status) {
-  crt_tc_body<SINGLE, false, WIDE, L, false>(W, pl, status);
+  crt_tc_body<SINGLE, false, WIDE, L, false, 1>(W, pl, status);
 }
 
-// Shared memory of one block: operand B, operand A, the staging buffer,
-// barriers; raised so that no more blocks fit on an SM than tc_blocks (at most
-// as many as its 512 TMEM columns hold: 2 x 32 or 2 x 64 columns a block).
-// GB300: 228 KB per SM, 1 KB of it reserved per resident block.
+// Shared memory of one block: operand B, the A buffers (2 for single
+// launches, 1 for grouped ones), the staging buffer, barriers; raised so that
+// no more blocks fit on an SM than its 512 TMEM columns hold (2 x 32 or 2 x 64
+// columns a block).  GB300: 228 KB per SM, 1 KB of it reserved per resident
+// block.
 constexpr int kSmemPerSM = 228 * 1024;
 
 int tc_max_blocks(bool real, bool wide) { return 512 / (2 * ((!real && wide) ? 64 : 32)); }
-
-// Blocks per SM: as many as TMEM holds, except single complex launches of
-// three or more K tiles (N >= 11), which keep 6: ZGEMM 16384^3 with N = 15
-// took 5.61 ms at 6 blocks and 5.70 at 8, while the grouped launch (N = 16,
-// problems of 64 to 2048 rows) went from 4.24 ms at 5 blocks to 3.90 at 8.
-int tc_blocks(bool real, bool wide, int N, bool grouped) {
-  const int tm = tc_max_blocks(real, wide);
-  const int KT = ((real ? 1 : 3) * N + 1 + 15) / 16;
-  return (!grouped && !real && KT >= 3 && tm > 6) ? 6 : tm;
-}
 
 size_t tc_smem_bytes(bool real, bool wide, int N, bool grouped) {
   const int J = (real ? 1 : 3) * N;
   const int KT = (J + 1 + 15) / 16;
   const int nc = (!real && wide) ? 64 : 32;
   const size_t stage = static_cast<size_t>((J * kStageRow + 127) / 128 * 128);
-  size_t need = static_cast<size_t>(KT) * (nc * 32 + 4096) + stage + 64;
-  const int maxb = tc_blocks(real, wide, N, grouped);
+  const int nbuf = grouped ? 1 : 2;                       // A buffers (crt_tc_body's NBUF)
+  size_t need = static_cast<size_t>(KT) * (nc * 32 + nbuf * 4096) + stage + 64;
+  const int maxb = tc_max_blocks(real, wide);
   const size_t floor_bytes = static_cast<size_t>(kSmemPerSM / (maxb + 1) - 1024 + 128);   // maxb + 1 blocks do not fit
   if (need < floor_bytes) need = floor_bytes;
   return (need + 127) / 128 * 128;
