@@ -228,7 +228,7 @@ struct GroupWork {
 // warps (8 or 16), EPI / 4 of them on each quarter of the TMEM lanes, each
 // taking 4 / EPI of a tile's columns (at least 32: with 64-wide tiles and 16
 // warps, half of them only wait and arrive).
-template <int BN, int EPI, class Work>
+template <int BN, int EPI, int RING, class Work>
 __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigned int* status, bool fence_maps) {
   using C = Cfg<BN>;
   constexpr int kParts = EPI / 4;                 // column parts of a tile
@@ -246,6 +246,12 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
   const uint32_t done = bar0 + 8u * (2 * kStages + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // unit ring (RING > 0): after the 256 bytes of barriers, ufull[RING], uempty[RING], then the units
+  uint64_t* rbars = reinterpret_cast<uint64_t*>(gbase + kStages * C::kStageBytes + 256);
+  const uint32_t rbar0 = smem_u32(rbars);
+  auto ufull = [&](int i) { return rbar0 + 8u * i; };
+  auto uempty = [&](int i) { return rbar0 + 8u * (RING + i); };
+  Unit* ring = reinterpret_cast<Unit*>(rbars + 2 * RING);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Ctl ctl{status, abort_s};
@@ -261,6 +267,10 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       mbar_init(tempty(i), 32 * EPI);
     }
     mbar_init(done, 1);
+    for (int i = 0; i < RING; ++i) {
+      mbar_init(ufull(i), 1);
+      mbar_init(uempty(i), 1 + EPI);                  // the MMA issuer and one lane per epilogue warp
+    }
     *abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -284,9 +294,17 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       // the next unit's descriptor is fetched while this one's loads are issued
       Unit nxt;
       if (blockIdx.x < nunits) nxt = W.get(blockIdx.x, hint);
-      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      long long t = 0;                                             // this CTA's unit count
+      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x, ++t) {
         const Unit U = nxt;
         if (u + gridDim.x < nunits) nxt = W.get(u + gridDim.x, hint);
+        if constexpr (RING > 0) {
+          // publish the unit to the MMA issuer and the epilogue warps
+          const int rs = static_cast<int>(t % RING);
+          if (!mbar_wait(uempty(rs), static_cast<uint32_t>((t / RING) & 1) ^ 1u, ctl)) { ok = false; break; }
+          ring[rs] = U;
+          mbar_arrive(ufull(rs));
+        }
         if (fence_maps && U.mapA != fenced) {
           // descriptors written by the host into global memory: acquire them for the TMA unit
           asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(U.mapA) : "memory");
@@ -328,12 +346,21 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       uint32_t used = 0u;                           // bit s: parity of slot s's uses so far
       bool ok = true;
       int hint = 0;
-      // the next unit's descriptor is fetched while this one's MMAs are issued
+      // the next unit's descriptor is fetched while this one's MMAs are issued (or read from the ring)
       Unit nxt;
-      if (blockIdx.x < nunits) nxt = W.get(blockIdx.x, hint);
-      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Unit U = nxt;
-        if (u + gridDim.x < nunits) nxt = W.get(u + gridDim.x, hint);
+      if (RING == 0 && blockIdx.x < nunits) nxt = W.get(blockIdx.x, hint);
+      long long t = 0;
+      for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x, ++t) {
+        Unit U;
+        if constexpr (RING > 0) {
+          const int rs = static_cast<int>(t % RING);
+          if (!mbar_wait(ufull(rs), static_cast<uint32_t>((t / RING) & 1), ctl)) { ok = false; break; }
+          U = ring[rs];
+          mbar_arrive(uempty(rs));
+        } else {
+          U = nxt;
+          if (u + gridDim.x < nunits) nxt = W.get(u + gridDim.x, hint);
+        }
         for (int c = 0; ok && c < U.nch; ++c) {
           for (int which = 0; ok && which < 2; ++which) {
             const int job = which ? U.jb : U.ja;
@@ -381,8 +408,18 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
     uint32_t used = 0u;                             // bit s: parity of slot s's uses so far
     bool ok = true;
     int hint = 0;
-    for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-      const Unit U = W.get(u, hint);
+    long long t = 0;
+    for (long long u = blockIdx.x; ok && u < nunits; u += gridDim.x, ++t) {
+      Unit U;
+      if constexpr (RING > 0) {
+        const int rs = static_cast<int>(t % RING);
+        if (!mbar_wait(ufull(rs), static_cast<uint32_t>((t / RING) & 1), ctl)) { ok = false; break; }
+        U = ring[rs];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(uempty(rs));
+      } else {
+        U = W.get(u, hint);
+      }
       const int64_t col = static_cast<int64_t>(U.tj) * BM + row_in_tile;
       // columns of this warp: [part * pw, part * pw + pw), pw >= 32; parts past the tile only wait
       const int pw = (U.bn / kParts) < 32 ? 32 : (U.bn / kParts);
@@ -469,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const __grid_constant__ Plan pl, const Sched s, int8_t* __restrict__ res, int64_t ldr,
                     int64_t n, int64_t rcap, unsigned int* status) {
   const SingleWork<BN> W{&mapA, &mapB, s, res, ldr, n, rcap};
-  gemm_body<BN, kEpiWarps>(W, pl, status, false);
+  gemm_body<BN, kEpiWarps, 0>(W, pl, status, false);
 }
 
 // ------------------------------------------------------------------ SM pairs
@@ -743,16 +780,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   pair_body(W, pl, status);
 }
 
-// Grouped launches: 256-row stages with each problem's own tile width, and 16
-// epilogue warps (short-k units are bound by their epilogue, not their MMAs).
+// Grouped launches: 256-row stages with each problem's own tile width, 16
+// epilogue warps (short-k units are bound by their epilogue, not their MMAs),
+// and a ring of unit descriptors in shared memory: the producer looks each
+// unit up in the problem table once, the MMA issuer and the epilogue warps
+// read it from the ring.
 constexpr int kGroupedEpi = 16;
 constexpr int kGroupedThreads = 32 * (2 + kGroupedEpi);
+constexpr int kGroupedRing = 8;
+static_assert(sizeof(Unit) % 8 == 0 && 2 * 8 * kGroupedRing + kGroupedRing * sizeof(Unit) <= 1024, "unit ring");
+constexpr int kGroupedSmem = Cfg<256>::kSmemBytes + 1024;
 
 __global__ void __launch_bounds__(kGroupedThreads, 1)
     gemm_f16_grouped_kernel(const GroupProblem* __restrict__ probs, int count, long long total,
                             const __grid_constant__ Plan pl, unsigned int* status) {
   const GroupWork W{probs, reinterpret_cast<const long long*>(probs + count), count, total};
-  gemm_body<256, kGroupedEpi>(W, pl, status, true);
+  gemm_body<256, kGroupedEpi, kGroupedRing>(W, pl, status, true);
 }
 
 // The largest shared-memory carveout: an SM holding one block of this kernel
@@ -774,7 +817,7 @@ cudaError_t set_smem_attrs() {
 cudaError_t set_grouped_attrs() {
   static cudaError_t err = [] {
     cudaError_t e = cudaFuncSetAttribute(gemm_f16_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<256>::kSmemBytes);
+                                         kGroupedSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gemm_f16_grouped_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                static_cast<int>(cudaSharedmemCarveoutMaxShared));
@@ -976,7 +1019,7 @@ cudaError_t launch_gemm_f16_grouped(const void* probs_dev, int count, long long 
   const long long grid = total_units < g_sms ? total_units : g_sms;
   const cudaError_t e = set_grouped_attrs();
   if (e != cudaSuccess) return e;
-  gemm_f16_grouped_kernel<<<static_cast<unsigned int>(grid), kGroupedThreads, Cfg<256>::kSmemBytes, st>>>(
+  gemm_f16_grouped_kernel<<<static_cast<unsigned int>(grid), kGroupedThreads, kGroupedSmem, st>>>(
       P, count, total_units, pl, status);
   count_launches(1);
   return cudaGetLastError();
