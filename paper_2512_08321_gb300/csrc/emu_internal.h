@@ -216,10 +216,12 @@ struct CrtProb {
 long long exp_seg_blocks(ExpSeg& s);       // sets hchunks, rows_contig; returns blocks
 long long split_seg_blocks(SplitSeg& s);   // sets htiles, rows_contig
 long long crt_prob_blocks(CrtProb& c);     // sets iblocks
-cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, int nseg, long long blocks,
+// block_seg: the segment of every block of the flattened grid (no search per block)
+cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, const int* block_seg, int nseg, long long blocks,
                                      const long long* row_begin_dev, long long total_rows, const Plan& pl,
                                      cudaStream_t st);
-cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_dev, int nseg, long long blocks,
+cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_dev, const int* block_seg, int nseg,
+                                 long long blocks,
                                  const Plan& pl, cudaStream_t st);
 cudaError_t launch_crt_grouped(bool single, const CrtProb* probs_dev, int nprob, long long blocks, const Plan& pl,
                                cudaStream_t st);

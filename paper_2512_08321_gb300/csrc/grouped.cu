@@ -27,6 +27,9 @@ struct emu_grouped_s {
   size_t mem_bytes = 0;
   size_t scratch_off = 0, scratch_bytes = 0;
   emu::ExpSeg* d_exp = nullptr;
+  int* maps = nullptr;              // segment of every exponent block, then of every split block
+  int* d_emap = nullptr;
+  int* d_smap = nullptr;
   int nexp = 0;
   long long exp_blocks = 0;
   long long* d_rowbeg = nullptr;
@@ -158,10 +161,11 @@ cudaError_t crt_phase(emu_grouped_s* g, cudaStream_t st) {
 cudaError_t enqueue(emu_grouped_s* g, cudaStream_t st, bool with_gemm) {
   cudaError_t e = cudaMemsetAsync(g->mem + g->scratch_off, 0, g->scratch_bytes, st);
   if (e != cudaSuccess) return e;
-  if ((e = launch_exponents_grouped(g->single, g->d_exp, g->nexp, g->exp_blocks, g->d_rowbeg, g->total_rows, *g->pl,
-                                    st)) != cudaSuccess)
+  if ((e = launch_exponents_grouped(g->single, g->d_exp, g->d_emap, g->nexp, g->exp_blocks, g->d_rowbeg,
+                                    g->total_rows, *g->pl, st)) != cudaSuccess)
     return e;
-  if ((e = launch_split_grouped(g->single, true, g->d_split, g->nsplit, g->split_blocks, *g->pl, st)) != cudaSuccess)
+  if ((e = launch_split_grouped(g->single, true, g->d_split, g->d_smap, g->nsplit, g->split_blocks, *g->pl, st)) !=
+      cudaSuccess)
     return e;
   if (!with_gemm) return cudaSuccess;
   if ((e = launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->status, st)) !=
@@ -378,6 +382,27 @@ emu_status_t emu_grouped_create(int is_single, int count, const emu_op_t* transa
   g->crt_blocks = cb;
   g->total_rows = rows;
   bool ok = true;
+  {
+    // segment of every block of the exponent and split launches
+    std::vector<int> maps(static_cast<size_t>(eb + sb) + 1, 0);
+    for (size_t q = 0; q < es.size(); ++q) {
+      const long long b1 = q + 1 < es.size() ? es[q + 1].block_begin : eb;
+      for (long long b = es[q].block_begin; b < b1; ++b) maps[b] = static_cast<int>(q);
+    }
+    for (size_t q = 0; q < ss.size(); ++q) {
+      const long long b1 = q + 1 < ss.size() ? ss[q + 1].block_begin : sb;
+      for (long long b = ss[q].block_begin; b < b1; ++b) maps[eb + b] = static_cast<int>(q);
+    }
+    if (cudaMalloc(&g->maps, sizeof(int) * maps.size()) == cudaSuccess) {
+      ok &= cudaMemcpy(g->maps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+      g->d_emap = g->maps;
+      g->d_smap = g->maps + eb;
+    } else {
+      g->maps = nullptr;
+      cudaGetLastError();
+      ok = false;
+    }
+  }
   if (!es.empty()) {
     ok &= cudaMemcpy(g->d_exp, es.data(), sizeof(ExpSeg) * es.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(g->d_rowbeg, rowb.data(), sizeof(long long) * rowb.size(), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -446,10 +471,11 @@ emu_status_t emu_grouped_phase_times(emu_grouped_t g, float* ms, void* stream) {
     if (cudaEventCreate(&e) != cudaSuccess) return EMU_ERR_CUDA;
   bool ok = cudaEventRecord(ev[0], st) == cudaSuccess;
   ok = ok && cudaMemsetAsync(g->mem + g->scratch_off, 0, g->scratch_bytes, st) == cudaSuccess;
-  ok = ok && launch_exponents_grouped(g->single, g->d_exp, g->nexp, g->exp_blocks, g->d_rowbeg, g->total_rows,
-                                      *g->pl, st) == cudaSuccess;
+  ok = ok && launch_exponents_grouped(g->single, g->d_exp, g->d_emap, g->nexp, g->exp_blocks, g->d_rowbeg,
+                                      g->total_rows, *g->pl, st) == cudaSuccess;
   ok = ok && cudaEventRecord(ev[1], st) == cudaSuccess;
-  ok = ok && launch_split_grouped(g->single, true, g->d_split, g->nsplit, g->split_blocks, *g->pl, st) == cudaSuccess;
+  ok = ok && launch_split_grouped(g->single, true, g->d_split, g->d_smap, g->nsplit, g->split_blocks, *g->pl,
+                                  st) == cudaSuccess;
   ok = ok && cudaEventRecord(ev[2], st) == cudaSuccess;
   ok = ok && launch_gemm_f16_grouped(g->d_gp, g->ngp, g->total_units, *g->pl, g->status, st) ==
                  cudaSuccess;
@@ -469,6 +495,7 @@ emu_status_t emu_grouped_destroy(emu_grouped_t g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->mem) cudaFree(g->mem);   // waits for work that still uses it
+  if (g->maps) cudaFree(g->maps);
   delete g;
   return EMU_OK;
 }

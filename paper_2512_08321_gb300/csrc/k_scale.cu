@@ -325,18 +325,10 @@ __global__ void exp_finalize_kernel(int64_t rows, const int* __restrict__ emax,
 }
 
 // ---- grouped forms: one launch per pass over every segment of a grouped call
-__device__ __forceinline__ int find_seg(const ExpSeg* segs, int nseg, long long b) {
-  int lo = 0, hi = nseg - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (segs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 template <bool S>
-__global__ void __launch_bounds__(kThreads) exp_max_grouped(const ExpSeg* __restrict__ segs, int nseg) {
-  const ExpSeg& g = segs[find_seg(segs, nseg, blockIdx.x)];
+__global__ void __launch_bounds__(kThreads) exp_max_grouped(const ExpSeg* __restrict__ segs,
+                                                            const int* __restrict__ block_seg) {
+  const ExpSeg& g = segs[block_seg[blockIdx.x]];
   const long long local = blockIdx.x - g.block_begin;
   const void* X = g.X;
   if (g.rows_contig)
@@ -348,8 +340,9 @@ __global__ void __launch_bounds__(kThreads) exp_max_grouped(const ExpSeg* __rest
 }
 
 template <bool S>
-__global__ void __launch_bounds__(kThreads) exp_sum_grouped(const ExpSeg* __restrict__ segs, int nseg) {
-  const ExpSeg& g = segs[find_seg(segs, nseg, blockIdx.x)];
+__global__ void __launch_bounds__(kThreads) exp_sum_grouped(const ExpSeg* __restrict__ segs,
+                                                            const int* __restrict__ block_seg) {
+  const ExpSeg& g = segs[block_seg[blockIdx.x]];
   const long long local = blockIdx.x - g.block_begin;
   const void* X = g.X;
   if (g.rows_contig)
@@ -599,18 +592,18 @@ long long exp_seg_blocks(ExpSeg& g) {
   return g.hchunks ? rb * g.hchunks : 0;
 }
 
-cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, int nseg, long long blocks,
+cudaError_t launch_exponents_grouped(bool single, const ExpSeg* segs_dev, const int* block_seg, int nseg, long long blocks,
                                      const long long* row_begin_dev, long long total_rows, const Plan& pl,
                                      cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
   if (blocks > 0) {
     if (blocks > 2147483647LL) return cudaErrorInvalidValue;
     if (single) {
-      exp_max_grouped<true><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
-      exp_sum_grouped<true><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
+      exp_max_grouped<true><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, block_seg);
+      exp_sum_grouped<true><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, block_seg);
     } else {
-      exp_max_grouped<false><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
-      exp_sum_grouped<false><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, nseg);
+      exp_max_grouped<false><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, block_seg);
+      exp_sum_grouped<false><<<static_cast<unsigned int>(blocks), kThreads, 0, st>>>(segs_dev, block_seg);
     }
     count_launches(2);
   }

@@ -405,16 +405,12 @@ __global__ void __launch_bounds__(kThreads) split_kernel(const void* __restrict_
 
 // one launch over every segment (rows of op(A) or columns of op(B) of each problem) of a grouped call
 template <bool SINGLE, typename T, int NCH = 0>
-__global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __restrict__ segs, int nseg,
+__global__ void __launch_bounds__(kThreads) split_grouped(const SplitSeg* __restrict__ segs,
+                                                          const int* __restrict__ block_seg,
                                                           const __grid_constant__ Plan pl) {
   __shared__ SplitSmem sm;
-  int lo = 0, hi = nseg - 1;
   const long long b = blockIdx.x;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (segs[mid].block_begin <= b) lo = mid; else hi = mid - 1;
-  }
-  const SplitSeg& g = segs[lo];
+  const SplitSeg& g = segs[block_seg[b]];
   const long long local = b - g.block_begin;
   const int64_t rt = local / g.htiles, ht = local % g.htiles;
   T* planes = static_cast<T*>(g.planes);
@@ -488,16 +484,16 @@ long long split_seg_blocks(SplitSeg& g) {
   return ((g.rows + kTileR - 1) / kTileR) * g.htiles;
 }
 
-cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_dev, int nseg, long long blocks,
-                                 const Plan& pl, cudaStream_t st) {
+cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_dev, const int* block_seg, int nseg,
+                                 long long blocks, const Plan& pl, cudaStream_t st) {
   if (nseg <= 0 || blocks <= 0) return cudaSuccess;
   if (blocks > 2147483647LL) return cudaErrorInvalidValue;
   const unsigned int gb = static_cast<unsigned int>(blocks);
   // fp16 planes: the chunk count compiled in, as in the single-GEMM split
   auto fixed = [&](auto nch_tag) {
     constexpr int NC = decltype(nch_tag)::value;
-    if (single) split_grouped<true, __half, NC><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
-    else split_grouped<false, __half, NC><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+    if (single) split_grouped<true, __half, NC><<<gb, kThreads, 0, st>>>(segs_dev, block_seg, pl);
+    else split_grouped<false, __half, NC><<<gb, kThreads, 0, st>>>(segs_dev, block_seg, pl);
   };
   bool done = fp16;
   if (fp16) {
@@ -513,11 +509,11 @@ cudaError_t launch_split_grouped(bool single, bool fp16, const SplitSeg* segs_de
   }
   if (!done) {
     if (single) {
-      if (fp16) split_grouped<true, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
-      else split_grouped<true, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+      if (fp16) split_grouped<true, __half><<<gb, kThreads, 0, st>>>(segs_dev, block_seg, pl);
+      else split_grouped<true, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, block_seg, pl);
     } else {
-      if (fp16) split_grouped<false, __half><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
-      else split_grouped<false, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, nseg, pl);
+      if (fp16) split_grouped<false, __half><<<gb, kThreads, 0, st>>>(segs_dev, block_seg, pl);
+      else split_grouped<false, int8_t><<<gb, kThreads, 0, st>>>(segs_dev, block_seg, pl);
     }
   }
   count_launches(1);
