@@ -9,15 +9,18 @@ namespace {
 // Exact non-negative bound products of
 // the 7-bit ceiling planes (entries <= 64, products <= 2^12).  Planes of both
 // operands: 0 = X_R (real input: X), 1 = X_I, 2 = X_R - X_I.
-//   complex: slot 0 = C-bar_I = A-bar_I B-bar_R + A-bar_R B-bar_I (2 nkb k-blocks),
-//            slot 1 = (A-bar_R - A-bar_I)(B-bar_R - B-bar_I) (nkb k-blocks),
-//            C-bar_R = C-bar_I + slot 1 (the identity of Section III-B);
-//   real:    slot 0 = C-bar = A-bar B-bar.
+//   complex: product 0 = C-bar_I = A-bar_I B-bar_R + A-bar_R B-bar_I (2 nkb k-blocks),
+//            product 1 = (A-bar_R - A-bar_I)(B-bar_R - B-bar_I) (nkb k-blocks),
+//            C-bar_R = C-bar_I + product 1 (the identity of Section III-B);
+//   real:    product 0 = C-bar = A-bar B-bar.
 // FP32 accumulation is exact while partial sums stay below 2^24, so each
 // accumulation restarts every kBoundChunk k-blocks (2048 k: sums <= 2^23).
-// TMEM holds, per slot, the FP32 accumulator (128 columns) and an int32
-// running sum (128 columns): after each chunk the epilogue adds the chunk
-// into the running sum, so the MMA can start the next chunk in the FP32 half.
+// TMEM holds two FP32 accumulators (128 columns each) and an int32 running
+// sum per product (128 columns each): after each chunk the epilogue adds the
+// chunk into its product's running sum.  A tile's chunks take the two FP32
+// accumulators in turn (the products' chunks interleaved while both have k
+// left, then the longer product's alone), so the MMA runs the next chunk in
+// one while the epilogue empties the other.
 // At the end of a tile each epilogue thread reads one output column (TMEM
 // lane) and 64 output rows; the row maxima over columns (5-step butterflies
 // across the warp) and the column maxima over rows of max(C-bar_R, C-bar_I) go
@@ -173,16 +176,18 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
     // ------------------------------------------------------------ MMA issuer (for a pair: the even CTA)
     if (lane == 0 && leader) {
       long long it = 0;
-      int used[2] = {0, 0};
+      uint32_t used = 0u;                           // bit a: parity of accumulator a's uses
       bool ok = true;
       for (long long u = first; ok && u < nunits; u += step) {
+        int pos = 0;                                 // chunks of this tile so far: accumulator pos & 1
         for (int c = 0; ok && c < nch0; ++c) {
           for (int slot = 0; ok && slot < 2; ++slot) {
             const int len = slot ? len1 : len0;
             if (c * kBoundChunk >= len) continue;
-            if (!wait_x(tempty(slot), static_cast<uint32_t>(used[slot] & 1) ^ 1u)) { ok = false; break; }
+            const int acc = pos++ & 1;
+            if (!wait_x(tempty(acc), ((used >> acc) & 1u) ^ 1u)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
+            const uint32_t td = tmem + static_cast<uint32_t>(acc * BN);
             const int kb0 = c * kBoundChunk, kb1 = min(len, (c + 1) * kBoundChunk);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % S);
@@ -200,8 +205,8 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
               if constexpr (PAIR) mma_commit_pair(empty(st)); else mma_commit(empty(st));
             }
             if (!ok) break;
-            if constexpr (PAIR) mma_commit_pair(tfull(slot)); else mma_commit(tfull(slot));
-            ++used[slot];
+            if constexpr (PAIR) mma_commit_pair(tfull(acc)); else mma_commit(tfull(acc));
+            used ^= 1u << acc;
           }
         }
       }
@@ -225,21 +230,23 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
     auto in_col = [&](int slot, int piece) {
       return lane_base + static_cast<uint32_t>(2 * BN + slot * BN + half * 64 + 32 * piece);
     };
-    int used[2] = {0, 0};
+    uint32_t used = 0u;                           // bit a: parity of accumulator a's uses
     bool ok = true;
     for (long long u = first; ok && u < nunits; u += step) {
       int tj, ti;
       tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
+      int pos = 0;
       for (int c = 0; ok && c < nch0; ++c) {
         for (int slot = 0; ok && slot < 2; ++slot) {
           const int len = slot ? len1 : len0;
           if (c * kBoundChunk >= len) continue;
-          if (!mbar_wait(tfull(slot), static_cast<uint32_t>(used[slot] & 1), ctl)) { ok = false; break; }
+          const int acc = pos++ & 1;                  // the FP32 accumulator of this chunk
+          if (!mbar_wait(tfull(acc), (used >> acc) & 1u, ctl)) { ok = false; break; }
           tc_fence_after();
 #pragma unroll 1
           for (int piece = 0; piece < 2; ++piece) {
             uint32_t v[32], a[32];
-            tmem_ld32(fp_col(slot, piece), v);
+            tmem_ld32(fp_col(acc, piece), v);
             if (c > 0) tmem_ld32(in_col(slot, piece), a);
             tmem_wait_ld();
 #pragma unroll
@@ -251,8 +258,8 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
           }
           tmem_wait_st();
           tc_fence_before();
-          if constexpr (PAIR) mbar_arrive_cluster(tempty_c0 + 8u * slot); else mbar_arrive(tempty(slot));
-          ++used[slot];
+          if constexpr (PAIR) mbar_arrive_cluster(tempty_c0 + 8u * acc); else mbar_arrive(tempty(acc));
+          used ^= 1u << acc;
         }
       }
       if (!ok) break;
