@@ -5,7 +5,8 @@
 // its FP16 rate.  Symmetric residues |r| <= 128 are exact fp16 values and a
 // product of two is at most 2^14, so an FP32 accumulator holds an exact
 // integer as long as every partial sum stays below 2^24.  The kernel
-// therefore splits k into chunks of `chunk_k` (<= 960): after each chunk the
+// therefore splits k into chunks of at most `chunk_k` (<= 960), as many as
+// that needs and of nearly equal size: after each chunk the
 // epilogue warps read the accumulator out of TMEM, reduce it modulo p_l
 // (|v| <= p/2 + 2 afterwards) and write it back, and the next chunk
 // accumulates on top.  The last chunk ends with the exact symmetric residue,
@@ -140,6 +141,12 @@ __device__ __forceinline__ uint32_t residue_word(const uint32_t* v, float p, flo
   const uint32_t hi = __byte_perm(static_cast<uint32_t>(r[2]), static_cast<uint32_t>(r[3]), 0x0040u);
   return __byte_perm(lo, hi, 0x5410u);
 }
+
+// k-blocks of chunk a of a unit: the nkb k-blocks split into nch chunks of
+// nearly equal size (at most ck each, as nch = ceil(nkb / ck)), so that the
+// last chunk is not a sliver that cannot hide the other job's epilogue.
+__device__ __forceinline__ int chunk_begin(int a, const Unit& U) { return (a * U.nkb) / U.nch; }
+__device__ __forceinline__ int chunk_end(int a, const Unit& U) { return ((a + 1) * U.nkb) / U.nch; }
 
 // descending k chunks on the odd units a CTA processes (its units are
 // blockIdx.x, blockIdx.x + gridDim.x, ...)
@@ -316,8 +323,8 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
           for (int which = 0; ok && which < 2; ++which) {
             const int job = which ? U.jb : U.ja;
             if (job < 0) continue;
-            const int kb1 = min(U.nkb, (a + 1) * U.ck);
-            for (int kb = a * U.ck; kb < kb1; ++kb, ++it) {
+            const int kb1 = chunk_end(a, U);
+            for (int kb = chunk_begin(a, U); kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
@@ -371,7 +378,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
             const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
             const uint32_t idesc = C::kIdescNoN | (static_cast<uint32_t>(U.bn >> 3) << 17);
             const int a = U.desc ? U.nch - 1 - c : c;
-            const int kb0 = a * U.ck, kb1 = min(U.nkb, (a + 1) * U.ck);
+            const int kb0 = chunk_begin(a, U), kb1 = chunk_end(a, U);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
@@ -606,8 +613,8 @@ __device__ __forceinline__ void pair_body(const SingleWork<kPairBN>& W, const Pl
           for (int which = 0; ok && which < 2; ++which) {
             const int job = which ? U.jb : U.ja;
             if (job < 0) continue;
-            const int kb1 = min(U.nkb, (a + 1) * U.ck);
-            for (int kb = a * U.ck; kb < kb1; ++kb, ++it) {
+            const int kb1 = chunk_end(a, U);
+            for (int kb = chunk_begin(a, U); kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % S);
               const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
@@ -656,7 +663,7 @@ __device__ __forceinline__ void pair_body(const SingleWork<kPairBN>& W, const Pl
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(slot * kPairBN);
             const int a = U.desc ? U.nch - 1 - c : c;
-            const int kb0 = a * U.ck, kb1 = min(U.nkb, (a + 1) * U.ck);
+            const int kb0 = chunk_begin(a, U), kb1 = chunk_end(a, U);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % S);
               const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
