@@ -148,6 +148,26 @@ __device__ __forceinline__ uint32_t residue_word(const uint32_t* v, float p, flo
 __device__ __forceinline__ int chunk_begin(int a, const Unit& U) { return (a * U.nkb) / U.nch; }
 __device__ __forceinline__ int chunk_end(int a, const Unit& U) { return ((a + 1) * U.nkb) / U.nch; }
 
+// In single launches a unit with one job (the last job pair when the job count
+// is odd) and two or more chunks runs its chunks in the two accumulator slots in turn (slot
+// c & 1), so the MMAs of one chunk overlap the in-place reduction of the one
+// before; the final epilogue adds the two partial sums (one reduced, |v| <= p/2
+// + 2, the other at most chunk_k products of 2^14: below 2^24, exact) before
+// the last reduction.
+__device__ __forceinline__ bool unit_split(const Unit& U) { return U.jb < 0 && U.nch >= 2; }
+
+// job and accumulator slot of step (chunk c, which) of a unit; false: no such step
+__device__ __forceinline__ bool unit_step(const Unit& U, bool split1, int c, int which, int& job, int& slot) {
+  if (split1) {
+    job = U.ja;
+    slot = c & 1;
+    return which == 0;
+  }
+  job = which ? U.jb : U.ja;
+  slot = which;
+  return job >= 0;
+}
+
 // descending k chunks on the odd units a CTA processes (its units are
 // blockIdx.x, blockIdx.x + gridDim.x, ...)
 __device__ __forceinline__ bool unit_desc(long long u, int kalt) {
@@ -368,17 +388,18 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
           U = nxt;
           if (u + gridDim.x < nunits) nxt = W.get(u + gridDim.x, hint);
         }
+        const bool split1 = RING == 0 && unit_split(U);   // single launches (the grouped kernel has no registers to spare)
         for (int c = 0; ok && c < U.nch; ++c) {
           for (int which = 0; ok && which < 2; ++which) {
-            const int job = which ? U.jb : U.ja;
-            if (job < 0) continue;
-            const int slot = which;
+            int job, slot;
+            if (!unit_step(U, split1, c, which, job, slot)) continue;
             if (!mbar_wait(tempty(slot), ((used >> slot) & 1u) ^ 1u, ctl)) { ok = false; break; }
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(slot * BN);
             const uint32_t idesc = C::kIdescNoN | (static_cast<uint32_t>(U.bn >> 3) << 17);
             const int a = U.desc ? U.nch - 1 - c : c;
             const int kb0 = chunk_begin(a, U), kb1 = chunk_end(a, U);
+            const bool fresh = split1 ? c < 2 : c == 0;     // the slot's first chunk of this unit
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % kStages);
               const uint32_t ph = static_cast<uint32_t>((it / kStages) & 1);
@@ -390,7 +411,7 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
               for (int kk = 0; kk < BK / UK; ++kk) {
                 // advance the start address by 32 bytes per 16 fp16 of k
                 const uint64_t off = static_cast<uint64_t>((kk * UK * 2) >> 4);
-                mma_f16(td, da + off, db + off, idesc, !(c == 0 && kb == kb0 && kk == 0));
+                mma_f16(td, da + off, db + off, idesc, !(fresh && kb == kb0 && kk == 0));
               }
               mma_commit(empty(st));
             }
@@ -431,12 +452,14 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
       // columns of this warp: [part * pw, part * pw + pw), pw >= 32; parts past the tile only wait
       const int pw = (U.bn / kParts) < 32 ? 32 : (U.bn / kParts);
       const bool mine = part * pw < U.bn;
+      const bool split1 = RING == 0 && unit_split(U);   // single launches (the grouped kernel has no registers to spare)
       for (int c = 0; ok && c < U.nch; ++c) {
         const bool last = (c == U.nch - 1);
+        // one-job unit: the second-to-last chunk's slot is reduced and then held for the final
+        const bool hold = split1 && c == U.nch - 2;
         for (int which = 0; ok && which < 2; ++which) {
-          const int job = which ? U.jb : U.ja;
-          if (job < 0) continue;
-          const int slot = which;
+          int job, slot;
+          if (!unit_step(U, split1, c, which, job, slot)) continue;
           const int l = job / U.ppm;
           const float p = static_cast<float>(pl.p[l]);
           const float inv_p = 1.0f / p;
@@ -447,7 +470,8 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
                               static_cast<uint32_t>(slot * BN + part * pw);
           if (!mine) {
             tc_fence_before();
-            mbar_arrive(tempty(slot));
+            if (!hold) mbar_arrive(tempty(slot));
+            if (split1 && last) mbar_arrive(tempty(slot ^ 1));   // the held slot
           } else if (!last) {
             // in-place reduction: keeps every later partial sum below 2^24
 #pragma unroll 1
@@ -464,19 +488,33 @@ __device__ __forceinline__ void gemm_body(const Work& W, const Plan& pl, unsigne
             }
             tmem_wait_st();
             tc_fence_before();
-            mbar_arrive(tempty(slot));
+            if (!hold) mbar_arrive(tempty(slot));
           } else {
             // final: exact symmetric residue, int8, row-contiguous
             const int64_t row0 = static_cast<int64_t>(U.ti) * U.bn + part * pw;
             int8_t* out = U.res + static_cast<int64_t>(job) * U.n * U.ldr + col * U.ldr + row0;
+            const uint32_t tb = ta + static_cast<uint32_t>(((slot ^ 1) - slot) * BN);   // the held slot
 #pragma unroll 1
             for (int cc = 0; cc < pw; cc += 32) {
               uint32_t v[32];
               tmem_ld32(ta + cc, v);
               tmem_wait_ld();
+              if (split1) {
+                // add the held slot's partial sum, 16 columns at a time
+#pragma unroll
+                for (int h = 0; h < 32; h += 16) {
+                  uint32_t o[16];
+                  tmem_ld16(tb + cc + h, o);
+                  tmem_wait_ld();
+#pragma unroll
+                  for (int q = 0; q < 16; ++q)
+                    v[h + q] = __float_as_uint(__uint_as_float(v[h + q]) + __uint_as_float(o[q]));
+                }
+              }
               if (cc == pw - 32) {
                 tc_fence_before();
                 mbar_arrive(tempty(slot));          // TMEM slot may be refilled
+                if (split1) mbar_arrive(tempty(slot ^ 1));
               }
               uint32_t w[8];
 #pragma unroll
