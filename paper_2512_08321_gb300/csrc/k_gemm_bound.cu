@@ -28,7 +28,7 @@ namespace {
 // fill, so they add nothing.
 constexpr int kBoundBN = 128;          // output rows per tile (MMA N)
 constexpr int kBoundChunk = 32;
-constexpr int kBoundTmemCols = 512;    // 2 slots x (128 FP32 + 128 int32) columns
+constexpr int kBoundTmemCols = 512;    // 2 FP32 accumulators + 2 int32 running sums, 128 columns each
 
 // One-SM tiles: 128 output columns x 128 rows, 6 stages of 32 KB.  SM pairs
 // (cta_group::2, a cluster of two CTAs): 256 columns x 128 rows, each CTA
@@ -51,10 +51,10 @@ struct BoundSched {
   int TJ, TI, tiles, group, nkb, real;
 };
 
-// which operand planes and k-block of the planes feed k-block kb of a slot
-__device__ __forceinline__ void bound_src(int slot, int kb, int nkb, bool real, int& pa, int& pb, int& kc) {
+// which operand planes and k-block of the planes feed k-block kb of a product
+__device__ __forceinline__ void bound_src(int prod, int kb, int nkb, bool real, int& pa, int& pb, int& kc) {
   if (real) { pa = 0; pb = 0; kc = kb; return; }
-  if (slot == 1) { pa = 2; pb = 2; kc = kb; return; }
+  if (prod == 1) { pa = 2; pb = 2; kc = kb; return; }
   if (kb < nkb) { pa = 0; pb = 1; kc = kb; }        // B-bar_R (MMA A) x A-bar_I (MMA B)
   else { pa = 1; pb = 0; kc = kb - nkb; }           // B-bar_I x A-bar_R
 }
@@ -84,7 +84,7 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
   Ctl ctl{status, abort_s};
   const bool real = s.real != 0;
   const int len0 = real ? s.nkb : 2 * s.nkb, len1 = real ? 0 : s.nkb;
-  const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk;   // len1 <= len0: slot 1 has no more chunks
+  const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk;   // len1 <= len0: product 1 has no more chunks
   const long long nunits = s.tiles;
   const uint32_t rank = PAIR ? cluster_rank() : 0u;
   const bool leader = rank == 0;
@@ -119,7 +119,7 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
   if constexpr (PAIR) cluster_sync(); else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  // the even CTA's barriers (the pair's loads count on its full barriers, both epilogues free its slots)
+  // the even CTA's barriers (the pair's loads count on its full barriers, both epilogues free its accumulators)
   const uint32_t full_c0 = PAIR ? map_to_rank(full(0), 0) : full(0);
   const uint32_t tempty_c0 = PAIR ? map_to_rank(tempty(0), 0) : tempty(0);
   auto wait_x = [&](uint32_t bar, uint32_t parity) {     // waits on barriers the other CTA arrives on
@@ -135,8 +135,8 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
         int tj, ti;
         tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
         for (int c = 0; ok && c < nch0; ++c) {
-          for (int slot = 0; ok && slot < 2; ++slot) {
-            const int len = slot ? len1 : len0;
+          for (int prod = 0; ok && prod < 2; ++prod) {
+            const int len = prod ? len1 : len0;
             if (c * kBoundChunk >= len) continue;
             const int kb1 = min(len, (c + 1) * kBoundChunk);
             for (int kb = c * kBoundChunk; kb < kb1; ++kb, ++it) {
@@ -144,7 +144,7 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
               const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
               if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
               int pa, pb, kc;
-              bound_src(slot, kb, s.nkb, real, pa, pb, kc);
+              bound_src(prod, kb, s.nkb, real, pa, pb, kc);
               const uint32_t sa = base + st * BC::kStageBytes;
               if constexpr (PAIR) {
                 if (leader) mbar_expect_tx(full(st), static_cast<uint32_t>(2 * BC::kStageBytes));
@@ -181,8 +181,8 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
       for (long long u = first; ok && u < nunits; u += step) {
         int pos = 0;                                 // chunks of this tile so far: accumulator pos & 1
         for (int c = 0; ok && c < nch0; ++c) {
-          for (int slot = 0; ok && slot < 2; ++slot) {
-            const int len = slot ? len1 : len0;
+          for (int prod = 0; ok && prod < 2; ++prod) {
+            const int len = prod ? len1 : len0;
             if (c * kBoundChunk >= len) continue;
             const int acc = pos++ & 1;
             if (!wait_x(tempty(acc), ((used >> acc) & 1u) ^ 1u)) { ok = false; break; }
@@ -224,11 +224,12 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int half = ew >> 2;                        // columns [64 half, 64 half + 64) of a slot
+    const int half = ew >> 2;                        // columns [64 half, 64 half + 64) of a tile
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(quad * 32) << 16);
-    auto fp_col = [&](int slot, int piece) { return lane_base + static_cast<uint32_t>(slot * BN + half * 64 + 32 * piece); };
-    auto in_col = [&](int slot, int piece) {
-      return lane_base + static_cast<uint32_t>(2 * BN + slot * BN + half * 64 + 32 * piece);
+    // FP32 accumulator acc, int32 running sum of product prod
+    auto fp_col = [&](int acc, int piece) { return lane_base + static_cast<uint32_t>(acc * BN + half * 64 + 32 * piece); };
+    auto in_col = [&](int prod, int piece) {
+      return lane_base + static_cast<uint32_t>(2 * BN + prod * BN + half * 64 + 32 * piece);
     };
     uint32_t used = 0u;                           // bit a: parity of accumulator a's uses
     bool ok = true;
@@ -237,8 +238,8 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
       tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
       int pos = 0;
       for (int c = 0; ok && c < nch0; ++c) {
-        for (int slot = 0; ok && slot < 2; ++slot) {
-          const int len = slot ? len1 : len0;
+        for (int prod = 0; ok && prod < 2; ++prod) {
+          const int len = prod ? len1 : len0;
           if (c * kBoundChunk >= len) continue;
           const int acc = pos++ & 1;                  // the FP32 accumulator of this chunk
           if (!mbar_wait(tfull(acc), (used >> acc) & 1u, ctl)) { ok = false; break; }
@@ -247,14 +248,14 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
           for (int piece = 0; piece < 2; ++piece) {
             uint32_t v[32], a[32];
             tmem_ld32(fp_col(acc, piece), v);
-            if (c > 0) tmem_ld32(in_col(slot, piece), a);
+            if (c > 0) tmem_ld32(in_col(prod, piece), a);
             tmem_wait_ld();
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const int x = static_cast<int>(__uint_as_float(v[q]));   // exact integer
               a[q] = static_cast<uint32_t>((c > 0 ? static_cast<int>(a[q]) : 0) + x);
             }
-            tmem_st32(in_col(slot, piece), a);
+            tmem_st32(in_col(prod, piece), a);
           }
           tmem_wait_st();
           tc_fence_before();
