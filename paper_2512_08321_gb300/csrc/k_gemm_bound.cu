@@ -14,7 +14,9 @@ namespace {
 //            C-bar_R = C-bar_I + product 1 (the identity of Section III-B);
 //   real:    product 0 = C-bar = A-bar B-bar.
 // FP32 accumulation is exact while partial sums stay below 2^24, so each
-// accumulation restarts every kBoundChunk k-blocks (2048 k: sums <= 2^23).
+// accumulation restarts every kBoundChunk k-blocks: 4096 k of products of
+// magnitude at most 64 x 64 = 2^12, so every partial sum is at most 2^24 in
+// magnitude, an integer FP32 holds exactly.
 // TMEM holds two FP32 accumulators (128 columns each) and an int32 running
 // sum per product (128 columns each): after each chunk the epilogue adds the
 // chunk into its product's running sum.  A tile's chunks take the two FP32
@@ -27,7 +29,7 @@ namespace {
 // to global memory by atomicMax.  Rows/columns beyond m/n read TMA's zero
 // fill, so they add nothing.
 constexpr int kBoundBN = 128;          // output rows per tile (MMA N)
-constexpr int kBoundChunk = 32;
+constexpr int kBoundChunk = 64;
 constexpr int kBoundTmemCols = 512;    // 2 FP32 accumulators + 2 int32 running sums, 128 columns each
 
 // One-SM tiles: 128 output columns x 128 rows, 6 stages of 32 KB.  SM pairs
