@@ -73,7 +73,7 @@ def test_real_accurate_bitexact(single, opA, opB):
 
 @pytest.mark.parametrize("real", [False, True])
 def test_bound_products_over_many_chunks(real):
-    # k = 5000: the bound accumulation restarts every 2048 (complex C-bar_I runs over 2k)
+    # k = 5000: the bound accumulation restarts every 4096 (complex C-bar_I runs over 2k: 3 chunks)
     if real:
         A, B = _real(70, 150, 5000, "N", "N", 1.0, 84, False)
         ref = RealEmulation(A, B, 12, scaling="accurate").out
