@@ -122,3 +122,31 @@ def test_fullsize_sampled_real(workload, moduli, tol):
     # the fewest listed moduli whose error is no worse than native is recorded; the bench's N must meet it
     default_N = wl["N"]
     assert report["by_moduli"][default_N]["max_normalised_error"] <= max(report["native"]["max_normalised_error"], tol)
+
+
+def test_sm_pair_tiles_at_size_sampled():
+    """Residue products on SM pairs (a launch form the autotuner can select) at a
+    large size, bit for bit against the oracle on sampled entries."""
+    m = n = k = 8192
+    N = 15
+    A = paper_matrix_device(m, k, 1.0, 2025, torch.complex128)      # storage (k, m)
+    B = paper_matrix_device(k, n, 1.0, 2026, torch.complex128)      # storage (n, k)
+    C = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    rng = np.random.default_rng(11)
+    rows = np.concatenate([[0, m - 1], rng.integers(0, m, 14)])
+    cols = np.concatenate([[0, n - 1], rng.integers(0, n, 14)])
+    saved = emu.emu_get_tuning(emu.EMU_TUNE_CTA_PAIR)
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_CTA_PAIR, 1), "tuning")
+    try:
+        emu.check(emu.emu_zgemm("N", "N", m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 0.0, C.data_ptr(), m,
+                                N, None), "zgemm")
+        torch.cuda.synchronize()
+        assert emu.emu_stream_status() == emu.EMU_OK
+    finally:
+        emu.emu_set_tuning(emu.EMU_TUNE_CTA_PAIR, saved)
+    got = C[torch.from_numpy(cols).cuda(), torch.from_numpy(rows).cuda()].cpu().numpy()
+    ur, uc = np.unique(rows), np.unique(cols)
+    Arows = A[:, torch.from_numpy(ur).cuda()].t().cpu().numpy()     # sampled rows of A, (r, k)
+    Bcols = B[torch.from_numpy(uc).cuda(), :].t().cpu().numpy()     # sampled columns of B, (k, c)
+    want = emulate_entries(Arows, Bcols, N, np.searchsorted(ur, rows), np.searchsorted(uc, cols))
+    assert np.array_equal(got.view(np.uint64), np.asarray(want, dtype=np.complex128).view(np.uint64))
