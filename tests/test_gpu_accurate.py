@@ -20,12 +20,13 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(autouse=True)
 def _accurate():
+    pair = emu.emu_get_tuning(emu.EMU_TUNE_BOUND_PAIR)
     emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE), "scaling")
     yield
     emu.emu_set_scaling(emu.EMU_SCALING_FAST)
     emu.emu_set_crt_mode(emu.EMU_CRT_EXACT)
     emu.emu_set_tuning(emu.EMU_TUNE_NBLOCK, 0)
-    emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, 0)
+    emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, pair)
 
 
 def _cplx(m, n, k, opA, opB, phi, seed, single):
@@ -179,12 +180,14 @@ def test_accuracy_gain_over_fast_at_same_N():
     assert accu[more].max() < fast[more].max(), (accu[more].max(), fast[more].max())
 
 
+@pytest.mark.parametrize("pair", [1, 0], ids=["sm_pairs", "one_sm"])
 @pytest.mark.parametrize("case", ["complex", "real", "single", "chunks", "edges", "one"])
-def test_bound_products_on_sm_pairs(case):
+def test_bound_products_on_sm_pairs(case, pair):
     """The bound products on SM pairs (256-column tiles, each CTA of a pair
-    holding 128 of them and loading half of the 128 rows): the same exponents
-    and results, including column counts that leave the odd CTA only padding."""
-    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, 1), "bound pair")
+    holding 128 of them and loading half of the 128 rows) and on one SM
+    (128-column tiles): the same exponents and results, including column
+    counts that leave the odd CTA of a pair only padding."""
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, pair), "bound pair")
     if case == "real":
         A, B = _real(300, 520, 333, "N", "T", 2.0, 94, False)
         ref = RealEmulation(A, apply_op_real(B, "T"), 14, scaling="accurate").out

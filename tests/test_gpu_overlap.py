@@ -73,3 +73,24 @@ def test_overlapped_blocks_real(single):
 def test_overlap_knob():
     assert emu.emu_get_tuning(emu.EMU_TUNE_OVERLAP) == -1         # default: on for the real GEMMs only
     assert emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, 2) == emu.EMU_ERR_INVALID_ARG
+
+
+def test_tolerance_call_with_overlap():
+    """emu_zgemm_tol hands its precomputed exponent sums to the GEMM; with the
+    overlapped column blocks (n >= 2048) the result equals the plain call with
+    the N it chose, bit for bit."""
+    import torch
+    from .helpers import dev, host
+    m, n, k = 300, 2048 + 200, 150
+    A = paper_matrix(m, k, 1.0, 520)
+    B = paper_matrix(k, n, 1.0, 521)
+    dA, dB = dev(A), dev(B)
+    dC = dev(np.zeros((m, n), dtype=np.complex128))
+    st, N = _with_overlap(True, lambda: emu.emu_zgemm_tol("N", "N", m, n, k, 1.0, dA.data_ptr(), m, dB.data_ptr(),
+                                                          k, 0.0, dC.data_ptr(), m, 1e-10,
+                                                          torch.cuda.current_stream()))
+    emu.check(st, "zgemm_tol")
+    torch.cuda.synchronize()
+    got = host(dC, m)
+    want = _with_overlap(False, lambda: run_gemm(A, B, N))
+    assert same_bits(got, want), mismatch_report(got, want)
