@@ -343,8 +343,10 @@ __device__ __forceinline__ void tc_epilogue(const Q& q, const TcPos& t, uint32_t
 // written once item n - 1's MMA has read it (issued a whole epilogue earlier,
 // so this seldom waits); the smaller block fits as many blocks per SM as the
 // TMEM columns allow.  Measured: single launches (ZGEMM 4096^3, N = 14) ran
-// 5 % more instructions with one buffer at the same 6 blocks, grouped launches
-// (N = 16) gained from 5 to 8 blocks; so single launches take 2, grouped 1.
+// 5 % more instructions with one buffer at the same 6 blocks, and at ZGEMM
+// 16384^3 (N = 15) took 5.47 ms with one buffer at 8 blocks against 5.36-5.39
+// with two at 6; grouped launches (N = 16) gained from 5 to 8 blocks.  So
+// single launches take 2, grouped 1.
 template <bool SINGLE, bool REAL, bool WIDE, int L, bool ROBUST, int NBUF, class Work>
 __device__ __forceinline__ void crt_tc_body(const Work& W, const Plan& pl, unsigned int* status) {
   using LY = TcLayout<REAL, WIDE>;
