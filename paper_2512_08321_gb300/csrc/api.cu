@@ -99,7 +99,8 @@ emu_status_t device_init(int dev, DeviceState*& ds) {
 // bufs = 2: two sets of B planes and residues (column blocks overlapped).
 struct Layout {
   int64_t kpad, ldr;
-  size_t off_x, off_y, off_scr, off_acc, off_pa, off_pb, off_res, total;
+  size_t off_x, off_y, off_scr, off_acc, off_bnd, off_pa, off_pb, off_res, total;
+  size_t bnd_bytes;             // accurate mode, complex input: bound-product scratch
   size_t pb_bytes, res_bytes;   // one set
 };
 
@@ -116,6 +117,8 @@ Layout layout(int64_t m, int64_t n, int64_t k, int N, bool fp16, int ppm = 3, in
   L.off_y = o;   o += al(static_cast<size_t>(n) * 2);
   L.off_scr = o; o += al(exponents_scratch_bytes(m > nb ? m : nb));
   L.off_acc = o; o += al(static_cast<size_t>(12) * (m + n));   // accurate mode: e, flag, bound maxima
+  L.bnd_bytes = ppm == 3 ? al(bound_scratch_bytes(m, nb)) : 0;
+  L.off_bnd = o; o += L.bnd_bytes;
   L.off_pa = o;  o += al(static_cast<size_t>(ppm * N) * m * L.kpad * esz);
   L.pb_bytes = al(static_cast<size_t>(ppm * N) * nb * L.kpad * esz);
   L.res_bytes = al(static_cast<size_t>(ppm * N) * nb * L.ldr);
@@ -414,7 +417,8 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
           launch_bound_split(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, L.kpad, pb, st) !=
               cudaSuccess)
         return EMU_ERR_CUDA;
-      e = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ds->status, st, tn.bound_pair == 1);
+      e = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ws + L.off_bnd, L.bnd_bytes, ds->status,
+                            st, tn.bound_pair == 1);
       if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
       if (e != cudaSuccess) return EMU_ERR_CUDA;
     }

@@ -84,7 +84,9 @@ size_t exponents_scratch_bytes(int64_t rows);
 //   launch_bound_split    7-bit ceiling planes ceil(|v| 2^(5-e)) as fp16, [planes][rows][kpad]:
 //                         complex 3 planes (Re, Im, Re - Im), real 1; flagged rows are zero
 //   launch_gemm_bound     exact bound products on tcgen05; atomicMax of the row maxima into
-//                         Mrow[m] and of the column maxima into Ncol[n] (both zeroed by the caller)
+//                         Mrow[m] and of the column maxima into Ncol[n] (both zeroed by the caller);
+//                         complex input parks one running sum per tile in `scratch`
+//                         (bound_scratch_bytes(m, n) bytes, fewer CTAs when it is smaller)
 //   launch_accu_finalize  x_r = 5 - e_r + max{E : 4^E max(M_r,1) <= (P-1)/2}
 cudaError_t launch_exp_max(bool single, bool real, const void* X, int64_t rows, int64_t k, int64_t rs, int64_t hs,
                            int* emax, unsigned int* flag, cudaStream_t st);
@@ -92,8 +94,9 @@ cudaError_t launch_bound_split(bool single, bool real, const void* X, int64_t ro
                                int64_t hs, const int* emax, const unsigned int* flag, int64_t kpad, void* planes,
                                cudaStream_t st);
 cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, const void* planesA,
-                              const void* planesB, unsigned int* Mrow, unsigned int* Ncol, unsigned int* status,
-                              cudaStream_t st, bool pair = false);
+                              const void* planesB, unsigned int* Mrow, unsigned int* Ncol, void* scratch,
+                              size_t scratch_bytes, unsigned int* status, cudaStream_t st, bool pair = false);
+size_t bound_scratch_bytes(int64_t m, int64_t n);
 cudaError_t launch_accu_finalize(int64_t rows, const int* emax, const unsigned int* flag, const unsigned int* Mb,
                                  const Plan& pl, int16_t* xout, cudaStream_t st);
 

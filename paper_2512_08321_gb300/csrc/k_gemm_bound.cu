@@ -17,32 +17,39 @@ namespace {
 // accumulation restarts every kBoundChunk k-blocks: 4096 k of products of
 // magnitude at most 64 x 64 = 2^12, so every partial sum is at most 2^24 in
 // magnitude, an integer FP32 holds exactly.
-// TMEM holds two FP32 accumulators (128 columns each) and an int32 running
-// sum per product (128 columns each): after each chunk the epilogue adds the
-// chunk into its product's running sum.  A tile's chunks take the two FP32
-// accumulators in turn (the products' chunks interleaved while both have k
-// left, then the longer product's alone), so the MMA runs the next chunk in
-// one while the epilogue empties the other.
-// At the end of a tile each epilogue thread reads one output column (TMEM
+// A tile is 256 output rows wide (MMA N = 256): an MMA of N = 128 reads a
+// third more operand bytes per flop and ran at about 0.75 of the rate the
+// 256-wide residue products reach.  TMEM holds the two FP32 accumulators (256
+// columns each), which a tile's chunks take in turn, so the MMA runs the next
+// chunk in one while the epilogue empties the other.  The int32 running sum of
+// the product being accumulated lives in the epilogue's registers (16 warps,
+// each thread one TMEM lane and 64 of the 256 columns); the products run one
+// after the other, and the finished C-bar_I sum of a complex tile is parked in
+// global scratch (128 KB per CTA, read back by the thread that wrote it) while
+// product 1 accumulates.
+// At the end of a tile each epilogue thread holds one output column (TMEM
 // lane) and 64 output rows; the row maxima over columns (5-step butterflies
 // across the warp) and the column maxima over rows of max(C-bar_R, C-bar_I) go
 // to global memory by atomicMax.  Rows/columns beyond m/n read TMA's zero
 // fill, so they add nothing.
-constexpr int kBoundBN = 128;          // output rows per tile (MMA N)
+constexpr int kBoundBN = 256;          // output rows per tile (MMA N)
 constexpr int kBoundChunk = 64;
-constexpr int kBoundTmemCols = 512;    // 2 FP32 accumulators + 2 int32 running sums, 128 columns each
+constexpr int kBoundTmemCols = 512;    // 2 FP32 accumulators, 256 columns each
+constexpr int kBoundEpi = 16;          // epilogue warps: 4 on each TMEM lane quadrant
+constexpr int kBoundThreads = 32 * (2 + kBoundEpi);
+constexpr int kBoundSums = kBoundBN / (kBoundEpi / 4);                  // 64 columns per epilogue thread
+constexpr size_t kBoundScratchPerCta = static_cast<size_t>(BM) * kBoundBN * 4;   // 128 KB
+constexpr int kBoundMaxCtas = 256;     // scratch bound of bound_scratch_bytes (GB300: 152 SMs)
 
-// One-SM tiles: 128 output columns x 128 rows, 6 stages of 32 KB.  SM pairs
-// (cta_group::2, a cluster of two CTAs): 256 columns x 128 rows, each CTA
-// holding 128 of the columns in its TMEM and loading 64 of the A-bar rows, so
-// a stage is 24 KB and 8 of them fit; the even CTA issues the MMAs (M = 256).
-// Measured at ZGEMM 16384^3, N = 15 in accurate mode: the exponent phase took
-// 26.8-27.3 ms on pairs against 27.7-28.2 on one SM, so pairs are the default.
+// One-SM tiles: 128 output columns x 256 rows, 4 stages of 48 KB.  SM pairs
+// (cta_group::2, a cluster of two CTAs): 256 columns x 256 rows, each CTA
+// holding 128 of the columns in its TMEM and loading 128 of the A-bar rows, so
+// a stage is 32 KB and 6 of them fit; the even CTA issues the MMAs (M = 256).
 template <bool PAIR>
 struct BoundCfg {
   static constexpr int kRowsB = PAIR ? kBoundBN / 2 : kBoundBN;      // A-bar rows per CTA and stage
   static constexpr int kStageBytes = kStageA + kRowsB * BK * 2;
-  static constexpr int kStages = PAIR ? 8 : 6;
+  static constexpr int kStages = PAIR ? 6 : 4;
   static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
   static constexpr int kTileCols = PAIR ? 2 * BM : BM;
   static constexpr uint32_t kIdesc = (1u << 4) | (static_cast<uint32_t>(kBoundBN >> 3) << 17) |
@@ -64,7 +71,7 @@ __device__ __forceinline__ void bound_src(int prod, int kb, int nkb, bool real, 
 template <bool PAIR>
 __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtensorMap* mapB, const BoundSched& s,
                                            unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
-                                           int64_t m, int64_t n, unsigned int* status) {
+                                           int* __restrict__ scratch, int64_t m, int64_t n, unsigned int* status) {
   using BC = BoundCfg<PAIR>;
   constexpr int BN = kBoundBN;
   constexpr int S = BC::kStages;
@@ -85,8 +92,7 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Ctl ctl{status, abort_s};
   const bool real = s.real != 0;
-  const int len0 = real ? s.nkb : 2 * s.nkb, len1 = real ? 0 : s.nkb;
-  const int nch0 = (len0 + kBoundChunk - 1) / kBoundChunk;   // len1 <= len0: product 1 has no more chunks
+  const int len0 = real ? s.nkb : 2 * s.nkb, len1 = real ? 0 : s.nkb;   // k-blocks of products 0 and 1
   const long long nunits = s.tiles;
   const uint32_t rank = PAIR ? cluster_rank() : 0u;
   const bool leader = rank == 0;
@@ -100,7 +106,7 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(tfull(i), 1);
-      mbar_init(tempty(i), (PAIR ? 2 : 1) * 32 * kEpiWarps);
+      mbar_init(tempty(i), (PAIR ? 2 : 1) * 32 * kBoundEpi);
     }
     mbar_init(done, 1);
     *abort_s = 0;
@@ -136,28 +142,24 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
       for (long long u = first; ok && u < nunits; u += step) {
         int tj, ti;
         tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
-        for (int c = 0; ok && c < nch0; ++c) {
-          for (int prod = 0; ok && prod < 2; ++prod) {
-            const int len = prod ? len1 : len0;
-            if (c * kBoundChunk >= len) continue;
-            const int kb1 = min(len, (c + 1) * kBoundChunk);
-            for (int kb = c * kBoundChunk; kb < kb1; ++kb, ++it) {
-              const int st = static_cast<int>(it % S);
-              const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
-              if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
-              int pa, pb, kc;
-              bound_src(prod, kb, s.nkb, real, pa, pb, kc);
-              const uint32_t sa = base + st * BC::kStageBytes;
-              if constexpr (PAIR) {
-                if (leader) mbar_expect_tx(full(st), static_cast<uint32_t>(2 * BC::kStageBytes));
-                const uint32_t fb = full_c0 + 8u * st;
-                tma_load_3d_pair(sa, mapA, fb, kc * BK, tj * BC::kTileCols + static_cast<int>(rank) * BM, pa);
-                tma_load_3d_pair(sa + kStageA, mapB, fb, kc * BK, ti * BN + static_cast<int>(rank) * BC::kRowsB, pb);
-              } else {
-                mbar_expect_tx(full(st), BC::kStageBytes);
-                tma_load_3d(sa, mapA, full(st), kc * BK, tj * BM, pa);
-                tma_load_3d(sa + kStageA, mapB, full(st), kc * BK, ti * BN, pb);
-              }
+        for (int prod = 0; ok && prod < 2; ++prod) {
+          const int len = prod ? len1 : len0;
+          for (int kb = 0; kb < len; ++kb, ++it) {
+            const int st = static_cast<int>(it % S);
+            const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
+            if (!mbar_wait(empty(st), ph ^ 1u, ctl)) { ok = false; break; }
+            int pa, pb, kc;
+            bound_src(prod, kb, s.nkb, real, pa, pb, kc);
+            const uint32_t sa = base + st * BC::kStageBytes;
+            if constexpr (PAIR) {
+              if (leader) mbar_expect_tx(full(st), static_cast<uint32_t>(2 * BC::kStageBytes));
+              const uint32_t fb = full_c0 + 8u * st;
+              tma_load_3d_pair(sa, mapA, fb, kc * BK, tj * BC::kTileCols + static_cast<int>(rank) * BM, pa);
+              tma_load_3d_pair(sa + kStageA, mapB, fb, kc * BK, ti * BN + static_cast<int>(rank) * BC::kRowsB, pb);
+            } else {
+              mbar_expect_tx(full(st), BC::kStageBytes);
+              tma_load_3d(sa, mapA, full(st), kc * BK, tj * BM, pa);
+              tma_load_3d(sa + kStageA, mapB, full(st), kc * BK, ti * BN, pb);
             }
           }
         }
@@ -180,17 +182,16 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
       long long it = 0;
       uint32_t used = 0u;                           // bit a: parity of accumulator a's uses
       bool ok = true;
+      int pos = 0;                                   // chunks so far: accumulator pos & 1
       for (long long u = first; ok && u < nunits; u += step) {
-        int pos = 0;                                 // chunks of this tile so far: accumulator pos & 1
-        for (int c = 0; ok && c < nch0; ++c) {
-          for (int prod = 0; ok && prod < 2; ++prod) {
-            const int len = prod ? len1 : len0;
-            if (c * kBoundChunk >= len) continue;
+        for (int prod = 0; ok && prod < 2; ++prod) {
+          const int len = prod ? len1 : len0;
+          for (int kb0 = 0; ok && kb0 < len; kb0 += kBoundChunk) {
             const int acc = pos++ & 1;
             if (!wait_x(tempty(acc), ((used >> acc) & 1u) ^ 1u)) { ok = false; break; }
             tc_fence_after();
             const uint32_t td = tmem + static_cast<uint32_t>(acc * BN);
-            const int kb0 = c * kBoundChunk, kb1 = min(len, (c + 1) * kBoundChunk);
+            const int kb1 = min(len, kb0 + kBoundChunk);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = static_cast<int>(it % S);
               const uint32_t ph = static_cast<uint32_t>((it / S) & 1);
@@ -225,77 +226,74 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
   } else {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;
-    const int quad = warp & 3;
-    const int half = ew >> 2;                        // columns [64 half, 64 half + 64) of a tile
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quad * 32) << 16);
-    // FP32 accumulator acc, int32 running sum of product prod
-    auto fp_col = [&](int acc, int piece) { return lane_base + static_cast<uint32_t>(acc * BN + half * 64 + 32 * piece); };
-    auto in_col = [&](int prod, int piece) {
-      return lane_base + static_cast<uint32_t>(2 * BN + prod * BN + half * 64 + 32 * piece);
-    };
-    uint32_t used = 0u;                           // bit a: parity of accumulator a's uses
+    const int quad = warp & 3;                       // TMEM lanes [32 quad, 32 quad + 32)
+    const int part = ew >> 2;                        // columns [64 part, 64 part + 64) of a tile
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(part * kBoundSums);
+    // this CTA's scratch: (lane l, tile column c) at c * BM + l, so a warp's stores are 128 contiguous bytes
+    int* park = real ? nullptr
+                     : scratch + static_cast<int64_t>(blockIdx.x) * (BM * kBoundBN) + (part * kBoundSums) * BM + quad * 32 + lane;
+    uint32_t used = 0u;                              // bit a: parity of accumulator a's uses
+    int pos = 0;
     bool ok = true;
     for (long long u = first; ok && u < nunits; u += step) {
       int tj, ti;
       tile_coords(static_cast<int>(u), s.TJ, s.TI, s.group, tj, ti);
-      int pos = 0;
-      for (int c = 0; ok && c < nch0; ++c) {
-        for (int prod = 0; ok && prod < 2; ++prod) {
-          const int len = prod ? len1 : len0;
-          if (c * kBoundChunk >= len) continue;
+      int sum[kBoundSums];                           // running sum of the product in progress
+      for (int prod = 0; ok && prod < 2; ++prod) {
+        const int len = prod ? len1 : len0;
+        if (len == 0) continue;
+#pragma unroll
+        for (int q = 0; q < kBoundSums; ++q) sum[q] = 0;
+        for (int kb0 = 0; kb0 < len; kb0 += kBoundChunk) {
           const int acc = pos++ & 1;                  // the FP32 accumulator of this chunk
           if (!mbar_wait(tfull(acc), (used >> acc) & 1u, ctl)) { ok = false; break; }
           tc_fence_after();
-#pragma unroll 1
-          for (int piece = 0; piece < 2; ++piece) {
-            uint32_t v[32], a[32];
-            tmem_ld32(fp_col(acc, piece), v);
-            if (c > 0) tmem_ld32(in_col(prod, piece), a);
+#pragma unroll
+          for (int piece = 0; piece < kBoundSums / 16; ++piece) {
+            uint32_t v[16];
+            tmem_ld16(lane_base + static_cast<uint32_t>(acc * BN + 16 * piece), v);
             tmem_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              const int x = static_cast<int>(__uint_as_float(v[q]));   // exact integer
-              a[q] = static_cast<uint32_t>((c > 0 ? static_cast<int>(a[q]) : 0) + x);
-            }
-            tmem_st32(in_col(prod, piece), a);
+            for (int q = 0; q < 16; ++q) sum[16 * piece + q] += static_cast<int>(__uint_as_float(v[q]));   // exact integer
           }
-          tmem_wait_st();
           tc_fence_before();
           if constexpr (PAIR) mbar_arrive_cluster(tempty_c0 + 8u * acc); else mbar_arrive(tempty(acc));
           used ^= 1u << acc;
         }
+        if (!ok) break;
+        if (prod == 0 && len1 > 0) {                 // C-bar_I waits in scratch while product 1 accumulates
+#pragma unroll
+          for (int q = 0; q < kBoundSums; ++q) park[q * BM] = sum[q];
+        }
       }
       if (!ok) break;
-      // max(C-bar_R, C-bar_I) per (row, this column); rows of this thread: 64 half + 32 piece + q
+      // max(C-bar_R, C-bar_I) = C-bar_I + max(product 1, 0) per (row, this column)
+      if (len1 > 0) {
+#pragma unroll
+        for (int q = 0; q < kBoundSums; ++q) {
+          const int ci = park[q * BM];
+          sum[q] = max(ci + sum[q], ci);
+        }
+      }
       const int64_t col = static_cast<int64_t>(tj) * BC::kTileCols + static_cast<int64_t>(rank) * BM + quad * 32 + lane;
       unsigned int colmax = 0u;
-#pragma unroll 1
-      for (int piece = 0; piece < 2; ++piece) {
-        uint32_t a0[32], a1[32];
-        tmem_ld32(in_col(0, piece), a0);
-        if (!real) tmem_ld32(in_col(1, piece), a1);
-        tmem_wait_ld();
-        int r[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int ci = static_cast<int>(a0[q]);
-          const int cr = real ? ci : ci + static_cast<int>(a1[q]);
-          r[q] = max(cr, ci);
-          colmax = max(colmax, static_cast<unsigned int>(r[q]));
-        }
-        // butterfly: lane L ends with the maximum over the warp of row L of this piece
+      for (int q = 0; q < kBoundSums; ++q) colmax = max(colmax, static_cast<unsigned int>(sum[q]));
+      // butterflies: lane L ends with the maximum over the warp of row 32 piece + L of this part
+#pragma unroll
+      for (int piece = 0; piece < kBoundSums / 32; ++piece) {
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
           const bool up = (lane & d) != 0;
 #pragma unroll
           for (int t = 0; t < d; ++t) {
-            const int send = up ? r[t] : r[t + d];
-            const int keep = up ? r[t + d] : r[t];
-            r[t] = max(keep, __shfl_xor_sync(0xffffffffu, send, d));
+            const int send = up ? sum[32 * piece + t] : sum[32 * piece + t + d];
+            const int keep = up ? sum[32 * piece + t + d] : sum[32 * piece + t];
+            sum[32 * piece + t] = max(keep, __shfl_xor_sync(0xffffffffu, send, d));
           }
         }
-        const int64_t row = static_cast<int64_t>(ti) * BN + half * 64 + 32 * piece + lane;
-        if (row < m) atomicMax(Mrow + row, static_cast<unsigned int>(r[0]));
+        const int64_t row = static_cast<int64_t>(ti) * BN + part * kBoundSums + 32 * piece + lane;
+        if (row < m) atomicMax(Mrow + row, static_cast<unsigned int>(sum[32 * piece]));
       }
       if (col < n) atomicMax(Ncol + col, colmax);
     }
@@ -312,29 +310,46 @@ __device__ __forceinline__ void bound_body(const CUtensorMap* mapA, const CUtens
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kBoundThreads, 1)
     gemm_bound_kernel(const __grid_constant__ CUtensorMap mapA,   // B-bar planes: MMA operand A
                       const __grid_constant__ CUtensorMap mapB,   // A-bar planes: MMA operand B
                       const BoundSched s, unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
-                      int64_t m, int64_t n, unsigned int* status) {
-  bound_body<false>(&mapA, &mapB, s, Mrow, Ncol, m, n, status);
+                      int* __restrict__ scratch, int64_t m, int64_t n, unsigned int* status) {
+  bound_body<false>(&mapA, &mapB, s, Mrow, Ncol, scratch, m, n, status);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBoundThreads, 1)
     gemm_bound_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                            const BoundSched s, unsigned int* __restrict__ Mrow, unsigned int* __restrict__ Ncol,
-                           int64_t m, int64_t n, unsigned int* status) {
-  bound_body<true>(&mapA, &mapB, s, Mrow, Ncol, m, n, status);
+                           int* __restrict__ scratch, int64_t m, int64_t n, unsigned int* status) {
+  bound_body<true>(&mapA, &mapB, s, Mrow, Ncol, scratch, m, n, status);
 }
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 
+// Scratch of a complex launch: 128 KB for each CTA it can run, at most one per
+// one-SM tile or two per pair tile, capped at kBoundMaxCtas (a launch with less
+// scratch runs fewer CTAs).  Real input needs none.
+size_t bound_scratch_bytes(int64_t m, int64_t n) {
+  if (m <= 0 || n <= 0) return 0;
+  const int64_t ti = cdiv(m, kBoundBN);
+  const int64_t one = cdiv(n, BM) * ti, two = 2 * cdiv(n, BoundCfg<true>::kTileCols) * ti;
+  int64_t ctas = one > two ? one : two;
+  if (ctas > kBoundMaxCtas) ctas = kBoundMaxCtas;
+  return static_cast<size_t>(ctas) * kBoundScratchPerCta;
+}
+
 cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, const void* planesA,
-                              const void* planesB, unsigned int* Mrow, unsigned int* Ncol, unsigned int* status,
-                              cudaStream_t st, bool pair) {
+                              const void* planesB, unsigned int* Mrow, unsigned int* Ncol, void* scratch,
+                              size_t scratch_bytes, unsigned int* status, cudaStream_t st, bool pair) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (kpad % BK || ((reinterpret_cast<uintptr_t>(planesA) | reinterpret_cast<uintptr_t>(planesB)) & 15u))
     return cudaErrorInvalidValue;
+  // complex input: room for at least one CTA (a pair: two), 4-byte aligned
+  const long long scr_ctas = real ? (1ll << 30) : static_cast<long long>(scratch_bytes / kBoundScratchPerCta);
+  if (!real && (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 3u) || scr_ctas < 1)) return cudaErrorInvalidValue;
   if (!get_encoder()) return cudaErrorNotSupported;
   static const cudaError_t attr = [] {
     cudaError_t e = cudaFuncSetAttribute(gemm_bound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -349,7 +364,7 @@ cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, con
   static const int clusters = [] {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * 1024);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kBoundThreads);
     cfg.dynamicSmemBytes = BoundCfg<true>::kSmem;
     int v = 0;
     if (cudaOccupancyMaxActiveClusters(&v, gemm_bound_pair_kernel, &cfg) != cudaSuccess) {
@@ -358,25 +373,30 @@ cudaError_t launch_gemm_bound(int64_t m, int64_t n, int64_t kpad, bool real, con
     }
     return v;
   }();
-  if (clusters <= 0) pair = false;          // no room for a CTA pair: one-SM tiles
+  if (clusters <= 0 || scr_ctas < 2) pair = false;   // no room for a CTA pair: one-SM tiles
   const int planes = real ? 1 : 3;
   const int cols = pair ? BoundCfg<true>::kTileCols : BM;
   CUtensorMap mapA, mapB;
   if (!make_map(&mapA, planesB, n, kpad, planes, BM)) return cudaErrorInvalidValue;
   if (!make_map(&mapB, planesA, m, kpad, planes, pair ? BoundCfg<true>::kRowsB : kBoundBN)) return cudaErrorInvalidValue;
   BoundSched s;
-  s.TJ = static_cast<int>((n + cols - 1) / cols);
-  s.TI = static_cast<int>((m + kBoundBN - 1) / kBoundBN);
+  s.TJ = static_cast<int>(cdiv(n, cols));
+  s.TI = static_cast<int>(cdiv(m, kBoundBN));
   s.tiles = s.TJ * s.TI;
   s.group = pair ? 8 : 16;                 // the same column span (2048) in a raster group
   s.nkb = static_cast<int>(kpad / BK);
   s.real = real ? 1 : 0;
+  int* scr = static_cast<int*>(scratch);
   if (pair) {
-    const int p = s.tiles < clusters ? s.tiles : clusters;
-    gemm_bound_pair_kernel<<<2 * p, kThreads, BoundCfg<true>::kSmem, st>>>(mapA, mapB, s, Mrow, Ncol, m, n, status);
+    long long p = s.tiles < clusters ? s.tiles : clusters;
+    if (p > scr_ctas / 2) p = scr_ctas / 2;
+    gemm_bound_pair_kernel<<<static_cast<unsigned int>(2 * p), kBoundThreads, BoundCfg<true>::kSmem, st>>>(
+        mapA, mapB, s, Mrow, Ncol, scr, m, n, status);
   } else {
-    const int grid = s.tiles < g_sms ? s.tiles : g_sms;
-    gemm_bound_kernel<<<grid, kThreads, BoundCfg<false>::kSmem, st>>>(mapA, mapB, s, Mrow, Ncol, m, n, status);
+    long long grid = s.tiles < g_sms ? s.tiles : g_sms;
+    if (grid > scr_ctas) grid = scr_ctas;
+    gemm_bound_kernel<<<static_cast<unsigned int>(grid), kBoundThreads, BoundCfg<false>::kSmem, st>>>(
+        mapA, mapB, s, Mrow, Ncol, scr, m, n, status);
   }
   count_launches(1);
   return cudaGetLastError();
