@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--overlap", choices=["auto", "on", "off"], default="auto",
                     help="EMU_TUNE_OVERLAP: split and CRT of neighbouring column blocks beside the products "
                          "(auto: the library's default, on for the real GEMMs)")
+    ap.add_argument("--bound-pair", choices=["auto", "on", "off"], default="auto",
+                    help="EMU_TUNE_BOUND_PAIR: accurate-mode bound products on SM pairs (auto: the library's default, on)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--scaling", choices=["fast", "accurate"], default="fast",
                     help="scaling vectors of Section III-B (fast or accurate mode)")
@@ -269,6 +271,8 @@ def main():
               "emu_set_scaling")
     if args.overlap != "auto":
         emu.check(emu.emu_set_tuning(emu.EMU_TUNE_OVERLAP, 1 if args.overlap == "on" else 0), "overlap")
+    if args.bound_pair != "auto":
+        emu.check(emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, 1 if args.bound_pair == "on" else 0), "bound pair")
     m, n, k, N = wl["m"], wl["n"], wl["k"], wl["N"]
     single = wl["single"]
     real = bool(wl.get("real"))
