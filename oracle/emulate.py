@@ -200,7 +200,7 @@ def emulate(A, B, N, opA="N", opB="N", **kw):
     return Emulation(apply_op(np.asarray(A), opA), apply_op(np.asarray(B), opB), N, **kw)
 
 
-def emulate_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64):
+def emulate_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64, xy=None):
     """Emulated result at the sampled entries (rows[t], cols[t]) only.
 
     Uses x_i, y_j and the truncated integers of Steps III-IV for the sampled
@@ -208,6 +208,10 @@ def emulate_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64):
     condition (cond) that is the value Steps V-v/V-vi reconstruct (the
     full-pipeline equality is checked on small sizes by the tests).
     A: m x k and B: k x n complex, after op().  Returns complex values.
+    xy: optional scaling vectors (x over all m rows, y over all n columns), for
+    instance the accurate mode's, which depend on whole rows and columns of the
+    bound product; by default the fast-mode exponents of the sampled rows and
+    columns.
     """
     P = Plan(N).P
     rows = np.asarray(rows)
@@ -216,8 +220,11 @@ def emulate_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64):
     uc, inv_c = np.unique(cols, return_inverse=True)
     Asub = np.asarray(A)[ur, :]
     Bsub = np.asarray(B)[:, uc]
-    x, *_ = vector_exponents(row_vectors(Asub), P)
-    y, *_ = vector_exponents(col_vectors(Bsub), P)
+    if xy is None:
+        x, *_ = vector_exponents(row_vectors(Asub), P)
+        y, *_ = vector_exponents(col_vectors(Bsub), P)
+    else:
+        x, y = np.asarray(xy[0])[ur], np.asarray(xy[1])[uc]
     Ar, Ai = to_pyint(truncate(Asub.real, x)), to_pyint(truncate(Asub.imag, x))
     Br, Bi = to_pyint(truncate(Bsub.real.T, y)), to_pyint(truncate(Bsub.imag.T, y))
     out = np.zeros(len(rows), dtype=np.complex128)

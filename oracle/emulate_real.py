@@ -122,10 +122,12 @@ def emulate_real(A, B, N, opA="N", opB="N", **kw):
     return RealEmulation(apply_op_real(np.asarray(A), opA), apply_op_real(np.asarray(B), opB), N, **kw)
 
 
-def emulate_real_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64):
+def emulate_real_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64, xy=None):
     """Emulated real result at sampled entries, from Steps III-IV of the sampled
     rows/columns and the exact integer dot product for c' (equal to the CRT
-    result by the CRT and condition (cond)).  A: m x k, B: k x n after op()."""
+    result by the CRT and condition (cond)).  A: m x k, B: k x n after op().
+    xy: optional scaling vectors over all rows and columns (as in
+    emulate_entries); by default the fast-mode exponents of the samples."""
     P = Plan(N).P
     rows = np.asarray(rows)
     cols = np.asarray(cols)
@@ -133,8 +135,11 @@ def emulate_real_entries(A, B, N, rows, cols, out_fmt=fp.BINARY64):
     uc, inv_c = np.unique(cols, return_inverse=True)
     Asub = np.asarray(A, dtype=np.float64)[ur, :]
     Bsub = np.asarray(B, dtype=np.float64)[:, uc]
-    x, *_ = vector_exponents(Asub, P)
-    y, *_ = vector_exponents(Bsub.T, P)
+    if xy is None:
+        x, *_ = vector_exponents(Asub, P)
+        y, *_ = vector_exponents(Bsub.T, P)
+    else:
+        x, y = np.asarray(xy[0])[ur], np.asarray(xy[1])[uc]
     Ai = to_pyint(truncate(Asub, x))
     Bi = to_pyint(truncate(Bsub.T, y))
     out = np.zeros(len(rows), dtype=np.float64)

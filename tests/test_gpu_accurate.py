@@ -209,3 +209,43 @@ def test_bound_products_on_sm_pairs(case, pair):
         got = run_gemm(A, B, 13)
     assert same_bits(got, ref), mismatch_report(got, ref)
     assert emu.emu_stream_status() == emu.EMU_OK
+
+
+@pytest.mark.parametrize("pair", [1, 0], ids=["sm_pairs", "one_sm"])
+@pytest.mark.parametrize("real", [False, True], ids=["complex", "real"])
+def test_bound_products_several_tiles_per_cta(real, pair):
+    """4096 x 4096 outputs, k = 2100: 256 (pairs) or 512 (one SM) bound-product
+    tiles, so every CTA runs several, each of three FP32 chunks (C-bar_I over 2k
+    in two, the difference product in one; real input: one of two), and complex
+    CTAs reuse their scratch.  The exponents come from the oracle's whole bound
+    product; results bit for bit on sampled entries."""
+    from oracle.accurate import accurate_exponents
+    from oracle.emulate import emulate_entries
+    from oracle.emulate_real import emulate_real_entries
+    from oracle.moduli import Plan
+    from paper_2512_08321_gb300.workloads import paper_matrix_device, paper_matrix_real_device
+    emu.check(emu.emu_set_tuning(emu.EMU_TUNE_BOUND_PAIR, pair), "bound pair")
+    m = n = 4096
+    k, N = 2100, 13
+    if real:
+        A = paper_matrix_real_device(m, k, 2.0, 120, torch.float64)      # storage (k, m)
+        B = paper_matrix_real_device(k, n, 2.0, 121, torch.float64)      # storage (n, k)
+        C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+        f = emu.emu_dgemm
+    else:
+        A = paper_matrix_device(m, k, 2.0, 122, torch.complex128)
+        B = paper_matrix_device(k, n, 2.0, 123, torch.complex128)
+        C = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+        f = emu.emu_zgemm
+    emu.check(f("N", "N", m, n, k, 1.0, A.data_ptr(), m, B.data_ptr(), k, 0.0, C.data_ptr(), m, N, None), "gemm")
+    torch.cuda.synchronize()
+    assert emu.emu_stream_status() == emu.EMU_OK
+    Ah, Bh = A.t().cpu().numpy(), B.t().cpu().numpy()                   # op(A) m x k, op(B) k x n
+    ex = accurate_exponents(Ah, Bh, Plan(N).P, real=real)
+    rng = np.random.default_rng(11)
+    rows = np.concatenate([[0, m - 1], rng.integers(0, m, 30)])
+    cols = np.concatenate([[0, n - 1], rng.integers(0, n, 30)])
+    got = C[torch.from_numpy(cols).cuda(), torch.from_numpy(rows).cuda()].cpu().numpy()
+    entries = emulate_real_entries if real else emulate_entries
+    want = entries(Ah, Bh, N, rows, cols, xy=(ex["x"], ex["y"]))
+    assert np.array_equal(got.view(np.float64), want.view(np.float64))

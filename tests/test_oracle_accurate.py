@@ -9,8 +9,8 @@ import numpy as np
 import pytest
 
 from oracle.accurate import PRE_BITS, accurate_exponents, exponent_accu, prescale
-from oracle.emulate import Emulation
-from oracle.emulate_real import RealEmulation
+from oracle.emulate import Emulation, emulate_entries
+from oracle.emulate_real import RealEmulation, emulate_real_entries
 from oracle.exact import _exact_matmul, complex_product_entries, real_product_entries
 from oracle.moduli import Plan
 from oracle.scaling import NONFINITE
@@ -127,3 +127,25 @@ def test_real_accurate_mode():
     em = RealEmulation(A, B, 9, scaling="accurate")
     exact = _exact_matmul(em.Ai, em.Bi)
     assert all(int(em.c[i, j]) == int(exact[i, j]) for i in range(10) for j in range(8))
+
+
+def test_sampled_entries_with_accurate_exponents():
+    """The sampled-entry oracle given the accurate mode's x and y (which depend
+    on whole rows and columns of the bound product) equals the full accurate
+    emulation, through the CRT, at those entries; complex and real."""
+    A = paper_matrix(40, 150, 2.0, 72)
+    B = paper_matrix(150, 36, 2.0, 73)
+    rng = np.random.default_rng(3)
+    rows, cols = rng.integers(0, 40, 30), rng.integers(0, 36, 30)
+    em = Emulation(A, B, 11, scaling="accurate", keep_residue_planes=False)
+    ex = accurate_exponents(A, B, Plan(11).P)
+    got = emulate_entries(A, B, 11, rows, cols, xy=(ex["x"], ex["y"]))
+    assert np.array_equal(got.view(np.float64), em.out[rows, cols].view(np.float64))
+    assert np.array_equal(ex["x"], em.x) and np.array_equal(ex["y"], em.y)
+    # without xy the fast-mode exponents apply, and the results differ here
+    assert not np.array_equal(emulate_entries(A, B, 11, rows, cols).view(np.float64), got.view(np.float64))
+    Ar, Br = A.real.copy(), B.real.copy()
+    er = RealEmulation(Ar, Br, 11, scaling="accurate")
+    exr = accurate_exponents(Ar, Br, Plan(11).P, real=True)
+    gotr = emulate_real_entries(Ar, Br, 11, rows, cols, xy=(exr["x"], exr["y"]))
+    assert np.array_equal(gotr, er.out[rows, cols])
