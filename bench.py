@@ -340,7 +340,7 @@ def main():
     # back (2 -> 3) and the last block's CRT (3 -> 4); the other blocks' exponents, planes and CRTs
     # run beside the products.  The per-phase times below come from one more step with overlap off.
     ov_setting = emu.emu_get_tuning(emu.EMU_TUNE_OVERLAP)
-    overlapped = ((ov_setting == 1 or (ov_setting < 0 and real)) and args.scaling == "fast" and n >= 2048)
+    overlapped = (ov_setting == 1 or (ov_setting < 0 and real)) and n >= 2048
     nblk = overlap_blocks(n) if overlapped else 1
     if overlapped:
         overlap_ms = {"planes_before_first_products": ev_ms(evs, 0, 2), "residue_products_all_blocks": ev_ms(evs, 2, 3),

@@ -313,14 +313,16 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *   EMU_TUNE_SPLIT_ELEMS residue split: entries per thread, 2/4
  *   EMU_TUNE_NBLOCK      output columns per block, 0 (automatic) or a multiple of 128;
  *                        a process setting only, never autotuned
- *   EMU_TUNE_OVERLAP     1: device-buffer GEMMs in fast scaling on the tcgen05
- *                        engine with n >= 2048 run in column blocks (the
+ *   EMU_TUNE_OVERLAP     1: device-buffer GEMMs on the tcgen05 engine with
+ *                        n >= 2048 run in column blocks (the
  *                        EMU_TUNE_NBLOCK width, else about eight blocks of a
  *                        multiple of 256 columns, at least 1024), and a
  *                        library-owned stream forms the next block's exponents
  *                        and planes and the previous block's CRT beside each
  *                        block's residue products (planes of B and residues
- *                        double-buffered); 0: one phase after another; -1
+ *                        double-buffered; in accurate scaling the bound
+ *                        products give every exponent first); 0: one phase
+ *                        after another; -1
  *                        (default): 1 for emu_dgemm/emu_sgemm, 0 for the complex
  *                        GEMMs.  On a power-capped GB300 the residue products
  *                        slow down beside the other phases: for the complex

@@ -268,9 +268,9 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
   Layout L;
   const bool accurate = (g_scaling == EMU_SCALING_ACCURATE);
   const bool presummed = presums && !accurate && k > 0;
-  // overlapped column blocks: device-buffer calls in fast mode on the tcgen05 engine
-  bool overlap = !hooks && (tn.overlap == 1 || (tn.overlap < 0 && dt.real)) && k > 0 && !accurate && fp16 &&
-                 n >= 2048;
+  // overlapped column blocks: device-buffer calls on the tcgen05 engine (accurate mode: once the
+  // bound products have given every exponent)
+  bool overlap = !hooks && (tn.overlap == 1 || (tn.overlap < 0 && dt.real)) && k > 0 && fp16 && n >= 2048;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (overlap) {
@@ -322,6 +322,39 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     return crt_on(st, mi, nj, r, xi, yj, Ci, false);
   };
   cudaError_t e;
+  // Section III-B accurate mode on the caller's stream: pre-scaling, 7-bit ceiling planes, bound
+  // products (B's planes column block by column block, in the first set of B planes), exponents
+  auto accurate_exponents = [&]() -> emu_status_t {
+    int* emA = reinterpret_cast<int*>(ws + L.off_acc);
+    unsigned int* fA = reinterpret_cast<unsigned int*>(emA + m);
+    unsigned int* MA = fA + m;
+    int* emB = reinterpret_cast<int*>(MA + m);
+    unsigned int* fB = reinterpret_cast<unsigned int*>(emB + n);
+    unsigned int* NB = fB + n;
+    if (cudaMemsetAsync(MA, 0, static_cast<size_t>(m) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(NB, 0, static_cast<size_t>(n) * 4, st) != cudaSuccess ||
+        launch_exp_max(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, st) != cudaSuccess ||
+        launch_bound_split(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, L.kpad, pa, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    for (int64_t j0 = 0; j0 < n; j0 += nb) {
+      const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
+      const void* Bj = block_ptr(j0);
+      emu_status_t r;
+      if (hooks && (r = hooks->wait_inputs(hooks->ctx, j0, nj, st)) != EMU_OK) return r;
+      if (launch_exp_max(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, st) != cudaSuccess ||
+          launch_bound_split(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, L.kpad, pb, st) !=
+              cudaSuccess)
+        return EMU_ERR_CUDA;
+      const cudaError_t be = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ws + L.off_bnd,
+                                               L.bnd_bytes, ds->status, st, tn.bound_pair == 1);
+      if (be == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
+      if (be != cudaSuccess) return EMU_ERR_CUDA;
+    }
+    if (launch_accu_finalize(m, emA, fA, MA, *pl, x, st) != cudaSuccess ||
+        launch_accu_finalize(n, emB, fB, NB, *pl, y, st) != cudaSuccess)
+      return EMU_ERR_CUDA;
+    return EMU_OK;
+  };
   phase(0, st);
   if (overlap) {
     // Column block b's residue products on the caller's stream; beside them,
@@ -335,9 +368,10 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     auto pbuf = [&](int64_t b) { return static_cast<char*>(pb) + (b & 1) * L.pb_bytes; };
     auto rbuf = [&](int64_t b) { return res + (b & 1) * L.res_bytes; };
     auto width = [&](int64_t b) { return (n - b * nb) < nb ? (n - b * nb) : nb; };
+    const bool have_xy = presummed || accurate;     // every exponent known before the pipeline starts
     auto prepare = [&](int64_t b) -> cudaError_t {   // exponents and planes of block b's columns of B
       const int64_t j0 = b * nb, nj = width(b);
-      cudaError_t err = presummed ? cudaSuccess
+      cudaError_t err = have_xy ? cudaSuccess
                                   : launch_exponents(dt.single, block_ptr(j0), nj, k, rsb, hsb, *pl, y + j0, scr, ax,
                                                      dt.real);
       if (err == cudaSuccess)
@@ -354,10 +388,11 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
       if (r != EMU_OK) return r;
       return cuda_status(cudaEventRecord(ds->ev_crt[b & 1], ax));
     };
+    if (accurate && (s = accurate_exponents()) != EMU_OK) return s;
     if ((presummed && (launch_exponent_finalize(m, presums[0], *pl, x, st) != cudaSuccess ||
                        launch_exponent_finalize(n, presums[1], *pl, y, st) != cudaSuccess)) ||
         cudaEventRecord(ds->ev_start, st) != cudaSuccess || cudaStreamWaitEvent(ax, ds->ev_start, 0) != cudaSuccess ||
-        (!presummed && launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, ax, dt.real) != cudaSuccess) ||
+        (!have_xy && launch_exponents(dt.single, A, m, k, rsa, hsa, *pl, x, scr, ax, dt.real) != cudaSuccess) ||
         launch_split(dt.single, conj_a, A, m, k, rsa, hsa, pls, x, fp16, L.kpad, pa, ax, tn.split_elems, dt.real) !=
             cudaSuccess ||
         prepare(0) != cudaSuccess)
@@ -397,34 +432,7 @@ emu_status_t gemm(Dt dt, emu_op_t ta, emu_op_t tb, int64_t m, int64_t n, int64_t
     if ((e = cudaMemsetAsync(x, 0, static_cast<size_t>(m) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
     if ((e = cudaMemsetAsync(y, 0, static_cast<size_t>(n) * 2, st)) != cudaSuccess) return EMU_ERR_CUDA;
   } else if (accurate) {
-    // Section III-B accurate mode: pre-scaling, 7-bit ceiling planes, bound products, exponents
-    int* emA = reinterpret_cast<int*>(ws + L.off_acc);
-    unsigned int* fA = reinterpret_cast<unsigned int*>(emA + m);
-    unsigned int* MA = fA + m;
-    int* emB = reinterpret_cast<int*>(MA + m);
-    unsigned int* fB = reinterpret_cast<unsigned int*>(emB + n);
-    unsigned int* NB = fB + n;
-    if (cudaMemsetAsync(MA, 0, static_cast<size_t>(m) * 4, st) != cudaSuccess ||
-        cudaMemsetAsync(NB, 0, static_cast<size_t>(n) * 4, st) != cudaSuccess ||
-        launch_exp_max(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, st) != cudaSuccess ||
-        launch_bound_split(dt.single, dt.real, A, m, k, rsa, hsa, emA, fA, L.kpad, pa, st) != cudaSuccess)
-      return EMU_ERR_CUDA;
-    for (int64_t j0 = 0; j0 < n; j0 += nb) {
-      const int64_t nj = (n - j0) < nb ? (n - j0) : nb;
-      const void* Bj = block_ptr(j0);
-      if (hooks && (s = hooks->wait_inputs(hooks->ctx, j0, nj, st)) != EMU_OK) return s;
-      if (launch_exp_max(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, st) != cudaSuccess ||
-          launch_bound_split(dt.single, dt.real, Bj, nj, k, rsb, hsb, emB + j0, fB + j0, L.kpad, pb, st) !=
-              cudaSuccess)
-        return EMU_ERR_CUDA;
-      e = launch_gemm_bound(m, nj, L.kpad, dt.real, pa, pb, MA, NB + j0, ws + L.off_bnd, L.bnd_bytes, ds->status,
-                            st, tn.bound_pair == 1);
-      if (e == cudaErrorNotSupported) return EMU_ERR_UNSUPPORTED;
-      if (e != cudaSuccess) return EMU_ERR_CUDA;
-    }
-    if (launch_accu_finalize(m, emA, fA, MA, *pl, x, st) != cudaSuccess ||
-        launch_accu_finalize(n, emB, fB, NB, *pl, y, st) != cudaSuccess)
-      return EMU_ERR_CUDA;
+    if ((s = accurate_exponents()) != EMU_OK) return s;
   } else if (presummed) {
     if (launch_exponent_finalize(m, presums[0], *pl, x, st) != cudaSuccess ||
         launch_exponent_finalize(n, presums[1], *pl, y, st) != cudaSuccess)

@@ -1,6 +1,7 @@
-"""Overlapped column blocks (EMU_TUNE_OVERLAP = 1, for n >= 2048 in fast
-scaling): the next block's exponents and planes and the previous block's CRT
-run on a second stream beside each block's residue products.
+"""Overlapped column blocks (EMU_TUNE_OVERLAP = 1, for n >= 2048): the next
+block's exponents and planes and the previous block's CRT run on a second
+stream beside each block's residue products (in accurate scaling every
+exponent comes first, from the bound products).
 Results must be bit-identical to the phases run one after another, and to
 the oracle on sampled entries."""
 import numpy as np
@@ -67,6 +68,36 @@ def test_overlapped_blocks_real(single):
     cols = np.concatenate([[0, 1024, 2048, n - 1], rng.integers(0, n, 20)])
     want = emulate_real_entries(A.astype(dt).astype(np.float64), B.astype(dt).astype(np.float64), N, rows, cols,
                                 out_fmt=fp.BINARY32 if single else fp.BINARY64)
+    assert same_bits(got[rows, cols], want), mismatch_report(got[rows, cols], want)
+
+
+@pytest.mark.parametrize("real", [False, True], ids=["complex", "real"])
+def test_overlapped_blocks_accurate(real):
+    """Accurate scaling: the bound products of all column blocks give every
+    exponent first, then the blocks overlap as in fast scaling; bit-identical
+    to one phase after another and to the oracle on sampled entries."""
+    from oracle.accurate import accurate_exponents
+    from oracle.moduli import Plan
+    m, n, k, N = 180, 2048 + 200, 300, 13
+    if real:
+        A, B = paper_matrix_real(m, k, 2.0, 520), paper_matrix_real(k, n, 2.0, 521)
+        run = lambda: run_real(A, B, N)
+    else:
+        A, B = paper_matrix(m, k, 2.0, 522), paper_matrix(k, n, 2.0, 523)
+        run = lambda: run_gemm(A, B, N)
+    emu.check(emu.emu_set_scaling(emu.EMU_SCALING_ACCURATE), "scaling")
+    try:
+        got = _with_overlap(True, run)
+        serial = _with_overlap(False, run)
+    finally:
+        emu.emu_set_scaling(emu.EMU_SCALING_FAST)
+    assert same_bits(got, serial), mismatch_report(got, serial)
+    ex = accurate_exponents(A, B, Plan(N).P, real=real)
+    rng = np.random.default_rng(8)
+    rows = np.concatenate([[0, m - 1], rng.integers(0, m, 22)])
+    cols = np.concatenate([[0, 1024, 2047, 2048, n - 1], rng.integers(0, n, 19)])
+    entries = emulate_real_entries if real else emulate_entries
+    want = entries(A, B, N, rows, cols, xy=(ex["x"], ex["y"]))
     assert same_bits(got[rows, cols], want), mismatch_report(got[rows, cols], want)
 
 
