@@ -357,9 +357,9 @@ emu_status_t emu_set_engine(emu_engine_t engine, int chunk_k);
  *                        call time (EMU_ERR_CUDA).  Grouped calls always use
  *                        one-SM tiles
  *   EMU_TUNE_BOUND_PAIR  accurate-mode bound products: 1 (default) tiles of 256
- *                        output columns x 128 rows on pairs of SMs
+ *                        output columns x 256 rows on pairs of SMs
  *                        (cta_group::2; one-SM tiles on a device that cannot
- *                        run them), 0 128 x 128 tiles on one SM; a process
+ *                        run them), 0 128 x 256 tiles on one SM; a process
  *                        setting only, never autotuned
  * emu_set_tuning sets the process default; emu_autotune_gemm times the
  * candidates of every knob for one shape on synthetic data (phases timed
